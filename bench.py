@@ -1,0 +1,400 @@
+"""Benchmark of the fused Zak-OTFS receiver (SS-CGA) on the 64x32 16-QAM batch workload.
+
+One step = the whole receiver (pilot Zak transforms, read-off and thresholding, data Zak
+transform, 10 CGA iterations, max-log demapping) over a batch of 1024 frames of 64 delay x
+32 Doppler bins, each with its own pilot frame, a 6-path fractional channel and an SNR drawn
+from 0..30 dB, through the library's C ABI (zotfs_rx).  Inputs are synthetic (synth/) and
+resident in HBM; 8 copies of the batch are rotated so the timed inputs exceed the 129 MB L2.
+
+Reported (one JSON line on rank 0):
+  value         frames/s over all ranks (device time, CUDA events)
+  e2e           the same metric with pinned host inputs copied in and the hard bits copied
+                back inside the timed region
+  plain_form    the plain single-frame FP32 form (one launch per stage) on the same frames
+  roofline      the fused kernel against the FP32 FMA peak (algorithmic flops per launch)
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same frames
+  clocks        nvidia-smi samples taken during the timed region
+
+`--impl reference` times the oracle alone (the reference arm of this workload).
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, Q, FRAMES, ITERS = 64, 32, 16, 1024, 10
+WORKLOAD = "SISO batch of 1024 frames, M=64, N=32, 16-QAM, separate pilot frame per frame, 6-path fractional " \
+           "channel (delay U[0,4], Doppler U[-3,3] bins, exponential PDP), SNR 0..30 dB, threshold 3 sigma, " \
+           "p_max 64, 10 CG iterations, complex FP32"
+SEED = 2604
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- work model
+
+def flops_per_frame(P, iters=ITERS, M=M, N=N, Q=Q):
+    """Algorithmic flops of one frame: CGA (two SS applies of 8 flops per tap-element plus
+    24 flops of vector updates per element and iteration, one adjoint for b), the two Zak
+    transforms (5 MN log2 N each) and demapping (~4 flops per constellation level per axis)."""
+    MN = M * N
+    cg = MN * (iters * (16 * P + 24) + 8 * P + 4)
+    dzt = 2 * 5 * MN * np.log2(N)
+    demap = MN * 2 * 4 * int(np.sqrt(Q))
+    return cg + dzt + demap
+
+
+def hbm_bytes_per_frame(M=M, N=N, Q=Q):
+    """Algorithmic HBM bytes of one frame in the fused kernel: pilot + data TD frames in
+    (complex64), hard bits out (LLRs and x_hat are not written in the timed step)."""
+    MN = M * N
+    return 2 * MN * 8 + MN * int(np.log2(Q)) // 8 + 4
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("common.cuh", "frame_engine.cuh", "frame_kernel.cuh", "frame_variant.cu"):
+        with open(os.path.join(ROOT, "paper_2604_02266_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "frame_kernel_64x32_batch1024.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------------ oracle arm
+
+def run_oracle(batch, frames):
+    """Full FP64 oracle receiver on the given frame indices; returns seconds."""
+    from oracle import receiver
+    t0 = time.perf_counter()
+    for f in frames:
+        receiver.receive(batch["y_pilot_td"][f].astype(complex), batch["y_data_td"][f].astype(complex), M, N, 1, 1, Q,
+                         float(batch["noise_var"][f]), float(batch["theta"][f]), ITERS, batch["a_pilot"], p_max=64)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(n_frames, sample):
+    idx = np.linspace(0, n_frames - 1, sample).astype(int)
+    return idx
+
+
+def impl_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    batch = synth.fractional_batch(FRAMES, seed=SEED, M=M, N=N, Q=Q)
+    sample = args.ref_frames
+    idx = oracle_sample(FRAMES, sample)
+    for _ in range(args.warmup):
+        run_oracle(batch, idx[:2])
+    times = [run_oracle(batch, idx) for _ in range(args.steps)]
+    fps = sample * args.steps / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": sample},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} of the {FRAMES} frames per step (evenly spaced), full FP64 receiver"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+METRIC = "equalized Zak-OTFS frames/s + p50/p99 latency, 64x32 16-QAM, vs plain form"
+
+
+# ------------------------------------------------------------------------- GPU arm
+
+def impl_zotfs(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Plan, launch_count
+
+    batch = synth.fractional_batch(FRAMES, seed=SEED + 1000 * rank, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    if args.threads:
+        plan.set_tuning(threads_per_frame=args.threads, fft_radix=args.radix, ctas_per_sm=args.ctas)
+    elif args.radix:
+        plan.set_tuning(fft_radix=args.radix, ctas_per_sm=args.ctas)
+    copies = 8  # 8 x 32 MB of TD frames > 129 MB L2
+    yp = [torch.from_numpy(batch["y_pilot_td"]).to(dev) for _ in range(copies)]
+    yd = [torch.from_numpy(batch["y_data_td"]).to(dev) for _ in range(copies)]
+    nv = torch.from_numpy(batch["noise_var"]).to(dev)
+    th = torch.from_numpy(batch["theta"]).to(dev)
+    outs = plan._rx_outputs(FRAMES, dev, False, False, False)
+    stream = torch.cuda.current_stream()
+
+    # path counts of this batch (same data every step) for the flop count
+    probe = plan.rx(yp[0], yd[0], nv, th, ITERS, FRAMES, want_paths=True)
+    P = probe["paths"].count.cpu().numpy()
+    status = probe["status"].cpu().numpy()
+    total_flops = float(sum(flops_per_frame(int(p)) for p in P))
+
+    def step(i):
+        plan.rx(yp[i % copies], yd[i % copies], nv, th, ITERS, FRAMES, out=outs)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step(i)
+            launches += launch_count()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    dev_s = float(step_ms.sum()) / 1e3
+    if ws > 1:
+        t = torch.tensor([dev_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = FRAMES * ws * args.steps / dev_s
+
+    # ---- end to end: pinned host frames in, hard bits out, every step
+    hp = torch.from_numpy(batch["y_pilot_td"]).pin_memory()
+    hd = torch.from_numpy(batch["y_data_td"]).pin_memory()
+    hbits = torch.empty_like(outs[3], device="cpu").pin_memory()
+    hstat = torch.empty_like(outs[4], device="cpu").pin_memory()
+    dp, dd = torch.empty_like(yp[0]), torch.empty_like(yd[0])
+
+    def e2e_step():
+        dp.copy_(hp, non_blocking=True)
+        dd.copy_(hd, non_blocking=True)
+        plan.rx(dp, dd, nv, th, ITERS, FRAMES, out=outs)
+        hbits.copy_(outs[3], non_blocking=True)
+        hstat.copy_(outs[4], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": FRAMES * ws * args.steps / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": int(hp.numel() * hp.element_size() + hd.numel() * hd.element_size()),
+           "d2h_bytes_per_step": int(hbits.numel() + hstat.numel() * 4)}
+
+    # ---- plain form: one frame at a time, one launch per stage
+    n_plain = args.plain_frames
+    pout = plan._rx_outputs(1, dev, False, False, False)
+    lat = []
+    for f in range(n_plain + 2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.rx(yp[0][f:f + 1], yd[0][f:f + 1], nv[f:f + 1], th[f:f + 1], ITERS, 1, out=pout, plain=True)
+        b.record(stream)
+        b.synchronize()
+        if f >= 2:  # first two are warm-up
+            lat.append(a.elapsed_time(b))
+    lat = np.array(lat) if lat else np.array([np.nan])
+    plain_fps = 1e3 * len(lat) / lat.sum() if n_plain > 0 else float("nan")
+
+    # ---- roofline of the fused kernel (one launch per step)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    kern_s = float(np.mean(step_ms)) / 1e3
+    achieved = total_flops / kern_s / 1e12
+    traffic = profiled_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock, "
+                               "MEASURED_PEAKS.json)",
+                "hbm_GBps": hbm_bytes_per_frame() * FRAMES / kern_s / 1e9,
+                "hbm_peak_GBps": float(peaks.get("hbm_gbs", 6800.0))}
+
+    # ---- FP64 oracle on the host cores (bounded sample)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        idx = oracle_sample(FRAMES, args.oracle_frames)
+        secs = run_oracle(batch, idx)
+        cpu = {"value": len(idx) / secs, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(idx)} of the {FRAMES} frames (evenly spaced), full FP64 receiver, single thread"}
+
+    if rank == 0:
+        bps = int(np.log2(Q))
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": FRAMES, "M": M, "N": N, "qam": Q,
+                       "iters": ITERS, "p_max": 64, "l2": "8 rotating input copies (256 MB) > L2",
+                       "threads_per_frame": plan.tuning()["threads_per_frame"] or "library default",
+                       "fft_radix": plan.tuning()["fft_radix"]},
+            "mbit_s": value * M * N * bps / 1e6,
+            "latency_ms": {"batch_p50": float(np.percentile(step_ms, 50)),
+                           "batch_p99": float(np.percentile(step_ms, 99))},
+            "plain_form": {"value": plain_fps, "unit": "frames/s", "frames": len(lat),
+                           "frame_latency_p50_ms": float(np.percentile(lat, 50)),
+                           "frame_latency_p99_ms": float(np.percentile(lat, 99))},
+            "speedup_vs_plain": value / plain_fps / ws,
+            "paths": {"mean": float(P.mean()), "min": int(P.min()), "max": int(P.max()),
+                      "truncated_frames": int((status == 6).sum())},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="zotfs", choices=["zotfs", "reference"])
+    ap.add_argument("--threads", type=int, default=0, help="threads per frame (tuning)")
+    ap.add_argument("--radix", type=int, default=0, help="FFT radix (tuning)")
+    ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM (tuning)")
+    ap.add_argument("--plain-frames", type=int, default=32)
+    ap.add_argument("--oracle-frames", type=int, default=48, help="oracle sample for cpu_baseline")
+    ap.add_argument("--ref-frames", type=int, default=8, help="oracle frames per step with --impl reference")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return impl_reference(args)
+    return impl_zotfs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,272 @@
+/*
+ * zotfs.h -- C ABI of the GB300 (sm_103a) Zak-OTFS receiver library.
+ *
+ * The library implements the data-parallel hot path of a Zak-OTFS receiver: the
+ * discrete Zak transform into the delay-Doppler (DD) grid, the point-pilot read-off
+ * that yields a path list, the structured-sparse (SS) channel operator H_dd and its
+ * adjoint, the compute-aware conjugate-gradient LMMSE equaliser (SS-CGA) and max-log
+ * QAM demapping.  Passages cited below are sections, equations and algorithms of
+ * arXiv:2604.02266 ("Real-Time and Scalable Zak-OTFS Receiver Processing on GPUs").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex numbers are interleaved {re, im}.  ZOTFS_C64 is two float32 (the layout
+ *    of torch.complex64); ZOTFS_C32_F16 / ZOTFS_C32_BF16 are two 16-bit floats.
+ *  - A DD grid X[k, l] (delay bin k < M, Doppler bin l < N) is stored vectorised as
+ *    q = l*M + k (Sec. IV-B, "We index the q-th row ... q = l M + k").
+ *  - A time-domain (TD) frame y[i], i = k + n*M < M*N, is stored in sample order.
+ *  - M and N are powers of two with 16 <= M <= 256, 8 <= N <= 64 and M*N <= 16384.
+ *  - MIMO (n_rx x n_tx, not in the paper): unknowns are stacked per tx antenna,
+ *    observations per rx antenna, one path list per (rx, tx) pair, and tx antenna t
+ *    sends its own pilot frame (time-orthogonal pilots).  Layouts, per frame f:
+ *        pilot TD frames  [f][t][r][MN]     data TD frames [f][r][MN]
+ *        path lists       [f][r][t]         x_hat          [f][t][MN]
+ *        LLRs             [f][t][MN][bps]   hard bits      [f][t][MN*bps/8] bytes
+ *    where bps = log2(qam); bits are packed LSB-first (bit b -> byte b/8, position b%8)
+ *    and within a symbol the I-axis Gray label (MSB first) precedes the Q-axis label.
+ *  - Every pointer named "dev" is device memory owned by the caller; "host" pointers are
+ *    read during the call only.  The library owns only what a plan or a batch holds.
+ *  - Calls taking a stream are stream-ordered and never synchronise the host, except
+ *    the create/destroy calls.  Argument errors are returned synchronously; per-frame
+ *    conditions (a truncated path list, a bad path, a non-finite residual, a timed-out
+ *    wait) are written to a caller-supplied device status array as zotfs_status values.
+ *  - No call throws across the ABI.  zotfs_last_error() returns a thread-local message
+ *    describing the most recent failure in the calling thread.
+ */
+#ifndef ZOTFS_H
+#define ZOTFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum zotfs_status {
+  ZOTFS_OK = 0,
+  ZOTFS_EINVAL = 1,        /* bad argument (synchronous) or a bad path entry (per frame) */
+  ZOTFS_ENOMEM = 2,        /* device or host allocation failed */
+  ZOTFS_ECUDA = 3,         /* a CUDA runtime call failed */
+  ZOTFS_EUNSUPPORTED = 4,  /* shape or option outside what the library handles */
+  ZOTFS_ETIMEOUT = 5,      /* a bounded device wait gave up (per frame) */
+  ZOTFS_ETRUNCATED = 6,    /* more than p_max taps passed the threshold (per frame, result valid) */
+  ZOTFS_ENONFINITE = 7     /* a CG residual became NaN/Inf (per frame) */
+} zotfs_status;
+
+/* The CUDA stream type: identical to cudaStream_t, without including CUDA headers. */
+typedef struct CUstream_st* zotfs_stream;
+
+/* Pulse shape of the link.  Recorded in the plan; the receiver arithmetic of Eq. zak
+ * does not depend on it (only the channel the frames went through does). */
+typedef enum zotfs_pulse { ZOTFS_PULSE_SINC = 0, ZOTFS_PULSE_RECT = 1 } zotfs_pulse;
+
+typedef enum zotfs_dtype {
+  ZOTFS_C64 = 0,       /* complex float32 */
+  ZOTFS_C32_F16 = 1,   /* complex float16 storage, float32 arithmetic */
+  ZOTFS_C32_BF16 = 2,  /* complex bfloat16 storage, float32 arithmetic */
+  ZOTFS_C128 = 3       /* complex float64 (plans with compute == ZOTFS_COMPUTE_FP64) */
+} zotfs_dtype;
+
+/* Arithmetic precision of a plan's kernels.  FP32: complex float32 vectors with the CG's
+ * inner products combined and alpha/beta formed in FP64.  FP64: everything in float64; the
+ * complex vectors the caller passes in or receives (DD inputs, operator inputs/outputs,
+ * x_hat) are then ZOTFS_C128, LLRs stay float32. */
+typedef enum zotfs_compute { ZOTFS_COMPUTE_FP32 = 0, ZOTFS_COMPUTE_FP64 = 1 } zotfs_compute;
+
+typedef enum zotfs_pilot_mode {
+  /* The paper's arrangement (Sec. V, Fig. 1): a point-pilot frame precedes each data
+   * frame; the read-off spans the whole grid (Eq. heff's index ranges). */
+  ZOTFS_PILOT_SEPARATE = 0,
+  /* Pilot and data share one frame: the pilot sits at (K0, L0) inside a guard band of
+   * delay offsets [-guard, guard] (all Doppler bins) carrying no data; the read-off
+   * covers delay offsets [0, guard] and the pilot's response H (a_pilot e_(K0,L0)) is
+   * subtracted before equalisation.  Not in the paper. */
+  ZOTFS_PILOT_EMBEDDED = 1
+} zotfs_pilot_mode;
+
+/* Per-plan options.  zotfs_plan_create fills the defaults given here. */
+typedef struct zotfs_options {
+  int32_t pilot_mode;  /* zotfs_pilot_mode, default ZOTFS_PILOT_SEPARATE */
+  int32_t K0, L0;      /* pilot position; default (M/2, N/2) (Sec. III-B "Channel Estimation") */
+  float   a_pilot;     /* pilot amplitude divided out of the read-off; default sqrt(MN)
+                          (a pilot frame with the energy of a data frame), 0.5 sqrt(MN) when
+                          embedded */
+  int32_t guard;       /* embedded mode: guard half-width in delay bins; default 2 */
+  int32_t p_max;       /* path-list capacity per antenna pair, 1..256; default 64 */
+  int32_t in_dtype;    /* zotfs_dtype of TD input frames; default ZOTFS_C64 */
+  int32_t tap_dtype;   /* zotfs_dtype of path taps in zotfs_paths; default ZOTFS_C64 */
+  int32_t compute;     /* zotfs_compute; default ZOTFS_COMPUTE_FP32 */
+} zotfs_options;
+
+typedef struct zotfs_plan_s* zotfs_plan;
+
+/* Device-resident path lists (the structured-sparse channel of Sec. IV-B, reduced to
+ * the P dominant taps {h_p, k_p - K0, l_p - L0}).  n_lists = n_frames * n_rx * n_tx,
+ * ordered [frame][rx][tx].  Entries of list i occupy [i*p_max, i*p_max + count[i]) and
+ * are sorted by ascending pilot-grid index q = l_p*M + k_p. */
+typedef struct zotfs_paths {
+  int32_t* count;   /* dev [n_lists]: number of paths P <= p_max */
+  int32_t* status;  /* dev [n_lists]: ZOTFS_OK or ZOTFS_ETRUNCATED; may be NULL on input */
+  int16_t* dk;      /* dev [n_lists*p_max]: delay offset k_p - K0, in [-M/2, M/2) */
+  int16_t* dl;      /* dev [n_lists*p_max]: Doppler offset l_p - L0, in [-N/2, N/2) */
+  void*    h;       /* dev [n_lists*p_max] complex taps h_p, element type tap_dtype */
+  int32_t  p_max;   /* capacity per list (must equal the plan's p_max) */
+  int32_t  tap_dtype;
+} zotfs_paths;
+
+/* ---------------------------------------------------------------- plans ------------ */
+
+/* Create a plan for frames of M delay x N Doppler bins, n_rx x n_tx antennas and square
+ * Gray QAM of order qam (4, 16 or 64).  Builds the root-of-unity tables (FP64 on the host,
+ * stored FP32) and the plan's scratch for the plain form.  The only allocating calls are
+ * the create calls.  *out is set to NULL on failure. */
+zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pulse, int qam,
+                               zotfs_plan* out);
+zotfs_status zotfs_plan_set_options(zotfs_plan plan, const zotfs_options* opts);
+zotfs_status zotfs_plan_get_options(zotfs_plan plan, zotfs_options* opts);
+zotfs_status zotfs_plan_destroy(zotfs_plan plan);
+
+/* Kernel launch shape for the fused per-frame kernels: threads per frame (a multiple of
+ * M dividing M*N, 32..1024) and the FFT radix (2 or 4) of the in-shared-memory Zak
+ * transform.  0 keeps the library's choice.  Used by the autotuner. */
+typedef struct zotfs_tuning {
+  int32_t threads_per_frame;
+  int32_t fft_radix;
+  int32_t ctas_per_sm;  /* resident CTAs per SM the persistent grid is sized for; 0 = max */
+} zotfs_tuning;
+zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* tuning);
+zotfs_status zotfs_plan_get_tuning(zotfs_plan plan, zotfs_tuning* tuning);
+
+/* ---------------------------------------------------------- hot-path stages -------- */
+
+/* Discrete Zak transform, Eq. zak: Y[k,l] = N^-1/2 sum_{n<N} y[k+nM] e^{-j2pi nl/N}.
+ * y_td: dev [n_grids][MN] of the plan's in_dtype.  y_dd: dev [n_grids][MN] ZOTFS_C64.
+ * Radix-2/4 FFT along the Doppler axis in shared memory. */
+zotfs_status zotfs_dzt(zotfs_plan plan, const void* y_td, float* y_dd, int n_grids,
+                       zotfs_stream stream);
+
+/* Channel estimation: Zak transform of each received pilot frame, read-off of
+ * the effective channel (Eq. heff, in its Hadamard form Eq. heff_hadamard, divided by
+ * a_pilot), thresholding |h_eff| > theta (Eq. heff_thres) and stable compaction into a
+ * path list.  When more than p_max taps pass, the p_max largest magnitudes are kept
+ * (ties to the lower q) and the list's status is ZOTFS_ETRUNCATED.
+ * y_pilot_td: dev, separate mode [n_frames][n_tx][n_rx][MN]; embedded mode the data
+ *             frames [n_frames][1][1][MN].  theta: dev float [n_frames].
+ * paths:      host struct of dev pointers, written for n_frames*n_rx*n_tx lists. */
+zotfs_status zotfs_estimate(zotfs_plan plan, const void* y_pilot_td, const float* theta,
+                            int n_frames, const zotfs_paths* paths, zotfs_stream stream);
+
+/* Structured-sparse operator apply (Eq. sparse_mvm / Eq. sparse_herm_mvm with the
+ * index maps Eq. map_chMatDD_col / Eq. herm_mapping and the twisted phase of Sec. IV-B):
+ *   adjoint == 0: u = H v,   v dev [n_frames][n_tx][MN] C64, u dev [n_frames][n_rx][MN] C64
+ *   adjoint != 0: u = H^H v, v dev [n_frames][n_rx][MN] C64, u dev [n_frames][n_tx][MN] C64
+ * Each path's quasi-periodic wrap count and phase are computed on the fly from the path
+ * list; no dense or per-entry matrix is formed.  status: dev int32 [n_frames] or NULL. */
+zotfs_status zotfs_ss_apply(zotfs_plan plan, const zotfs_paths* paths, const float* v, float* u,
+                            int adjoint, int n_frames, int32_t* status, zotfs_stream stream);
+
+/* LMMSE equalisation by the compute-aware CGA (Algorithm 1): b = H^H y, then
+ * `iters` fixed iterations of {a = H^H H p + lambda p; alpha = c_n / Re(p^H a); x += alpha p;
+ * c -= alpha a; p = c + (c_n'/c_n) p}, lambda = noise_var[f].  Vectors stay in shared
+ * memory; alpha and beta are formed in FP64.  Readings: alpha = 0 when Re(p^H a) = 0 and
+ * beta = 0 when c_n = 0.
+ * y:         dev data frames, TD [n_frames][n_rx][MN] in the plan's in_dtype when
+ *            y_is_dd == 0, else DD [n_frames][n_rx][MN] C64 (embedded mode: TD only).
+ * noise_var: dev float [n_frames].  x_hat: dev [n_frames][n_tx][MN] C64.
+ * status:    dev int32 [n_frames] or NULL. */
+zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const zotfs_paths* paths,
+                            const float* noise_var, int iters, float* x_hat, int n_frames,
+                            int32_t* status, zotfs_stream stream);
+
+/* Demapping (Eq. demod extended to soft output): per bit j the max-log LLR
+ * (min_{s: b_j=1} |x-s|^2 - min_{s: b_j=0} |x-s|^2) / noise_var[f] over the plan's Gray
+ * square QAM with unit mean energy, and the hard bit (LLR < 0).  llr (dev float
+ * [n_frames][n_tx][MN][bps]) and bits (dev uint8 [n_frames][n_tx][MN*bps/8]) may each be
+ * NULL.  x_hat: dev [n_frames][n_tx][MN] C64. */
+zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise_var, float* llr,
+                         uint8_t* bits, int n_frames, zotfs_stream stream);
+
+/* The whole receiver fused: per frame in one persistent kernel whose CTAs pull
+ * frames from a device work counter: pilot Zak transforms and read-off -> path lists in
+ * shared memory -> data Zak transform -> CGA -> demapping.  HBM traffic is the TD
+ * frames in and the results out.  Outputs paths, x_hat and llr may be NULL (bits too,
+ * but then nothing is returned but status).  status: dev int32 [n_frames] (required). */
+zotfs_status zotfs_rx(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td,
+                      const float* noise_var, const float* theta, int iters,
+                      const zotfs_paths* paths, float* x_hat, float* llr, uint8_t* bits,
+                      int32_t* status, int n_frames, zotfs_stream stream);
+
+/* The plain form: the same receiver run one frame at a time with one kernel launch per
+ * stage and per CG step (Zak transform, read-off, compaction, b = H^H y, and per iteration
+ * H p, H^H t + lambda p, two inner products, the x/c update and the p update), vectors in
+ * the plan's global scratch, FP32.  It is the comparison baseline for zotfs_rx, with the
+ * same arguments and results. */
+zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td,
+                            const float* noise_var, const float* theta, int iters,
+                            const zotfs_paths* paths, float* x_hat, float* llr, uint8_t* bits,
+                            int32_t* status, int n_frames, zotfs_stream stream);
+
+/* ------------------------------------------------------ uneven persistent batch ---- */
+
+/* One frame of an uneven batch: its own shape, antennas, QAM order, noise and threshold,
+ * and its own device buffers (layouts as above with n_frames = 1). */
+typedef struct zotfs_frame_desc {
+  int32_t M, N, n_rx, n_tx, qam, iters;
+  int32_t pilot_mode, guard, p_max, in_dtype;
+  int32_t K0, L0;           /* -1: M/2, N/2 */
+  float   noise_var, theta, a_pilot;  /* a_pilot <= 0: the plan default for the mode */
+  const void* y_pilot;      /* dev TD pilots (separate mode) */
+  const void* y_data;       /* dev TD data frames */
+  float*   x_hat;           /* dev or NULL */
+  float*   llr;             /* dev or NULL */
+  uint8_t* bits;            /* dev or NULL */
+  int32_t* path_count;      /* dev [n_rx*n_tx] or NULL: the estimated path lists ... */
+  int16_t* path_dk;         /* ... dev [n_rx*n_tx*p_max] */
+  int16_t* path_dl;
+  float*   path_h;          /* dev [n_rx*n_tx*p_max] C64 */
+} zotfs_frame_desc;
+
+typedef struct zotfs_batch_s* zotfs_batch;
+
+/* Launch shape for one bucket of an uneven batch (frames of equal M, N, n_rx, n_tx). */
+typedef struct zotfs_tuning_entry {
+  int32_t M, N, n_rx, n_tx;
+  zotfs_tuning tuning;
+} zotfs_tuning_entry;
+
+typedef struct zotfs_batch_opts {
+  int32_t threads_per_frame;  /* 0: per-bucket choice (tuning table entry, else the library's) */
+  int32_t ctas_per_sm;        /* 0: as many as fit */
+  int32_t fft_radix;          /* 0: per-bucket choice, else 2 or 4 */
+  int32_t n_tuning;           /* entries in `tuning` (host array, read during create only) */
+  const zotfs_tuning_entry* tuning;
+} zotfs_batch_opts;
+
+/* Build a batch from host descriptors: validates every frame, groups frames into buckets
+ * of equal (M, N, n_rx, n_tx, qam, pilot mode, p_max, in_dtype), uploads the descriptors
+ * and the per-shape root-of-unity tables, and sizes each bucket's persistent grid in
+ * proportion to its share of the batch's work so all buckets run side by side.
+ * Descriptors hold device pointers that must stay valid while the batch is used.
+ * Allocates. */
+zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames,
+                                const zotfs_batch_opts* opts, zotfs_batch* out);
+/* Run the batch: one persistent frame kernel per bucket, forked from `stream` onto the
+ * batch's own streams and joined back (events), stream-ordered, no allocation and no host
+ * synchronisation, so it can be captured in a CUDA graph.  status: dev int32 [n_frames]
+ * in descriptor order.  One batch must not run on two streams at once. */
+zotfs_status zotfs_rx_batch(zotfs_batch batch, int32_t* status, zotfs_stream stream);
+zotfs_status zotfs_batch_destroy(zotfs_batch batch);
+
+/* ----------------------------------------------------------------- misc ------------ */
+
+/* Thread-local message for the most recent failure in this thread ("" if none). */
+const char* zotfs_last_error(void);
+/* Number of fused-kernel launches (CTAs grids) the most recent call in this thread made. */
+int zotfs_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZOTFS_H */

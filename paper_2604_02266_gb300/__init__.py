@@ -1,0 +1,261 @@
+"""GB300-native Zak-OTFS receiver hot path (SS-CGA), Python binding.
+
+The library itself is ``libzotfs.so`` (hand-written CUDA for sm_103a, C ABI in
+``include/zotfs.h``).  This package only marshals PyTorch tensors into that ABI: device
+pointers, sizes and the current CUDA stream.  There is no CPU or PyTorch fallback; if the
+library is missing, loading it raises.
+
+Tensor conventions (see include/zotfs.h for the full contract):
+
+* complex data is ``torch.complex64`` (ZOTFS_C64), or a ``[..., 2]`` float16 / bfloat16
+  tensor for 16-bit storage;
+* a DD grid is vectorised q = l*M + k; a TD frame is in sample order;
+* frames are batched on the leading axis: pilots ``[F, n_tx, n_rx, M*N]``, data
+  ``[F, n_rx, M*N]``, ``x_hat [F, n_tx, M*N]``, LLRs ``[F, n_tx, M*N, bps]``,
+  bits ``[F, n_tx, M*N*bps/8]`` (uint8, LSB-first).
+"""
+
+import ctypes as C
+import math
+
+import torch
+
+from . import _zotfs as Z
+from ._zotfs import (ZotfsError, OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, ETRUNCATED,  # noqa: F401
+                     ENONFINITE, STATUS_NAMES, C64, C32_F16, C32_BF16, C128, COMPUTE_FP32, COMPUTE_FP64,
+                     PILOT_SEPARATE, PILOT_EMBEDDED, PULSE_SINC, PULSE_RECT)
+
+__all__ = ["Plan", "Paths", "Batch", "ZotfsError", "library_path", "launch_count"]
+
+_DTYPES = {C64: torch.complex64, C32_F16: torch.float16, C32_BF16: torch.bfloat16, C128: torch.complex128}
+
+
+def library_path():
+    return Z.LIB_PATH
+
+
+def launch_count():
+    """Fused-kernel launches made by the most recent library call in this thread."""
+    return int(Z.zotfs_last_launch_count())
+
+
+def _p(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _s(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None:
+            if not t.is_cuda:
+                raise ValueError("zotfs tensors must live on a CUDA device")
+            if not t.is_contiguous():
+                raise ValueError("zotfs tensors must be contiguous")
+
+
+class Paths:
+    """Device path lists for ``n_lists = n_frames * n_rx * n_tx`` antenna pairs."""
+
+    def __init__(self, n_lists, p_max, tap_dtype=C64, device="cuda"):
+        self.n_lists = n_lists
+        self.p_max = p_max
+        self.tap_dtype = tap_dtype
+        self.count = torch.zeros(n_lists, dtype=torch.int32, device=device)
+        self.status = torch.zeros(n_lists, dtype=torch.int32, device=device)
+        self.dk = torch.zeros(n_lists * p_max, dtype=torch.int16, device=device)
+        self.dl = torch.zeros(n_lists * p_max, dtype=torch.int16, device=device)
+        if tap_dtype in (C64, C128):
+            self.h = torch.zeros(n_lists * p_max, dtype=_DTYPES[tap_dtype], device=device)
+        else:
+            self.h = torch.zeros(n_lists * p_max, 2, dtype=_DTYPES[tap_dtype], device=device)
+        self._c = Z.zotfs_paths(self.count.data_ptr(), self.status.data_ptr(), self.dk.data_ptr(),
+                                self.dl.data_ptr(), self.h.data_ptr(), p_max, tap_dtype)
+
+    @property
+    def c(self):
+        return C.byref(self._c)
+
+    def to_host(self):
+        """List of (dk, dl, h) numpy arrays per list (h as complex128)."""
+        cnt = self.count.cpu().numpy()
+        dk = self.dk.cpu().numpy().reshape(self.n_lists, self.p_max)
+        dl = self.dl.cpu().numpy().reshape(self.n_lists, self.p_max)
+        if self.tap_dtype in (C64, C128):
+            h = self.h.cpu().numpy().reshape(self.n_lists, self.p_max)
+        else:
+            hh = self.h.float().cpu().numpy().reshape(self.n_lists, self.p_max, 2)
+            h = hh[..., 0] + 1j * hh[..., 1]
+        return [(dk[i, :cnt[i]].astype(int), dl[i, :cnt[i]].astype(int), h[i, :cnt[i]].astype(complex))
+                for i in range(self.n_lists)]
+
+
+class Plan:
+    """A zotfs plan: one grid shape, antenna configuration and QAM order."""
+
+    def __init__(self, M, N, n_rx=1, n_tx=1, qam=16, pulse=PULSE_SINC, **options):
+        h = C.c_void_p()
+        Z.check(Z.zotfs_plan_create(M, N, n_rx, n_tx, pulse, qam, C.byref(h)))
+        self._h = h
+        self.M, self.N, self.n_rx, self.n_tx, self.qam = M, N, n_rx, n_tx, qam
+        self.MN = M * N
+        self.bps = int(round(math.log2(qam)))
+        if options:
+            self.set_options(**options)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                Z.zotfs_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    # ----------------------------------------------------------------- configuration
+    def options(self):
+        o = Z.zotfs_options()
+        Z.check(Z.zotfs_plan_get_options(self._h, C.byref(o)))
+        return {f: getattr(o, f) for f, _ in o._fields_}
+
+    def set_options(self, **kw):
+        o = Z.zotfs_options()
+        Z.check(Z.zotfs_plan_get_options(self._h, C.byref(o)))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        Z.check(Z.zotfs_plan_set_options(self._h, C.byref(o)))
+
+    def set_tuning(self, threads_per_frame=0, fft_radix=0, ctas_per_sm=0):
+        t = Z.zotfs_tuning(threads_per_frame, fft_radix, ctas_per_sm)
+        Z.check(Z.zotfs_plan_set_tuning(self._h, C.byref(t)))
+
+    def tuning(self):
+        t = Z.zotfs_tuning()
+        Z.check(Z.zotfs_plan_get_tuning(self._h, C.byref(t)))
+        return {"threads_per_frame": t.threads_per_frame, "fft_radix": t.fft_radix, "ctas_per_sm": t.ctas_per_sm}
+
+    @property
+    def p_max(self):
+        return self.options()["p_max"]
+
+    @property
+    def cdtype(self):
+        """torch dtype of the plan's complex vectors (complex64, or complex128 for FP64 plans)."""
+        return torch.complex128 if self.options()["compute"] == COMPUTE_FP64 else torch.complex64
+
+    def new_paths(self, n_frames, device="cuda"):
+        o = self.options()
+        return Paths(n_frames * self.n_rx * self.n_tx, o["p_max"], o["tap_dtype"], device)
+
+    # ---------------------------------------------------------------------- stages
+    def dzt(self, y_td, out=None, stream=None):
+        n = y_td.numel() // self.MN if y_td.is_complex() else y_td.numel() // (2 * self.MN)
+        out = torch.empty(n, self.MN, dtype=self.cdtype, device=y_td.device) if out is None else out
+        _need_cuda(y_td, out)
+        Z.check(Z.zotfs_dzt(self._h, _p(y_td), _p(out), n, _s(stream)))
+        return out
+
+    def estimate(self, y_pilot_td, theta, n_frames, paths=None, stream=None):
+        paths = self.new_paths(n_frames, y_pilot_td.device) if paths is None else paths
+        _need_cuda(y_pilot_td, theta)
+        Z.check(Z.zotfs_estimate(self._h, _p(y_pilot_td), _p(theta), n_frames, paths.c, _s(stream)))
+        return paths
+
+    def ss_apply(self, paths, v, n_frames, adjoint=False, out=None, status=None, stream=None):
+        nout = self.n_tx if adjoint else self.n_rx
+        out = torch.empty(n_frames, nout, self.MN, dtype=self.cdtype, device=v.device) if out is None else out
+        _need_cuda(v, out, status)
+        Z.check(Z.zotfs_ss_apply(self._h, paths.c, _p(v), _p(out), int(bool(adjoint)), n_frames, _p(status),
+                                 _s(stream)))
+        return out
+
+    def equalize(self, y, paths, noise_var, iters, n_frames, y_is_dd=False, x_hat=None, status=None,
+                 stream=None):
+        x_hat = (torch.empty(n_frames, self.n_tx, self.MN, dtype=self.cdtype, device=y.device)
+                 if x_hat is None else x_hat)
+        _need_cuda(y, noise_var, x_hat, status)
+        Z.check(Z.zotfs_equalize(self._h, _p(y), int(bool(y_is_dd)), paths.c, _p(noise_var), iters, _p(x_hat),
+                                 n_frames, _p(status), _s(stream)))
+        return x_hat
+
+    def demap(self, x_hat, noise_var, n_frames, llr=True, bits=True, stream=None):
+        dev = x_hat.device
+        L = torch.empty(n_frames, self.n_tx, self.MN, self.bps, dtype=torch.float32, device=dev) if llr else None
+        B = torch.empty(n_frames, self.n_tx, self.MN * self.bps // 8, dtype=torch.uint8, device=dev) if bits else None
+        _need_cuda(x_hat, noise_var, L, B)
+        Z.check(Z.zotfs_demap(self._h, _p(x_hat), _p(noise_var), _p(L), _p(B), n_frames, _s(stream)))
+        return L, B
+
+    def _rx_outputs(self, n_frames, device, want_paths, want_x, want_llr):
+        paths = self.new_paths(n_frames, device) if want_paths else None
+        x = torch.empty(n_frames, self.n_tx, self.MN, dtype=self.cdtype, device=device) if want_x else None
+        L = torch.empty(n_frames, self.n_tx, self.MN, self.bps, dtype=torch.float32, device=device) if want_llr else None
+        B = torch.empty(n_frames, self.n_tx, self.MN * self.bps // 8, dtype=torch.uint8, device=device)
+        st = torch.empty(n_frames, dtype=torch.int32, device=device)
+        return paths, x, L, B, st
+
+    def rx(self, y_pilot_td, y_data_td, noise_var, theta, iters, n_frames, want_paths=False, want_x=False,
+           want_llr=False, out=None, stream=None, plain=False):
+        """Whole receiver per frame (fused persistent kernel, or the plain form)."""
+        if out is None:
+            out = self._rx_outputs(n_frames, y_data_td.device, want_paths, want_x, want_llr)
+        paths, x, L, B, st = out
+        _need_cuda(y_pilot_td, y_data_td, noise_var, theta, x, L, B, st)
+        fn = Z.zotfs_rx_plain if plain else Z.zotfs_rx
+        Z.check(fn(self._h, _p(y_pilot_td), _p(y_data_td), _p(noise_var), _p(theta), iters,
+                   paths.c if paths is not None else None, _p(x), _p(L), _p(B), _p(st), n_frames, _s(stream)))
+        return {"paths": paths, "x_hat": x, "llr": L, "bits": B, "status": st}
+
+
+class Batch:
+    """An uneven batch (zotfs_batch_create / zotfs_rx_batch).  ``frames`` is a list of dicts
+    with the zotfs_frame_desc fields; tensor-valued fields are device tensors whose
+    storage must stay alive while the batch is used (the Batch keeps references)."""
+
+    _PTR_FIELDS = ("y_pilot", "y_data", "x_hat", "llr", "bits", "path_count", "path_dk", "path_dl", "path_h")
+
+    def __init__(self, frames, threads_per_frame=0, ctas_per_sm=0, fft_radix=0, tuning=None):
+        n = len(frames)
+        arr = (Z.zotfs_frame_desc * max(n, 1))()
+        self._keep = []
+        for i, fr in enumerate(frames):
+            d = arr[i]
+            d.K0 = d.L0 = -1
+            for key, val in fr.items():
+                if key in self._PTR_FIELDS:
+                    if val is not None:
+                        _need_cuda(val)
+                        self._keep.append(val)
+                        setattr(d, key, val.data_ptr())
+                else:
+                    setattr(d, key, val)
+        entries = tuning or []
+        tarr = (Z.zotfs_tuning_entry * max(len(entries), 1))()
+        for i, (shape, tun) in enumerate(entries):
+            tarr[i].M, tarr[i].N, tarr[i].n_rx, tarr[i].n_tx = shape
+            tarr[i].tuning = Z.zotfs_tuning(tun.get("threads_per_frame", 0), tun.get("fft_radix", 0),
+                                            tun.get("ctas_per_sm", 0))
+        opts = Z.zotfs_batch_opts(threads_per_frame, ctas_per_sm, fft_radix, len(entries), tarr)
+        h = C.c_void_p()
+        Z.check(Z.zotfs_batch_create(arr, n, C.byref(opts), C.byref(h)))
+        self._h = h
+        self.n_frames = n
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                Z.zotfs_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def run(self, status, stream=None):
+        _need_cuda(status)
+        Z.check(Z.zotfs_rx_batch(self._h, _p(status), _s(stream)))
+        return status

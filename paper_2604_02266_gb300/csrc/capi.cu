@@ -1,0 +1,488 @@
+// C ABI of the zotfs library: plans, argument validation and dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace zotfs {
+
+thread_local std::string g_err;
+thread_local int g_launches = 0;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+zotfs_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return ZOTFS_ECUDA;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+static zotfs_status inval(const std::string& msg) {
+  set_error(msg);
+  return ZOTFS_EINVAL;
+}
+
+void fill_plan_args(const zotfs_plan_s* plan, FrameArgs& A) {
+  std::memset(&A, 0, sizeof(A));
+  A.M = plan->M;
+  A.N = plan->N;
+  A.logM = plan->logM;
+  A.logN = plan->logN;
+  A.nrx = plan->nrx;
+  A.ntx = plan->ntx;
+  A.K0 = plan->opt.K0;
+  A.L0 = plan->opt.L0;
+  A.pilot_mode = plan->opt.pilot_mode;
+  A.guard = plan->opt.guard;
+  A.p_max = plan->opt.p_max;
+  A.in_dtype = plan->opt.in_dtype;
+  A.tap_dtype = plan->opt.tap_dtype;
+  A.qam = plan->qam;
+  A.bps = plan->bps;
+  A.a_pilot = plan->opt.a_pilot;
+  A.inv_sqrtN = 1.0 / std::sqrt((double)plan->N);
+  A.sqrtN = std::sqrt((double)plan->N);
+  A.pam_d = std::sqrt(3.0 / (2.0 * (plan->qam - 1)));
+  const bool fp64 = plan->opt.compute == ZOTFS_COMPUTE_FP64;
+  A.W = fp64 ? (const void*)plan->d_W64 : (const void*)plan->d_W;
+  A.Tab = fp64 ? (const void*)plan->d_Tab64 : (const void*)plan->d_Tab;
+}
+
+static int real_bytes_of(const zotfs_plan_s* plan) { return plan->opt.compute == ZOTFS_COMPUTE_FP64 ? 8 : 4; }
+
+bool choose_frame_cfg(int M, int N, int nrx, int ntx, int p_max, int threads_override, FrameCfg& cfg,
+                      int real_bytes) {
+  const int MN = M * N, nb = nrx > ntx ? nrx : ntx;
+  static const int kPref[] = {0, 1, 3, 2, 4, 5, 6, 7};
+  const size_t kSmemCap = 227 * 1024;
+  for (int idx : kPref) {
+    int E, NB, TMAX, rb;
+    if (!frame_variant_info(idx, E, NB, TMAX, rb)) continue;
+    if (rb != real_bytes) continue;
+    if (NB < nb || E > N || (N % E) != 0) continue;
+    const int T = MN / E;
+    if (T < 32 || (T % 32) != 0 || T > TMAX || (T % M) != 0) continue;
+    if (threads_override > 0 && T != threads_override) continue;
+    const size_t smem = frame_smem_bytes(M, N, E, nrx, ntx, p_max, real_bytes);
+    if (smem > kSmemCap) continue;
+    cfg.E = E;
+    cfg.NB = NB;
+    cfg.T = T;
+    cfg.variant = idx;
+    cfg.smem = smem;
+    return true;
+  }
+  return false;
+}
+
+zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameArgs& A, int radix, int ctas_per_sm,
+                                 cudaStream_t stream) {
+  int* counter = plan->d_counters + (plan->counter_next++ & 63);
+  A.work_counter = counter;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work counter)");
+  int blocks = 0;
+  e = frame_variant_occupancy(cfg.variant, cfg.T, cfg.smem, blocks);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (blocks < 1) {
+    set_error("frame kernel does not fit on an SM (registers or shared memory)");
+    return ZOTFS_EUNSUPPORTED;
+  }
+  if (ctas_per_sm > 0 && ctas_per_sm < blocks) blocks = ctas_per_sm;
+  long long grid = (long long)plan->sm_count * blocks;
+  if (grid > A.n_frames) grid = A.n_frames;
+  e = frame_variant_launch(cfg.variant, A, radix, (int)grid, cfg.T, cfg.smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frame kernel launch");
+  ++g_launches;
+  return ZOTFS_OK;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static zotfs_status check_paths(const zotfs_plan_s* plan, const zotfs_paths* paths, bool need_status_ok) {
+  (void)need_status_ok;
+  if (!paths) return inval("paths is NULL");
+  if (!paths->count || !paths->dk || !paths->dl || !paths->h) return inval("paths: NULL device pointer");
+  if (paths->p_max != plan->opt.p_max) return inval("paths.p_max differs from the plan's p_max");
+  if (paths->tap_dtype != plan->opt.tap_dtype) return inval("paths.tap_dtype differs from the plan's tap_dtype");
+  return ZOTFS_OK;
+}
+
+static zotfs_status frame_cfg_or_fail(const zotfs_plan_s* plan, int nrx, int ntx, FrameCfg& cfg) {
+  if (!choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, cfg,
+                        real_bytes_of(plan))) {
+    set_error("no shared-memory-resident frame kernel for this shape/antenna count/tuning");
+    return ZOTFS_EUNSUPPORTED;
+  }
+  return ZOTFS_OK;
+}
+
+static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 4 ? 4 : 2; }
+
+}  // namespace zotfs
+
+using namespace zotfs;
+
+extern "C" {
+
+const char* zotfs_last_error(void) { return g_err.c_str(); }
+int zotfs_last_launch_count(void) { return g_launches; }
+
+zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pulse, int qam, zotfs_plan* out) {
+  g_launches = 0;
+  if (!out) return inval("out is NULL");
+  *out = nullptr;
+  if (!is_pow2(M) || M < 16 || M > 256) return inval("M must be a power of two in [16, 256]");
+  if (!is_pow2(N) || N < 8 || N > 64) return inval("N must be a power of two in [8, 64]");
+  if (M * N > 16384) return inval("M*N must be <= 16384");
+  if (n_rx < 1 || n_rx > 4 || n_tx < 1 || n_tx > 4) return inval("n_rx, n_tx must be in [1, 4]");
+  if (qam != 4 && qam != 16 && qam != 64) return inval("qam must be 4, 16 or 64");
+  if (pulse != ZOTFS_PULSE_SINC && pulse != ZOTFS_PULSE_RECT) return inval("unknown pulse");
+
+  zotfs_plan_s* p = new (std::nothrow) zotfs_plan_s();
+  if (!p) {
+    set_error("host allocation failed");
+    return ZOTFS_ENOMEM;
+  }
+  std::memset(p, 0, sizeof(*p));
+  p->M = M;
+  p->N = N;
+  p->logM = ilog2(M);
+  p->logN = ilog2(N);
+  p->nrx = n_rx;
+  p->ntx = n_tx;
+  p->qam = qam;
+  p->bps = ilog2(qam);
+  p->pulse = pulse;
+  p->opt.pilot_mode = ZOTFS_PILOT_SEPARATE;
+  p->opt.K0 = M / 2;
+  p->opt.L0 = N / 2;
+  p->opt.a_pilot = (float)std::sqrt((double)M * N);
+  p->opt.guard = 2;
+  p->opt.p_max = 64;
+  p->opt.in_dtype = ZOTFS_C64;
+  p->opt.tap_dtype = ZOTFS_C64;
+  p->opt.compute = ZOTFS_COMPUTE_FP32;
+  p->tune.threads_per_frame = 0;
+  p->tune.fft_radix = 2;
+  p->tune.ctas_per_sm = 0;
+
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "device query");
+  }
+  const int MN = M * N;
+  // root-of-unity tables: FP64 on the host, stored FP32
+  std::vector<float2> W(MN), Tab(MN);
+  std::vector<double2> W64(MN), Tab64(MN);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int t = 0; t < MN; ++t) {
+    const double a = two_pi * (double)t / (double)MN;
+    W64[t] = make_double2(std::cos(a), std::sin(a));
+    W[t] = make_float2((float)W64[t].x, (float)W64[t].y);
+  }
+  for (int dl = -N / 2; dl < N / 2; ++dl)
+    for (int k = 0; k < M; ++k) {
+      const size_t src = (size_t)(((long long)dl * k) & (MN - 1));
+      Tab[(size_t)(dl + N / 2) * M + k] = W[src];
+      Tab64[(size_t)(dl + N / 2) * M + k] = W64[src];
+    }
+  p->plain_bytes = plain_scratch_bytes(M, N, n_rx, n_tx, 256);
+  e = cudaMalloc(&p->d_W, sizeof(float2) * MN);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab, sizeof(float2) * MN);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_W64, sizeof(double2) * MN);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab64, sizeof(double2) * MN);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(int) * 64);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_plain, p->plain_bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_W, W.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_Tab, Tab.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_W64, W64.data(), sizeof(double2) * MN, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_Tab64, Tab64.data(), sizeof(double2) * MN, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_counters, 0, sizeof(int) * 64);
+  if (e != cudaSuccess) {
+    zotfs_plan_destroy(p);
+    if (e == cudaErrorMemoryAllocation) {
+      set_error("device allocation failed");
+      return ZOTFS_ENOMEM;
+    }
+    return cuda_fail(e, "plan tables");
+  }
+  *out = p;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_plan_destroy(zotfs_plan plan) {
+  if (!plan) return ZOTFS_OK;
+  if (plan->d_W) cudaFree(plan->d_W);
+  if (plan->d_Tab) cudaFree(plan->d_Tab);
+  if (plan->d_W64) cudaFree(plan->d_W64);
+  if (plan->d_Tab64) cudaFree(plan->d_Tab64);
+  if (plan->d_counters) cudaFree(plan->d_counters);
+  if (plan->d_plain) cudaFree(plan->d_plain);
+  delete plan;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_plan_set_options(zotfs_plan plan, const zotfs_options* o) {
+  if (!plan || !o) return inval("NULL argument");
+  zotfs_options n = *o;
+  if (n.pilot_mode != ZOTFS_PILOT_SEPARATE && n.pilot_mode != ZOTFS_PILOT_EMBEDDED) return inval("pilot_mode");
+  if (n.K0 < 0) n.K0 = plan->M / 2;
+  if (n.L0 < 0) n.L0 = plan->N / 2;
+  if (n.K0 != plan->M / 2 || n.L0 != plan->N / 2)
+    return inval("the pilot must sit at (M/2, N/2) (Sec. III-B 'Channel Estimation')");
+  if (!(n.a_pilot > 0.f)) {
+    const double s = std::sqrt((double)plan->M * plan->N);
+    n.a_pilot = (float)(n.pilot_mode == ZOTFS_PILOT_EMBEDDED ? 0.5 * s : s);
+  }
+  if (!std::isfinite(n.a_pilot)) return inval("a_pilot must be finite");
+  if (n.pilot_mode == ZOTFS_PILOT_EMBEDDED) {
+    if (plan->nrx != 1 || plan->ntx != 1) return inval("embedded pilot: SISO plans only");
+    if (n.guard < 0 || n.guard >= plan->M / 2) return inval("guard must be in [0, M/2)");
+  }
+  if (n.p_max < 1 || n.p_max > 256) return inval("p_max must be in [1, 256]");
+  for (int d : {n.in_dtype, n.tap_dtype})
+    if (d != ZOTFS_C64 && d != ZOTFS_C32_F16 && d != ZOTFS_C32_BF16 && d != ZOTFS_C128) return inval("unknown dtype");
+  if (n.compute != ZOTFS_COMPUTE_FP32 && n.compute != ZOTFS_COMPUTE_FP64) return inval("compute must be FP32 or FP64");
+  if (n.compute == ZOTFS_COMPUTE_FP64) {
+    FrameCfg cfg;
+    if (!choose_frame_cfg(plan->M, plan->N, plan->nrx, plan->ntx, n.p_max, 0, cfg, 8))
+      return inval("no FP64 frame kernel for this shape / antenna count");
+  }
+  plan->opt = n;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_plan_get_options(zotfs_plan plan, zotfs_options* o) {
+  if (!plan || !o) return inval("NULL argument");
+  *o = plan->opt;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* t) {
+  if (!plan || !t) return inval("NULL argument");
+  if (t->fft_radix != 0 && t->fft_radix != 2 && t->fft_radix != 4) return inval("fft_radix must be 0, 2 or 4");
+  if (t->threads_per_frame < 0 || t->threads_per_frame > 1024) return inval("threads_per_frame");
+  if (t->ctas_per_sm < 0) return inval("ctas_per_sm");
+  zotfs_tuning n = *t;
+  if (n.fft_radix == 0) n.fft_radix = 2;
+  if (n.threads_per_frame > 0) {
+    FrameCfg cfg;
+    if (!choose_frame_cfg(plan->M, plan->N, plan->nrx, plan->ntx, plan->opt.p_max, n.threads_per_frame, cfg,
+                          real_bytes_of(plan)))
+      return inval("no frame kernel with that many threads per frame for this plan");
+  }
+  plan->tune = n;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_plan_get_tuning(zotfs_plan plan, zotfs_tuning* t) {
+  if (!plan || !t) return inval("NULL argument");
+  *t = plan->tune;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_dzt(zotfs_plan plan, const void* y_td, float* y_dd, int n_grids, zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_grids < 0) return inval("n_grids < 0");
+  if (n_grids == 0) return ZOTFS_OK;
+  if (!y_td || !y_dd) return inval("NULL buffer");
+  if (!aligned16(y_td)) return inval("y_td must be 16-byte aligned");
+  FrameCfg cfg;
+  zotfs_status s = frame_cfg_or_fail(plan, 1, 1, cfg);
+  if (s) return s;
+  FrameArgs A;
+  fill_plan_args(plan, A);
+  A.nrx = A.ntx = 1;
+  A.mode = kDzt;
+  A.n_frames = n_grids;
+  A.y_data = y_td;
+  A.u_out = y_dd;
+  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+}
+
+zotfs_status zotfs_estimate(zotfs_plan plan, const void* y_pilot_td, const float* theta, int n_frames,
+                            const zotfs_paths* paths, zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_frames < 0) return inval("n_frames < 0");
+  zotfs_status s = check_paths(plan, paths, true);
+  if (s) return s;
+  if (n_frames == 0) return ZOTFS_OK;
+  if (!y_pilot_td || !theta) return inval("NULL buffer");
+  if (!aligned16(y_pilot_td)) return inval("y_pilot_td must be 16-byte aligned");
+  const bool emb = plan->opt.pilot_mode == ZOTFS_PILOT_EMBEDDED;
+  FrameCfg cfg;
+  s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
+  if (s) return s;
+  FrameArgs A;
+  fill_plan_args(plan, A);
+  A.mode = kEstimate | kWritePaths;
+  A.n_frames = n_frames;
+  if (emb) A.y_data = y_pilot_td;
+  else A.y_pilot = y_pilot_td;
+  A.theta = theta;
+  A.pcount = paths->count;
+  A.pstatus = paths->status;
+  A.pdk = paths->dk;
+  A.pdl = paths->dl;
+  A.ph = paths->h;
+  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+}
+
+zotfs_status zotfs_ss_apply(zotfs_plan plan, const zotfs_paths* paths, const float* v, float* u, int adjoint,
+                            int n_frames, int32_t* status, zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_frames < 0) return inval("n_frames < 0");
+  zotfs_status s = check_paths(plan, paths, false);
+  if (s) return s;
+  if (n_frames == 0) return ZOTFS_OK;
+  if (!v || !u) return inval("NULL buffer");
+  FrameCfg cfg;
+  s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
+  if (s) return s;
+  FrameArgs A;
+  fill_plan_args(plan, A);
+  A.mode = kLoadPaths | kApply;
+  A.n_frames = n_frames;
+  A.adjoint = adjoint ? 1 : 0;
+  A.v_in = v;
+  A.u_out = u;
+  A.status = status;
+  A.pcount = paths->count;
+  A.pdk = paths->dk;
+  A.pdl = paths->dl;
+  A.ph = paths->h;
+  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+}
+
+zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const zotfs_paths* paths,
+                            const float* noise_var, int iters, float* x_hat, int n_frames, int32_t* status,
+                            zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_frames < 0 || iters < 0) return inval("n_frames and iters must be >= 0");
+  zotfs_status s = check_paths(plan, paths, false);
+  if (s) return s;
+  if (n_frames == 0) return ZOTFS_OK;
+  if (!y || !noise_var || !x_hat) return inval("NULL buffer");
+  if (y_is_dd && plan->opt.pilot_mode == ZOTFS_PILOT_EMBEDDED)
+    return inval("embedded pilot: equalize takes the TD frame (the pilot is removed after the Zak transform)");
+  if (!y_is_dd && !aligned16(y)) return inval("y must be 16-byte aligned");
+  FrameCfg cfg;
+  s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
+  if (s) return s;
+  FrameArgs A;
+  fill_plan_args(plan, A);
+  A.mode = kLoadPaths | kCG | kWriteX;
+  A.n_frames = n_frames;
+  A.y_data = y;
+  A.y_is_dd = y_is_dd ? 1 : 0;
+  A.noise_var = noise_var;
+  A.iters = iters;
+  A.x_hat = x_hat;
+  A.status = status;
+  A.pcount = paths->count;
+  A.pdk = paths->dk;
+  A.pdl = paths->dl;
+  A.ph = paths->h;
+  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+}
+
+zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise_var, float* llr, uint8_t* bits,
+                         int n_frames, zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_frames < 0) return inval("n_frames < 0");
+  if (n_frames == 0) return ZOTFS_OK;
+  if (!x_hat || !noise_var) return inval("NULL buffer");
+  if (!llr && !bits) return ZOTFS_OK;
+  FrameCfg cfg;
+  zotfs_status s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
+  if (s) return s;
+  FrameArgs A;
+  fill_plan_args(plan, A);
+  A.mode = kLoadX | kDemap;
+  A.n_frames = n_frames;
+  A.x_in = x_hat;
+  A.noise_var = noise_var;
+  A.llr = llr;
+  A.bits = bits;
+  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+}
+
+zotfs_status zotfs_rx(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,
+                      const float* theta, int iters, const zotfs_paths* paths, float* x_hat, float* llr, uint8_t* bits,
+                      int32_t* status, int n_frames, zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_frames < 0 || iters < 0) return inval("n_frames and iters must be >= 0");
+  if (n_frames == 0) return ZOTFS_OK;
+  const bool emb = plan->opt.pilot_mode == ZOTFS_PILOT_EMBEDDED;
+  if ((!emb && !y_pilot_td) || !y_data_td || !noise_var || !theta || !status) return inval("NULL buffer");
+  if ((!emb && !aligned16(y_pilot_td)) || !aligned16(y_data_td)) return inval("TD frames must be 16-byte aligned");
+  if (paths) {
+    zotfs_status s = check_paths(plan, paths, true);
+    if (s) return s;
+  }
+  FrameCfg cfg;
+  zotfs_status s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
+  if (s) return s;
+  FrameArgs A;
+  fill_plan_args(plan, A);
+  A.mode = kEstimate | kCG | kDemap | (paths ? kWritePaths : 0) | (x_hat ? kWriteX : 0);
+  A.n_frames = n_frames;
+  A.y_pilot = y_pilot_td;
+  A.y_data = y_data_td;
+  A.noise_var = noise_var;
+  A.theta = theta;
+  A.iters = iters;
+  A.x_hat = x_hat;
+  A.llr = llr;
+  A.bits = bits;
+  A.status = status;
+  if (paths) {
+    A.pcount = paths->count;
+    A.pstatus = paths->status;
+    A.pdk = paths->dk;
+    A.pdl = paths->dl;
+    A.ph = paths->h;
+  }
+  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+}
+
+zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,
+                            const float* theta, int iters, const zotfs_paths* paths, float* x_hat, float* llr,
+                            uint8_t* bits, int32_t* status, int n_frames, zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_frames < 0 || iters < 0) return inval("n_frames and iters must be >= 0");
+  if (n_frames == 0) return ZOTFS_OK;
+  const bool emb = plan->opt.pilot_mode == ZOTFS_PILOT_EMBEDDED;
+  if ((!emb && !y_pilot_td) || !y_data_td || !noise_var || !theta || !status) return inval("NULL buffer");
+  if (plan->opt.compute != ZOTFS_COMPUTE_FP32) {
+    set_error("the plain form runs in FP32 only");
+    return ZOTFS_EUNSUPPORTED;
+  }
+  if (paths) {
+    zotfs_status s = check_paths(plan, paths, true);
+    if (s) return s;
+  }
+  return run_plain(plan, y_pilot_td, y_data_td, noise_var, theta, iters, paths, x_hat, llr, bits, status, n_frames,
+                   stream);
+}
+
+}  // extern "C"

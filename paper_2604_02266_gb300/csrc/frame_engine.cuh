@@ -1,0 +1,529 @@
+// Frame-resident Zak-OTFS receiver engine: one CTA owns one frame at a time and keeps
+// everything it needs in shared memory.
+//
+// Work split.  A CTA of T threads handles an M x N grid (times the antenna blocks); thread
+// t owns column k = t mod M and the E = MN/T consecutive Doppler rows
+// [j0, j0 + E), j0 = (t / M) E, of every block.  The per-element CG vectors (x, c, p and the
+// operator outputs) live in that thread's registers.
+//
+// Shared-memory vector layout ("ext").  The vector an operator gathers from is stored as
+// its quasi-periodic extension (footnote of Eq. y_channel_DD):
+//     X_ext[A, r] = X[<A>_M, <r>_N] exp(j2pi floor(A/M) <r>_N / N)
+// for columns A in [-M/2, 3M/2) and rows r in [0, N + E - 1), column-major: element (A, r)
+// at (A + M/2) CS + r with column stride CS = N + E - 1 (odd, so the 32 consecutive columns
+// a warp reads fall in distinct banks).
+// With it, path p's contribution to output (k, l) -- the twisted shift of Sec. IV-B with
+// map Eq. map_chMatDD_col, wrap count n and phase phi -- becomes a plain shifted read:
+//     (H v)[k, l]   = sum_p h_p W[dl (k - dk)]      X_ext[k - dk, l - dl]
+//     (H^H u)[k, l] = sum_p conj(h_p W[dl k])       U_ext[k + dk, l + dl]
+// with W[t] = exp(j2pi t/(MN)) and (dk, dl) = (k_p - K0, l_p - L0).  The quasi-periodic
+// phase exp(j2pi n l_{p,q} / N) of the paper's phi is carried by the stored halo columns,
+// the term (l_p - L0) A by the per-(path, column) coefficient, so each gather is one
+// shared load at a constant offset and two packed FMAs.  Rows are periodic (no phase), so
+// E - 1 halo rows let a thread read its E consecutive source rows without a wrap.
+//
+// Everything is templated on the arithmetic type R (float, or double for FP64 plans).
+#pragma once
+
+#include "common.cuh"
+
+namespace zotfs {
+
+template <typename R>
+struct PathRecT {             // one dominant path in shared memory
+  typename Cx<R>::C h;        // h_p
+  typename Cx<R>::C hf;       // h_p * W[-dl dk]: forward coefficient is hf * W[dl k]
+  int dk, dl;                 // centred offsets k_p - K0, l_p - L0
+  int pad0, pad1;
+};
+
+enum FrameMode : int {
+  kEstimate = 1,     // pilots -> path lists in shared memory
+  kLoadPaths = 2,    // path lists from global memory
+  kCG = 4,           // data frame -> x_hat
+  kDemap = 8,        // x_hat -> LLRs / bits
+  kWriteX = 16,      // store x_hat
+  kWritePaths = 32,  // store the estimated path lists
+  kApply = 64,       // one operator apply u = H v or H^H v
+  kLoadX = 128,      // x_hat from global memory (demap only)
+  kDzt = 256         // Zak transform only (y_td -> y_dd)
+};
+
+// per-frame status bits, folded into one zotfs_status at the end (most severe wins)
+enum StatusBit : int { kStTrunc = 1, kStInval = 2, kStNonFinite = 4, kStTimeout = 8 };
+__device__ __forceinline__ int status_from_bits(int b) {
+  if (b & kStTimeout) return ZOTFS_ETIMEOUT;
+  if (b & kStNonFinite) return ZOTFS_ENONFINITE;
+  if (b & kStInval) return ZOTFS_EINVAL;
+  if (b & kStTrunc) return ZOTFS_ETRUNCATED;
+  return ZOTFS_OK;
+}
+
+struct FrameArgs {
+  // geometry (one shape per launch)
+  int M, N, logM, logN, nrx, ntx, T;
+  int K0, L0, pilot_mode, guard, p_max, in_dtype, tap_dtype, qam, bps;
+  double a_pilot, inv_sqrtN, sqrtN, pam_d;
+  const void* W;    // W[t] = exp(j2pi t/(MN)), t in [0, MN), complex R
+  const void* Tab;  // Tab[(dl + N/2) M + k] = W[(dl k) mod MN], complex R
+  // work distribution
+  int n_frames, mode;
+  int* work_counter;
+  // inputs (complex vectors are complex R unless a dtype says otherwise)
+  const void* y_pilot;
+  const void* y_data;
+  int y_is_dd;
+  const float* noise_var;
+  const float* theta;
+  int iters;
+  const void* v_in;
+  int adjoint;
+  const void* x_in;
+  // path lists in global memory: read with kLoadPaths, written with kWritePaths
+  int32_t* pcount;
+  int32_t* pstatus;
+  int16_t* pdk;
+  int16_t* pdl;
+  void* ph;
+  // outputs
+  void* x_hat;
+  float* llr;
+  uint8_t* bits;
+  int32_t* status;
+  void* u_out;
+  // uneven batches: per-frame buffers come from descriptors (frame f of this launch is
+  // descriptor frame_ids[f]); NULL for the single-shape calls
+  const zotfs_frame_desc* descs;
+  const int* frame_ids;
+};
+
+// Global-memory path lists of one frame: list li (= r * n_tx + t) has count[li] entries at
+// [li * p_max, li * p_max + count[li]) of dk, dl and h.
+struct PathIO {
+  int32_t* count;
+  int32_t* status;  // may be NULL
+  int16_t* dk;
+  int16_t* dl;
+  void* h;
+  int tap_dtype;
+};
+
+// Everything one frame reads and writes, resolved at the start of the frame.
+struct FrameIO {
+  const char* y_pilot;  // pilot TD grids [t][r] of this frame (separate pilot mode)
+  const char* y_data;   // data grids [r] (TD, or DD when y_is_dd)
+  const char* v_in;     // operator input [b][MN] (apply mode)
+  const char* x_in;     // x_hat input [t][MN] (demap-only mode)
+  float lam, theta;
+  int iters;
+  char* x_hat;          // [t][MN] or NULL
+  float* llr;           // [t][MN][bps] or NULL
+  uint8_t* bits;        // [t][MN bps / 8] or NULL
+  char* u_out;          // [b][MN] (apply / DZT modes)
+  PathIO paths;         // lists of this frame (in for kLoadPaths, out for kWritePaths)
+  int32_t* status;      // this frame's status word or NULL
+};
+
+struct SharedHdr {       // fixed part of the dynamic shared memory
+  uint64_t mbar;
+  double dsc[4];
+  double fsc[4];
+  int isc[4];
+  int scan[40];
+  double red[32];
+};
+
+// Shared-memory bytes needed by a frame kernel launch (host and device agree on this).
+__host__ __device__ __forceinline__ int ext_rows(int N, int E) { return N + E - 1; }  // = column stride CS
+__host__ __device__ __forceinline__ size_t ext_block_elems(int M, int N, int E) {
+  return (size_t)ext_rows(N, E) * (size_t)(2 * M);
+}
+__host__ __device__ __forceinline__ size_t frame_smem_bytes(int M, int N, int E, int nrx, int ntx, int p_max,
+                                                            int real_bytes) {
+  size_t hdr = (sizeof(SharedHdr) + 127) & ~size_t(127);
+  const size_t rec = (size_t)4 * real_bytes + 16;  // PathRecT<R>
+  size_t paths = (size_t)nrx * ntx * p_max * rec + (size_t)nrx * ntx * sizeof(int) * 2;
+  paths = (paths + 127) & ~size_t(127);
+  int nb = nrx > ntx ? nrx : ntx;
+  size_t ext = (size_t)nb * ext_block_elems(M, N, E) * 2 * real_bytes;
+  return hdr + paths + ext;
+}
+
+constexpr uint32_t kMaxPolls = 1u << 22;
+
+// ------------------------------------------------------------------ staging + DZT
+
+// Copy one TD grid (MN complex of `dtype`) into dst[0, MN) as complex R by a bulk async
+// copy (narrower storage lands in the upper part of the buffer and is widened in place).
+// All threads call; returns false (uniformly) if the bounded wait gave up.
+template <typename R, int E>
+__device__ __forceinline__ bool stage_grid(typename Cx<R>::C* dst, const void* src, int MN, int dtype,
+                                           uint64_t* bar, uint32_t& phase) {
+  using C = typename Cx<R>::C;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const uint32_t bytes = (uint32_t)MN * (uint32_t)dtype_bytes(dtype);
+  const bool native = dtype == Cx<R>::kIoDtype;
+  char* d = reinterpret_cast<char*>(dst) + (native ? 0 : (size_t)MN * sizeof(C) - bytes);
+  __syncthreads();  // earlier generic accesses to dst are complete
+  if (tid == 0) {
+    fence_proxy_async_smem();
+    bulk_g2s(d, src, bytes, bar);
+  }
+  bool ok = mbar_wait_bounded(bar, phase, kMaxPolls);
+  if (!ok) ok = mbar_wait_bounded(bar, phase, kMaxPolls);  // let an in-flight copy land
+  phase ^= 1u;
+  if (__syncthreads_or(!ok)) return false;
+  if (!native) {
+    C tmp[E];  // MN == T * E
+#pragma unroll
+    for (int i = 0; i < E; ++i) tmp[i] = load_complex<C>(d, (size_t)tid + (size_t)i * T, dtype);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E; ++i) dst[tid + i * T] = tmp[i];
+    __syncthreads();
+  }
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::C tw(const FrameArgs& A, size_t idx) {
+  return __ldg(reinterpret_cast<const typename Cx<R>::C*>(A.W) + idx);
+}
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::C tab(const FrameArgs& A, size_t idx) {
+  return __ldg(reinterpret_cast<const typename Cx<R>::C*>(A.Tab) + idx);
+}
+
+// In-place DIF FFT along the Doppler axis of X[n][k] (n < N rows of M): afterwards row
+// bitrev(l) holds sqrt(N) Y[., l] of Eq. zak.  radix 4 fuses pairs of radix-2 stages.
+template <typename R>
+__device__ __forceinline__ void dzt_inplace(typename Cx<R>::C* X, const FrameArgs& A, int radix) {
+  using C = typename Cx<R>::C;
+  const int M = A.M, N = A.N, logM = A.logM, MN = M * N, T = blockDim.x;
+  int h = N >> 1;
+  if (radix == 4) {
+    // radix-4 DIF stages handle spans (h, h/2) at once: 4 points n, n+q, n+2q, n+3q with q = h/2
+    for (; h >= 2; h >>= 2) {
+      const int q = h >> 1;         // quarter of the current block length 2h
+      const int tws = N / (2 * h);  // twiddle stride of the first radix-2 stage
+      for (int b = threadIdx.x; b < MN / 4; b += T) {
+        const int k = b & (M - 1), g = b >> logM;  // g in [0, N/4)
+        const int gi = g & (q - 1);
+        const int n0 = (g - gi) * 4 + gi;
+        C* p0 = X + (size_t)n0 * M + k;
+        const C x0 = p0[0], x1 = p0[(size_t)q * M], x2 = p0[(size_t)2 * q * M], x3 = p0[(size_t)3 * q * M];
+        // first radix-2 stage (span h = 2q): pairs (x0,x2), (x1,x3) with twiddles W_{2h}^{gi}, W_{2h}^{gi+q}
+        const C w0 = conjf2(tw<R>(A, (size_t)(gi * tws) << logM));
+        const C w1 = conjf2(tw<R>(A, (size_t)((gi + q) * tws) << logM));
+        const C a0 = cadd(x0, x2), a2 = cmul(csub(x0, x2), w0);
+        const C a1 = cadd(x1, x3), a3 = cmul(csub(x1, x3), w1);
+        // second radix-2 stage (span q): pairs (a0,a1), (a2,a3) with twiddle W_{h}^{gi}
+        const C w2 = conjf2(tw<R>(A, (size_t)(gi * tws * 2) << logM));
+        p0[0] = cadd(a0, a1);
+        p0[(size_t)q * M] = cmul(csub(a0, a1), w2);
+        p0[(size_t)2 * q * M] = cadd(a2, a3);
+        p0[(size_t)3 * q * M] = cmul(csub(a2, a3), w2);
+      }
+      __syncthreads();
+    }
+  }
+  for (; h >= 1; h >>= 1) {
+    const int tws = N / (2 * h);
+    for (int b = threadIdx.x; b < MN / 2; b += T) {
+      const int k = b & (M - 1), g = b >> logM;
+      const int gi = g & (h - 1);
+      const int n = ((g - gi) << 1) + gi;
+      C* p0 = X + (size_t)n * M + k;
+      const C u = p0[0], v = p0[(size_t)h * M];
+      const C w = conjf2(tw<R>(A, (size_t)(gi * tws) << logM));
+      p0[0] = cadd(u, v);
+      p0[(size_t)h * M] = cmul(csub(u, v), w);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int l, int logN) { return (int)(__brev((unsigned)l) >> (32 - logN)); }
+
+// --------------------------------------------------------------- ext writing
+
+// Store the thread's E values of one block (column k, rows j0..j0+E-1) into ext, with the
+// quasi-periodic halo column and the periodic halo rows.
+template <typename R, int E>
+__device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArgs& A, int k, int j0,
+                                          const typename Cx<R>::C (&v)[E]) {
+  using C = typename Cx<R>::C;
+  const int M = A.M, N = A.N, CS = N + E - 1, Hk = M >> 1, logM = A.logM, MN = M * N;
+  // halo column: k < M/2 stores X_ext[k + M] = X[k] W_N[l]; k >= M/2 stores X_ext[k - M] = X[k] W_N[-l]
+  const bool low = k < Hk;
+  C* mcol = ext + (size_t)(k + Hk) * CS;
+  C* hcol = ext + (size_t)((low ? k + M : k - M) + Hk) * CS;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int l = j0 + i;
+    const int widx = low ? (l << logM) : ((MN - (l << logM)) & (MN - 1));
+    const C hv = cmul(v[i], tw<R>(A, widx));
+    mcol[l] = v[i];
+    hcol[l] = hv;
+    if (l < E - 1) {
+      mcol[l + N] = v[i];
+      hcol[l + N] = hv;
+    }
+  }
+}
+
+// ----------------------------------------------------------- operator gathers
+
+// Forward rows of output block r: out[i] = (H p)_r[k, j0 + i] over tx blocks t, paths of (r, t).
+template <typename R, int E>
+__device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
+                                           const int* cnt, const FrameArgs& A, int r, int k, int j0,
+                                           typename Cx<R>::C (&out)[E]) {
+  using C = typename Cx<R>::C;
+  const int M = A.M, N = A.N, CS = N + E - 1, Hk = M >> 1;
+  C accA[E], accB[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);
+  const C* colk = ext + (size_t)(k + Hk) * CS;
+  for (int t = 0; t < A.ntx; ++t) {
+    const C* src = colk + (size_t)t * blk;
+    const int li = r * A.ntx + t;
+    const PathRecT<R>* pl = paths + (size_t)li * A.p_max;
+    const int P = cnt[li];
+#pragma unroll 2
+    for (int p = 0; p < P; ++p) {
+      const PathRecT<R> rec = pl[p];
+      const C D = cmul(rec.hf, tab<R>(A, (rec.dl + (N >> 1)) * M + k));
+      const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
+      const C* a = src + ((j0 - rec.dl) & (N - 1)) - rec.dk * CS;  // column k - dk, first row (j0 - dl) mod N
+#pragma unroll
+      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < E; ++i) out[i] = Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
+}
+
+// Adjoint rows of output block t: out[i] = (H^H u)_t[k, j0 + i] over rx blocks r, paths of (r, t).
+template <typename R, int E>
+__device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
+                                           const int* cnt, const FrameArgs& A, int t, int k, int j0,
+                                           typename Cx<R>::C (&out)[E]) {
+  using C = typename Cx<R>::C;
+  const int M = A.M, N = A.N, CS = N + E - 1, Hk = M >> 1;
+  C accA[E], accB[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);
+  const C* colk = ext + (size_t)(k + Hk) * CS;
+  for (int r = 0; r < A.nrx; ++r) {
+    const C* src = colk + (size_t)r * blk;
+    const int li = r * A.ntx + t;
+    const PathRecT<R>* pl = paths + (size_t)li * A.p_max;
+    const int P = cnt[li];
+#pragma unroll 2
+    for (int p = 0; p < P; ++p) {
+      const PathRecT<R> rec = pl[p];
+      const C D = conjf2(cmul(rec.h, tab<R>(A, (rec.dl + (N >> 1)) * M + k)));
+      const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
+      const C* a = src + ((j0 + rec.dl) & (N - 1)) + rec.dk * CS;  // column k + dk, first row (j0 + dl) mod N
+#pragma unroll
+      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < E; ++i) out[i] = Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
+}
+
+// ------------------------------------------------------------ read-off + compaction
+
+// Read the effective channel off a Zak-transformed pilot grid X (DIF output, rows in
+// bit-reversed order) and compact the taps with |h_eff| > theta (Eq. heff_hadamard,
+// Eq. heff_thres) into out[0, P) in ascending q, keeping the p_max largest when more pass
+// (ties to the lower q).  Returns P; sets `trunc`.  Every thread owns q in
+// [tid*EQ, tid*EQ + EQ), EQ = MN/T.  When gout is set the list is also stored as list li.
+template <typename R, int EQ>
+__device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const FrameArgs& A, R theta,
+                                               PathRecT<R>* out, SharedHdr* S, const PathIO* gout, int li,
+                                               int& trunc) {
+  using C = typename Cx<R>::C;
+  using Key = typename Cx<R>::Key;
+  const int M = A.M, N = A.N, logM = A.logM, MN = M * N, tid = threadIdx.x;
+  const R scale = (R)A.inv_sqrtN / (R)A.a_pilot;
+  const R th2 = theta * theta;
+  C hv[EQ];
+  Key mb[EQ];
+  short dks[EQ], dls[EQ];
+  uint32_t pass = 0;
+#pragma unroll
+  for (int i = 0; i < EQ; ++i) {
+    const int q = tid * EQ + i;
+    const int k = q & (M - 1), l = q >> logM;
+    const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
+    const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+    const C Y = X[(size_t)bitrev(l, A.logN) * M + k];
+    const C h = cscale(cmul(Y, tw<R>(A, (size_t)((-A.K0 * dl) & (MN - 1)))), scale);
+    const R m2 = h.x * h.x + h.y * h.y;
+    const bool region = (A.pilot_mode == ZOTFS_PILOT_SEPARATE) || (dk >= 0 && dk <= A.guard);
+    hv[i] = h;
+    mb[i] = Cx<R>::key(m2);
+    dks[i] = (short)dk;
+    dls[i] = (short)dl;
+    if (region && m2 > th2) pass |= 1u << i;
+  }
+  int total;
+  int base = block_exclusive_scan(__popc(pass), S->scan, total);
+  uint32_t keep = pass;
+  trunc = 0;
+  if (total > A.p_max) {
+    trunc = 1;
+    const int K = A.p_max;
+    Key lo = 0, hi = Cx<R>::key_inf();  // bit patterns of non-negative values are ordered
+    while (lo < hi) {
+      const Key mid = lo + ((hi - lo + 1) >> 1);
+      int c = 0;
+#pragma unroll
+      for (int i = 0; i < EQ; ++i)
+        if (((pass >> i) & 1u) && mb[i] >= mid) ++c;
+      c = block_sum_i(c, S->scan);
+      if (c >= K) lo = mid; else hi = mid - 1;
+    }
+    const Key vK = lo;  // the K-th largest |h|^2 among the passing taps
+    int gt = 0;
+    uint32_t eq = 0;
+#pragma unroll
+    for (int i = 0; i < EQ; ++i) {
+      if ((pass >> i) & 1u) {
+        if (mb[i] > vK) ++gt;
+        else if (mb[i] == vK) eq |= 1u << i;
+      }
+    }
+    const int n_gt = block_sum_i(gt, S->scan);
+    const int need = K - n_gt;  // ties at vK kept in ascending q
+    int eq_total;
+    int eq_base = block_exclusive_scan(__popc(eq), S->scan, eq_total);
+    keep = 0;
+#pragma unroll
+    for (int i = 0; i < EQ; ++i) {
+      if ((pass >> i) & 1u) {
+        if (mb[i] > vK) keep |= 1u << i;
+        else if (mb[i] == vK) {
+          if (eq_base < need) keep |= 1u << i;
+          ++eq_base;
+        }
+      }
+    }
+    base = block_exclusive_scan(__popc(keep), S->scan, total);
+  }
+  int pos = base;
+#pragma unroll
+  for (int i = 0; i < EQ; ++i) {
+    if ((keep >> i) & 1u) {
+      PathRecT<R> rec;
+      rec.h = hv[i];
+      rec.dk = dks[i];
+      rec.dl = dls[i];
+      rec.hf = cmul(hv[i], tw<R>(A, (size_t)((-dls[i] * dks[i]) & (MN - 1))));
+      rec.pad0 = rec.pad1 = 0;
+      out[pos] = rec;
+      if (gout) {
+        const size_t g = (size_t)li * A.p_max + pos;
+        gout->dk[g] = (int16_t)dks[i];
+        gout->dl[g] = (int16_t)dls[i];
+        store_complex(gout->h, g, gout->tap_dtype, hv[i]);
+      }
+      ++pos;
+    }
+  }
+  if (gout && threadIdx.x == 0) {
+    gout->count[li] = total;
+    if (gout->status) gout->status[li] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Load a caller-provided path list; out-of-range entries are zeroed and flagged.
+template <typename R>
+__device__ __forceinline__ int load_paths(const FrameArgs& A, const PathIO& gin, int li, PathRecT<R>* out,
+                                          int& bad) {
+  using C = typename Cx<R>::C;
+  const int M = A.M, N = A.N, MN = M * N;
+  int P = gin.count[li];
+  bad = 0;
+  if (P < 0 || P > A.p_max) {
+    bad = 1;
+    P = P < 0 ? 0 : A.p_max;
+  }
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const size_t g = (size_t)li * A.p_max + p;
+    int dk = gin.dk[g], dl = gin.dl[g];
+    C h = load_complex<C>(gin.h, g, gin.tap_dtype);
+    if (dk < -(M >> 1) || dk >= (M >> 1) || dl < -(N >> 1) || dl >= (N >> 1)) {
+      bad = 1;
+      dk = 0;
+      dl = 0;
+      h = Cx<R>::make(0, 0);
+    }
+    PathRecT<R> rec;
+    rec.h = h;
+    rec.dk = dk;
+    rec.dl = dl;
+    rec.hf = cmul(h, tw<R>(A, (size_t)((-dl * dk) & (MN - 1))));
+    rec.pad0 = rec.pad1 = 0;
+    out[p] = rec;
+  }
+  bad = __syncthreads_or(bad);
+  return P;
+}
+
+// ------------------------------------------------------------------------ demap
+
+// Max-log LLRs of one sqrt(Q)-PAM axis with Gray labels (I or Q part of square QAM):
+// bit j < hb of the axis label (MSB first).  Unused outputs are left at 0.
+template <typename R>
+__device__ __forceinline__ void pam_llr(R x, int hb, R d, R inv_lam, R& o0, R& o1, R& o2) {
+  const int m = 1 << hb;
+  const R inf = (R)INFINITY;
+  R mn0a = inf, mn0b = inf, mn0c = inf, mn1a = inf, mn1b = inf, mn1c = inf;
+  for (int i = 0; i < m; ++i) {
+    const R a = (R)(2 * i - (m - 1)) * d;
+    const R di = (x - a) * (x - a);
+    const int g = i ^ (i >> 1);
+    const int b0 = (g >> (hb - 1)) & 1;
+    const int b1 = hb > 1 ? (g >> (hb - 2)) & 1 : 0;
+    const int b2 = hb > 2 ? g & 1 : 0;
+    if (b0) mn1a = fmin(mn1a, di); else mn0a = fmin(mn0a, di);
+    if (b1) mn1b = fmin(mn1b, di); else mn0b = fmin(mn0b, di);
+    if (b2) mn1c = fmin(mn1c, di); else mn0c = fmin(mn0c, di);
+  }
+  o0 = (mn1a - mn0a) * inv_lam;
+  o1 = hb > 1 ? (mn1b - mn0b) * inv_lam : (R)0;
+  o2 = hb > 2 ? (mn1c - mn0c) * inv_lam : (R)0;
+}
+
+// Max-log LLRs of one Gray square-QAM symbol: l[0..bps) = I-axis bits then Q-axis bits
+// (output as float); returns the hard label, bit j set when LLR j < 0 in precision R.
+template <typename R>
+__device__ __forceinline__ int qam_llr(typename Cx<R>::C x, int bps, R d, R inv_lam, float (&l)[6]) {
+  const int hb = bps >> 1;
+  R i0, i1, i2, q0, q1, q2;
+  pam_llr<R>(x.x, hb, d, inv_lam, i0, i1, i2);
+  pam_llr<R>(x.y, hb, d, inv_lam, q0, q1, q2);
+  R lr[6];
+  if (hb == 1) {
+    lr[0] = i0; lr[1] = q0; lr[2] = lr[3] = lr[4] = lr[5] = (R)0;
+  } else if (hb == 2) {
+    lr[0] = i0; lr[1] = i1; lr[2] = q0; lr[3] = q1; lr[4] = lr[5] = (R)0;
+  } else {
+    lr[0] = i0; lr[1] = i1; lr[2] = i2; lr[3] = q0; lr[4] = q1; lr[5] = q2;
+  }
+  int hard = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    l[j] = (float)lr[j];
+    if (j < bps) hard |= (lr[j] < (R)0 ? 1 : 0) << (bps - 1 - j);
+  }
+  return hard;
+}
+
+}  // namespace zotfs

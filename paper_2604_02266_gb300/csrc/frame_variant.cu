@@ -1,0 +1,94 @@
+// One instantiation of the frame kernel, selected by ZOTFS_VARIANT at compile time so the
+// variants build in parallel.  The table in frame_table.cu lists them.
+#include "frame_kernel.cuh"
+
+#ifndef ZOTFS_VARIANT
+#error "compile with -DZOTFS_VARIANT=<index>"
+#endif
+
+#if ZOTFS_VARIANT == 0
+#define V_E 8
+#define V_NB 1
+#define V_TMAX 256
+#define V_MINB 2
+#elif ZOTFS_VARIANT == 1
+#define V_E 8
+#define V_NB 1
+#define V_TMAX 512
+#define V_MINB 1
+#elif ZOTFS_VARIANT == 2
+#define V_E 4
+#define V_NB 1
+#define V_TMAX 512
+#define V_MINB 1
+#elif ZOTFS_VARIANT == 3
+#define V_E 16
+#define V_NB 1
+#define V_TMAX 256
+#define V_MINB 1
+#elif ZOTFS_VARIANT == 4
+#define V_E 4
+#define V_NB 2
+#define V_TMAX 512
+#define V_MINB 1
+#elif ZOTFS_VARIANT == 5
+#define V_E 2
+#define V_NB 4
+#define V_TMAX 512
+#define V_MINB 1
+#elif ZOTFS_VARIANT == 6
+#define V_E 8
+#define V_NB 1
+#define V_TMAX 256
+#define V_MINB 1
+#define V_R double
+#elif ZOTFS_VARIANT == 7
+#define V_E 4
+#define V_NB 2
+#define V_TMAX 256
+#define V_MINB 1
+#define V_R double
+#else
+#error "unknown ZOTFS_VARIANT"
+#endif
+
+#ifndef V_R
+#define V_R float
+#endif
+
+#define ZCAT2(a, b) a##b
+#define ZCAT(a, b) ZCAT2(a, b)
+#define VFUN(name) ZCAT(ZCAT(frame_v, ZOTFS_VARIANT), name)
+
+namespace zotfs {
+
+using KernT = void (*)(const FrameArgs, int);
+static KernT kern() { return frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB>; }
+
+void VFUN(_info)(int& E, int& NB, int& TMAX, int& real_bytes) {
+  E = V_E;
+  NB = V_NB;
+  TMAX = V_TMAX;
+  real_bytes = (int)sizeof(V_R);
+}
+
+cudaError_t VFUN(_launch)(const FrameArgs& A, int radix, int grid, int T, size_t smem, cudaStream_t stream) {
+  static int configured_smem[64] = {0};  // per device: the max dynamic smem already granted
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && configured_smem[dev] < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_smem[dev] = (int)smem;
+  }
+  frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB><<<grid, T, smem, stream>>>(A, radix);
+  return cudaGetLastError();
+}
+
+cudaError_t VFUN(_occupancy)(int T, size_t smem, int& blocks) {
+  cudaError_t e = cudaFuncSetAttribute(kern(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern(), T, smem);
+}
+
+}  // namespace zotfs

@@ -1,0 +1,69 @@
+// Host-side internals shared by the zotfs translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/zotfs.h"
+#include "frame_engine.cuh"
+
+struct zotfs_plan_s {
+  int M, N, logM, logN, nrx, ntx, qam, bps;
+  zotfs_pulse pulse;
+  zotfs_options opt;
+  zotfs_tuning tune;
+  int device, sm_count;
+  float2* d_W;    // W[t] = exp(j 2 pi t / MN), FP32
+  float2* d_Tab;  // Tab[(dl + N/2) M + k] = W[(dl k) mod MN], FP32
+  double2* d_W64;   // the same tables in FP64 (FP64 plans)
+  double2* d_Tab64;
+  int* d_counters;
+  int counter_next;
+  // plain-form scratch (one frame): y_dd, b/x/c/p/t/a vectors, scalars, paths
+  void* d_plain;
+  size_t plain_bytes;
+};
+
+namespace zotfs {
+
+using PathRec = PathRecT<float>;
+
+void set_error(const std::string& msg);
+zotfs_status cuda_fail(cudaError_t e, const char* what);
+int ilog2(int v);
+bool is_pow2(int v);
+
+// Fill the constant parts of FrameArgs from a plan.
+void fill_plan_args(const zotfs_plan_s* plan, FrameArgs& A);
+
+// Choose the frame-kernel configuration for a shape; returns false if no SMEM-resident
+// variant fits (the caller then reports ZOTFS_EUNSUPPORTED or uses the big-frame path).
+struct FrameCfg {
+  int E, NB, T;   // template rows/thread, blocks, threads per CTA
+  int variant;    // index into the instantiation table
+  size_t smem;
+};
+bool choose_frame_cfg(int M, int N, int nrx, int ntx, int p_max, int threads_override, FrameCfg& cfg,
+                      int real_bytes = 4);
+
+// Launch the persistent frame kernel (counter reset included).  n_frames > 0.
+zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameArgs& A, int radix,
+                                 int ctas_per_sm, cudaStream_t stream);
+
+// Variant table implemented in frame_variants.cu
+int frame_variant_count();
+bool frame_variant_info(int v, int& E, int& NB, int& TMAX, int& real_bytes);
+cudaError_t frame_variant_launch(int v, const FrameArgs& A, int radix, int grid, int T, size_t smem,
+                                 cudaStream_t stream);
+cudaError_t frame_variant_occupancy(int v, int T, size_t smem, int& blocks);
+
+// Plain form (plain.cu)
+size_t plain_scratch_bytes(int M, int N, int nrx, int ntx, int p_max);
+zotfs_status run_plain(zotfs_plan_s* plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,
+                       const float* theta, int iters, const zotfs_paths* paths, float* x_hat, float* llr,
+                       uint8_t* bits, int32_t* status, int n_frames, cudaStream_t stream);
+
+extern thread_local int g_launches;
+
+}  // namespace zotfs
