@@ -82,6 +82,7 @@ SIGNATURES = {
     "zotfs_demap": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "zotfs_rx": (_I, [_P, _P, _P, _P, _P, _I, C.POINTER(zotfs_paths), _P, _P, _P, _P, _I, _P]),
     "zotfs_rx_plain": (_I, [_P, _P, _P, _P, _P, _I, C.POINTER(zotfs_paths), _P, _P, _P, _P, _I, _P]),
+    "zotfs_equalize_static": (_I, [_I, _I, _I, _I, C.POINTER(zotfs_paths), _P, _P, _I, _P, _P, _I, _P]),
     "zotfs_batch_create": (_I, [C.POINTER(zotfs_frame_desc), _I, C.POINTER(zotfs_batch_opts), C.POINTER(_P)]),
     "zotfs_rx_batch": (_I, [_P, _P, _P]),
     "zotfs_batch_destroy": (_I, [_P]),
@@ -137,6 +138,7 @@ zotfs_equalize = _mk("zotfs_equalize")
 zotfs_demap = _mk("zotfs_demap")
 zotfs_rx = _mk("zotfs_rx")
 zotfs_rx_plain = _mk("zotfs_rx_plain")
+zotfs_equalize_static = _mk("zotfs_equalize_static")
 zotfs_batch_create = _mk("zotfs_batch_create")
 zotfs_rx_batch = _mk("zotfs_rx_batch")
 zotfs_batch_destroy = _mk("zotfs_batch_destroy")

@@ -5,6 +5,7 @@
 // for the fused kernels.  Its operator kernel evaluates the paper's index maps
 // (Eq. map_chMatDD_col, Eq. herm_mapping) and phase literally, with explicit wraps.
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -372,3 +373,197 @@ zotfs_status run_plain(zotfs_plan_s* plan, const void* y_pilot_td, const void* y
 }
 
 }  // namespace zotfs
+
+// ------------------------------------------------------------------------------------
+// Equalisation without any allocation: the plain-form CGA with its scratch in a fixed
+// array that the library image carries, for callers that may not allocate device memory
+// once they are running (see zotfs_equalize_static in include/zotfs.h).
+// ------------------------------------------------------------------------------------
+
+namespace zotfs {
+namespace {
+
+constexpr int kStaticMaxGrid = 4096;  // M * N
+constexpr int kStaticMaxAnt = 4;      // n_rx, n_tx
+constexpr int kStaticMaxPaths = 64;   // p_max
+constexpr size_t kStaticBytes = 768 * 1024;
+
+// The scratch every zotfs_equalize_static call uses, on every device that loads the library.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {nullptr};  // device address of g_static_scratch per device
+
+struct StaticLayout {
+  size_t W, paths, counts, t, x, c, p, a, scal, flags, total;
+};
+
+StaticLayout static_layout(int MN, int nrx, int ntx, int p_max) {
+  StaticLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  L.W = take((size_t)MN * sizeof(float2));
+  L.paths = take((size_t)nrx * ntx * p_max * sizeof(PathRec));
+  L.counts = take((size_t)nrx * ntx * sizeof(int));
+  L.t = take((size_t)nrx * MN * sizeof(float2));
+  L.x = take((size_t)ntx * MN * sizeof(float2));
+  L.c = take((size_t)ntx * MN * sizeof(float2));
+  L.p = take((size_t)ntx * MN * sizeof(float2));
+  L.a = take((size_t)ntx * MN * sizeof(float2));
+  L.scal = take(8 * sizeof(double));
+  L.flags = take(4 * sizeof(int));
+  L.total = off;
+  return L;
+}
+
+// W[t] = exp(j 2 pi t / MN) evaluated on the device (sincospi in FP64, rounded to FP32).
+__global__ void static_twiddle_kernel(float2* W, int MN) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= MN) return;
+  double s, c;
+  sincospi(2.0 * (double)t / (double)MN, &s, &c);
+  W[t] = make_float2((float)c, (float)s);
+}
+
+// Caller path lists -> path records (h, dk, dl) the plain operator kernel reads; entries
+// outside the centred offset range are zeroed.
+__global__ void static_paths_kernel(const int32_t* count, const int16_t* dk, const int16_t* dl, const float2* h,
+                                    int nl, int p_max, int M, int N, PathRec* out, int* counts, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nl * p_max) return;
+  const int li = i / p_max, p = i - li * p_max;
+  int P = count[li];
+  if (P < 0 || P > p_max) {
+    if (p == 0) flags[2] = 1;
+    P = P < 0 ? 0 : p_max;
+  }
+  if (p == 0) counts[li] = P;
+  if (p >= P) return;
+  PathRec r;
+  r.dk = dk[i];
+  r.dl = dl[i];
+  r.h = h[i];
+  if (r.dk < -(M / 2) || r.dk >= M / 2 || r.dl < -(N / 2) || r.dl >= N / 2) {
+    r.dk = r.dl = 0;
+    r.h = make_float2(0.f, 0.f);
+    flags[2] = 1;
+  }
+  r.hf = r.h;
+  r.pad0 = r.pad1 = 0;
+  out[i] = r;
+}
+
+__global__ void static_status_kernel(const int* flags, int32_t* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    *status = flags[1] ? ZOTFS_ENONFINITE : (flags[2] ? ZOTFS_EINVAL : ZOTFS_OK);
+}
+
+}  // namespace
+}  // namespace zotfs
+
+extern "C" zotfs_status zotfs_equalize_static(int M, int N, int n_rx, int n_tx, const zotfs_paths* paths,
+                                              const float* y_dd, const float* noise_var, int iters, float* x_hat,
+                                              int32_t* status, int n_frames, zotfs_stream stream) {
+  using namespace zotfs;
+  g_launches = 0;
+  if (!is_pow2(M) || M < 16 || M > 256 || !is_pow2(N) || N < 8 || N > 64) {
+    set_error("zotfs_equalize_static: M, N must be powers of two, 16 <= M <= 256, 8 <= N <= 64");
+    return ZOTFS_EINVAL;
+  }
+  if (M * N > kStaticMaxGrid || n_rx < 1 || n_tx < 1 || n_rx > kStaticMaxAnt || n_tx > kStaticMaxAnt) {
+    set_error("zotfs_equalize_static: the fixed scratch holds M*N <= 4096 and at most 4 x 4 antennas");
+    return ZOTFS_EUNSUPPORTED;
+  }
+  if (!paths || !paths->count || !paths->dk || !paths->dl || !paths->h) {
+    set_error("zotfs_equalize_static: NULL path list");
+    return ZOTFS_EINVAL;
+  }
+  if (paths->tap_dtype != ZOTFS_C64 || paths->p_max < 1 || paths->p_max > kStaticMaxPaths) {
+    set_error("zotfs_equalize_static: path taps must be ZOTFS_C64 with 1 <= p_max <= 64");
+    return paths->p_max > kStaticMaxPaths ? ZOTFS_EUNSUPPORTED : ZOTFS_EINVAL;
+  }
+  if (n_frames < 0 || iters < 0) {
+    set_error("zotfs_equalize_static: n_frames and iters must be >= 0");
+    return ZOTFS_EINVAL;
+  }
+  if (n_frames == 0) return ZOTFS_OK;
+  if (!y_dd || !noise_var || !x_hat) {
+    set_error("zotfs_equalize_static: NULL buffer");
+    return ZOTFS_EINVAL;
+  }
+  const int MN = M * N, nl = n_rx * n_tx, p_max = paths->p_max;
+  const StaticLayout L = static_layout(MN, n_rx, n_tx, p_max);
+  if (L.total > kStaticBytes) {
+    set_error("zotfs_equalize_static: problem larger than the fixed scratch");
+    return ZOTFS_EUNSUPPORTED;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) {
+    set_error("zotfs_equalize_static: device index out of range");
+    return ZOTFS_EUNSUPPORTED;
+  }
+  char* base;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+      g_static_ptr[dev] = ptr;
+    }
+    base = static_cast<char*>(g_static_ptr[dev]);
+  }
+  float2* W = reinterpret_cast<float2*>(base + L.W);
+  PathRec* pl = reinterpret_cast<PathRec*>(base + L.paths);
+  int* counts = reinterpret_cast<int*>(base + L.counts);
+  float2* tv = reinterpret_cast<float2*>(base + L.t);
+  float2* xv = reinterpret_cast<float2*>(base + L.x);
+  float2* cv = reinterpret_cast<float2*>(base + L.c);
+  float2* pv = reinterpret_cast<float2*>(base + L.p);
+  float2* av = reinterpret_cast<float2*>(base + L.a);
+  double* scal = reinterpret_cast<double*>(base + L.scal);
+  int* flags = reinterpret_cast<int*>(base + L.flags);
+  PlainGeo G{M, N, ilog2(M), ilog2(N), n_rx, n_tx, p_max, W};
+  const int nx = n_tx * MN;
+  static_twiddle_kernel<<<nblk(MN), kBlock, 0, stream>>>(W, MN);
+  ++g_launches;
+  for (int f = 0; f < n_frames; ++f) {
+    e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(flags)");
+    static_paths_kernel<<<nblk(nl * p_max), kBlock, 0, stream>>>(
+        paths->count + (size_t)f * nl, paths->dk + (size_t)f * nl * p_max, paths->dl + (size_t)f * nl * p_max,
+        reinterpret_cast<const float2*>(paths->h) + (size_t)f * nl * p_max, nl, p_max, M, N, pl, counts, flags);
+    const float2* yf = reinterpret_cast<const float2*>(y_dd) + (size_t)f * n_rx * MN;
+    const float* lamp = noise_var + f;
+    plain_apply_kernel<<<nblk(nx), kBlock, 0, stream>>>(G, pl, counts, yf, cv, 1, 0.f, nullptr);  // b -> c
+    plain_init_kernel<<<nblk(nx), kBlock, 0, stream>>>(cv, xv, cv, pv, nx);
+    plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiCn0, flags);
+    g_launches += 4;
+    for (int it = 0; it < iters; ++it) {
+      plain_apply_kernel<<<nblk(n_rx * MN), kBlock, 0, stream>>>(G, pl, counts, pv, tv, 0, 0.f, nullptr);
+      plain_apply_kernel<<<nblk(nx), kBlock, 0, stream>>>(G, pl, counts, tv, av, 1, 0.f, nullptr);
+      plain_addlam_kernel<<<nblk(nx), kBlock, 0, stream>>>(av, pv, lamp, nx);
+      plain_dot_kernel<<<1, 1024, 0, stream>>>(pv, av, nx, scal, kEpiAlpha, flags);
+      plain_xc_kernel<<<nblk(nx), kBlock, 0, stream>>>(xv, cv, pv, av, scal, nx);
+      plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiBeta, flags);
+      plain_p_kernel<<<nblk(nx), kBlock, 0, stream>>>(pv, cv, scal, nx);
+      g_launches += 7;
+    }
+    e = cudaMemcpyAsync(x_hat + (size_t)f * nx * 2, xv, (size_t)nx * sizeof(float2), cudaMemcpyDeviceToDevice,
+                        stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(x_hat)");
+    if (status) {
+      static_status_kernel<<<1, 32, 0, stream>>>(flags, status + f);
+      ++g_launches;
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "zotfs_equalize_static launch");
+  return ZOTFS_OK;
+}

@@ -133,7 +133,7 @@ def test_rx_noiseless_integer_channel_bit_exact():
     from paper_2604_02266_gb300 import C128, COMPUTE_FP64
     n_checked = 0
     for Q in (4, 16, 64):
-        M, N, F, iters = 32, 16, 4, 100
+        M, N, F, iters = 32, 16, 8, 100
         b = synth.fractional_batch(F, seed=88 + Q, M=M, N=N, Q=Q, snr_db=(60,), integer=True)
         plan = Plan(M, N, 1, 1, Q)
         out = _run(plan, b, iters, F)
