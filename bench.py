@@ -378,7 +378,7 @@ def impl_zotfs(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="zotfs", choices=["zotfs", "reference"])
     ap.add_argument("--threads", type=int, default=0, help="threads per frame (tuning)")
