@@ -30,6 +30,9 @@ struct Bucket {
   int ids_off = 0;
   float2* d_W = nullptr;
   float2* d_Tab = nullptr;
+  bool big = false;      // vectors too large for shared memory: the large-frame kernel
+  zotfs::BigCfg bigcfg{};
+  char* d_big = nullptr;  // its scratch slots (one per CTA of the bucket's grid)
 };
 
 }  // namespace
@@ -188,12 +191,15 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     B.ctas_per_sm = cps;
     if (!choose_frame_cfg(B.M, B.N, B.nrx, B.ntx, B.p_max, tpf, B.cfg) &&
         !(tpf > 0 && choose_frame_cfg(B.M, B.N, B.nrx, B.ntx, B.p_max, 0, B.cfg))) {
-      set_error("bucket " + std::to_string(B.M) + "x" + std::to_string(B.N) + " " + std::to_string(B.nrx) + "x" +
-                std::to_string(B.ntx) + ": no shared-memory-resident frame kernel for this shape");
-      st = ZOTFS_EUNSUPPORTED;
-      break;
+      if (!choose_big_cfg(B.M, B.N, B.nrx, B.ntx, B.p_max, B.bigcfg)) {
+        set_error("bucket " + std::to_string(B.M) + "x" + std::to_string(B.N) + " " + std::to_string(B.nrx) + "x" +
+                  std::to_string(B.ntx) + ": no kernel for this shape");
+        st = ZOTFS_EUNSUPPORTED;
+        break;
+      }
+      B.big = true;
     }
-    e = frame_variant_occupancy(B.cfg.variant, B.cfg.T, B.cfg.smem, occ[bi]);
+    e = B.big ? big_occupancy(B.bigcfg, occ[bi]) : frame_variant_occupancy(B.cfg.variant, B.cfg.T, B.cfg.smem, occ[bi]);
     if (e != cudaSuccess) {
       st = cuda_fail(e, "occupancy query");
       break;
@@ -241,6 +247,13 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     }
     B.d_W = it->second.first;
     B.d_Tab = it->second.second;
+    if (B.big) {
+      e = cudaMalloc(&B.d_big, B.bigcfg.slot_bytes * (size_t)B.grid);
+      if (e != cudaSuccess) {
+        st = e == cudaErrorMemoryAllocation ? ZOTFS_ENOMEM : cuda_fail(e, "large-frame scratch");
+        if (st == ZOTFS_ENOMEM) set_error("large-frame scratch allocation failed");
+      }
+    }
   }
   // streams and fork/join events
   const size_t ns = b->buckets.size();
@@ -317,7 +330,8 @@ zotfs_status zotfs_rx_batch(zotfs_batch b, int32_t* status, zotfs_stream stream)
     A.status = status;
     A.descs = b->d_descs;
     A.frame_ids = b->d_ids + B.ids_off;
-    e = frame_variant_launch(B.cfg.variant, A, B.radix, B.grid, B.cfg.T, B.cfg.smem, s);
+    e = B.big ? big_launch(B.bigcfg, A, B.radix, B.grid, B.d_big, s)
+              : frame_variant_launch(B.cfg.variant, A, B.radix, B.grid, B.cfg.T, B.cfg.smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "bucket kernel launch");
     ++g_launches;
     e = cudaEventRecord(b->events[1 + bi], s);
@@ -332,6 +346,8 @@ zotfs_status zotfs_batch_destroy(zotfs_batch b) {
   for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t ev : b->events) cudaEventDestroy(ev);
+  for (Bucket& B : b->buckets)
+    if (B.d_big) cudaFree(B.d_big);
   for (auto& kv : b->tables) {
     cudaFree(kv.second.first);
     cudaFree(kv.second.second);

@@ -117,16 +117,30 @@ static zotfs_status check_paths(const zotfs_plan_s* plan, const zotfs_paths* pat
   return ZOTFS_OK;
 }
 
-static zotfs_status frame_cfg_or_fail(const zotfs_plan_s* plan, int nrx, int ntx, FrameCfg& cfg) {
-  if (!choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, cfg,
-                        real_bytes_of(plan))) {
-    set_error("no shared-memory-resident frame kernel for this shape/antenna count/tuning");
+static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 4 ? 4 : 2; }
+
+// Launch the shared-memory frame kernel when the shape fits one CTA, else the large-frame
+// kernel on the plan's scratch slots.
+static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream) {
+  FrameCfg cfg;
+  if (choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, cfg,
+                       real_bytes_of(plan)))
+    return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  BigCfg big;
+  if (real_bytes_of(plan) != 4 || !plan->d_big || !choose_big_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, big)) {
+    set_error("no kernel for this shape / antenna count / precision");
     return ZOTFS_EUNSUPPORTED;
   }
+  int* counter = plan->d_counters + (plan->counter_next++ & 63);
+  A.work_counter = counter;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work counter)");
+  int grid = plan->big_slots < A.n_frames ? plan->big_slots : A.n_frames;
+  e = big_launch(big, A, radix_of(plan), grid, plan->d_big, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "large-frame kernel launch");
+  ++g_launches;
   return ZOTFS_OK;
 }
-
-static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 4 ? 4 : 2; }
 
 }  // namespace zotfs
 
@@ -205,6 +219,20 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
   if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab64, sizeof(double2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(int) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_plain, p->plain_bytes);
+  {
+    FrameCfg fc;
+    BigCfg bc;
+    if (e == cudaSuccess && !choose_frame_cfg(M, N, n_rx, n_tx, 256, 0, fc, 4) &&
+        choose_big_cfg(M, N, n_rx, n_tx, 64, bc)) {
+      int occ = 0;
+      e = big_occupancy(bc, occ);
+      if (e == cudaSuccess) {
+        p->big_slots = p->sm_count * (occ > 0 ? occ : 1);
+        p->big_slot_bytes = bc.slot_bytes;
+        e = cudaMalloc(&p->d_big, bc.slot_bytes * (size_t)p->big_slots);
+      }
+    }
+  }
   if (e == cudaSuccess) e = cudaMemcpy(p->d_W, W.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_Tab, Tab.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_W64, W64.data(), sizeof(double2) * MN, cudaMemcpyHostToDevice);
@@ -230,6 +258,7 @@ zotfs_status zotfs_plan_destroy(zotfs_plan plan) {
   if (plan->d_Tab64) cudaFree(plan->d_Tab64);
   if (plan->d_counters) cudaFree(plan->d_counters);
   if (plan->d_plain) cudaFree(plan->d_plain);
+  if (plan->d_big) cudaFree(plan->d_big);
   delete plan;
   return ZOTFS_OK;
 }
@@ -300,9 +329,6 @@ zotfs_status zotfs_dzt(zotfs_plan plan, const void* y_td, float* y_dd, int n_gri
   if (n_grids == 0) return ZOTFS_OK;
   if (!y_td || !y_dd) return inval("NULL buffer");
   if (!aligned16(y_td)) return inval("y_td must be 16-byte aligned");
-  FrameCfg cfg;
-  zotfs_status s = frame_cfg_or_fail(plan, 1, 1, cfg);
-  if (s) return s;
   FrameArgs A;
   fill_plan_args(plan, A);
   A.nrx = A.ntx = 1;
@@ -310,7 +336,7 @@ zotfs_status zotfs_dzt(zotfs_plan plan, const void* y_td, float* y_dd, int n_gri
   A.n_frames = n_grids;
   A.y_data = y_td;
   A.u_out = y_dd;
-  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  return launch_any(plan, 1, 1, A, stream);
 }
 
 zotfs_status zotfs_estimate(zotfs_plan plan, const void* y_pilot_td, const float* theta, int n_frames,
@@ -324,9 +350,6 @@ zotfs_status zotfs_estimate(zotfs_plan plan, const void* y_pilot_td, const float
   if (!y_pilot_td || !theta) return inval("NULL buffer");
   if (!aligned16(y_pilot_td)) return inval("y_pilot_td must be 16-byte aligned");
   const bool emb = plan->opt.pilot_mode == ZOTFS_PILOT_EMBEDDED;
-  FrameCfg cfg;
-  s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
-  if (s) return s;
   FrameArgs A;
   fill_plan_args(plan, A);
   A.mode = kEstimate | kWritePaths;
@@ -339,7 +362,7 @@ zotfs_status zotfs_estimate(zotfs_plan plan, const void* y_pilot_td, const float
   A.pdk = paths->dk;
   A.pdl = paths->dl;
   A.ph = paths->h;
-  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  return launch_any(plan, plan->nrx, plan->ntx, A, stream);
 }
 
 zotfs_status zotfs_ss_apply(zotfs_plan plan, const zotfs_paths* paths, const float* v, float* u, int adjoint,
@@ -351,9 +374,6 @@ zotfs_status zotfs_ss_apply(zotfs_plan plan, const zotfs_paths* paths, const flo
   if (s) return s;
   if (n_frames == 0) return ZOTFS_OK;
   if (!v || !u) return inval("NULL buffer");
-  FrameCfg cfg;
-  s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
-  if (s) return s;
   FrameArgs A;
   fill_plan_args(plan, A);
   A.mode = kLoadPaths | kApply;
@@ -366,7 +386,7 @@ zotfs_status zotfs_ss_apply(zotfs_plan plan, const zotfs_paths* paths, const flo
   A.pdk = paths->dk;
   A.pdl = paths->dl;
   A.ph = paths->h;
-  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  return launch_any(plan, plan->nrx, plan->ntx, A, stream);
 }
 
 zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const zotfs_paths* paths,
@@ -382,9 +402,6 @@ zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const z
   if (y_is_dd && plan->opt.pilot_mode == ZOTFS_PILOT_EMBEDDED)
     return inval("embedded pilot: equalize takes the TD frame (the pilot is removed after the Zak transform)");
   if (!y_is_dd && !aligned16(y)) return inval("y must be 16-byte aligned");
-  FrameCfg cfg;
-  s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
-  if (s) return s;
   FrameArgs A;
   fill_plan_args(plan, A);
   A.mode = kLoadPaths | kCG | kWriteX;
@@ -399,7 +416,7 @@ zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const z
   A.pdk = paths->dk;
   A.pdl = paths->dl;
   A.ph = paths->h;
-  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  return launch_any(plan, plan->nrx, plan->ntx, A, stream);
 }
 
 zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise_var, float* llr, uint8_t* bits,
@@ -410,9 +427,6 @@ zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise
   if (n_frames == 0) return ZOTFS_OK;
   if (!x_hat || !noise_var) return inval("NULL buffer");
   if (!llr && !bits) return ZOTFS_OK;
-  FrameCfg cfg;
-  zotfs_status s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
-  if (s) return s;
   FrameArgs A;
   fill_plan_args(plan, A);
   A.mode = kLoadX | kDemap;
@@ -421,7 +435,7 @@ zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise
   A.noise_var = noise_var;
   A.llr = llr;
   A.bits = bits;
-  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  return launch_any(plan, plan->nrx, plan->ntx, A, stream);
 }
 
 zotfs_status zotfs_rx(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,
@@ -438,9 +452,6 @@ zotfs_status zotfs_rx(zotfs_plan plan, const void* y_pilot_td, const void* y_dat
     zotfs_status s = check_paths(plan, paths, true);
     if (s) return s;
   }
-  FrameCfg cfg;
-  zotfs_status s = frame_cfg_or_fail(plan, plan->nrx, plan->ntx, cfg);
-  if (s) return s;
   FrameArgs A;
   fill_plan_args(plan, A);
   A.mode = kEstimate | kCG | kDemap | (paths ? kWritePaths : 0) | (x_hat ? kWriteX : 0);
@@ -461,7 +472,7 @@ zotfs_status zotfs_rx(zotfs_plan plan, const void* y_pilot_td, const void* y_dat
     A.pdl = paths->dl;
     A.ph = paths->h;
   }
-  return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  return launch_any(plan, plan->nrx, plan->ntx, A, stream);
 }
 
 zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,

@@ -248,26 +248,29 @@ __device__ __forceinline__ int bitrev(int l, int logN) { return (int)(__brev((un
 // --------------------------------------------------------------- ext writing
 
 // Store the thread's E values of one block (column k, rows j0..j0+E-1) into ext, with the
-// quasi-periodic halo column and the periodic halo rows.
-template <typename R, int E>
+// quasi-periodic halo column and the periodic halo rows.  kRowMajor selects the global-memory
+// layout (element (A, r) at r * 2M + A + M/2) instead of the shared-memory column-major one.
+template <typename R, int E, bool kRowMajor = false>
 __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArgs& A, int k, int j0,
                                           const typename Cx<R>::C (&v)[E]) {
   using C = typename Cx<R>::C;
   const int M = A.M, N = A.N, CS = N + E - 1, Hk = M >> 1, logM = A.logM, MN = M * N;
+  const size_t rstep = kRowMajor ? (size_t)(2 * M) : 1;  // distance between consecutive rows
   // halo column: k < M/2 stores X_ext[k + M] = X[k] W_N[l]; k >= M/2 stores X_ext[k - M] = X[k] W_N[-l]
   const bool low = k < Hk;
-  C* mcol = ext + (size_t)(k + Hk) * CS;
-  C* hcol = ext + (size_t)((low ? k + M : k - M) + Hk) * CS;
+  const int mc = k + Hk, hc = (low ? k + M : k - M) + Hk;
+  C* mcol = ext + (kRowMajor ? (size_t)mc : (size_t)mc * CS);
+  C* hcol = ext + (kRowMajor ? (size_t)hc : (size_t)hc * CS);
 #pragma unroll
   for (int i = 0; i < E; ++i) {
     const int l = j0 + i;
     const int widx = low ? (l << logM) : ((MN - (l << logM)) & (MN - 1));
     const C hv = cmul(v[i], tw<R>(A, widx));
-    mcol[l] = v[i];
-    hcol[l] = hv;
+    mcol[l * rstep] = v[i];
+    hcol[l * rstep] = hv;
     if (l < E - 1) {
-      mcol[l + N] = v[i];
-      hcol[l + N] = hv;
+      mcol[(l + N) * rstep] = v[i];
+      hcol[(l + N) * rstep] = hv;
     }
   }
 }
@@ -275,12 +278,14 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
 // ----------------------------------------------------------- operator gathers
 
 // Forward rows of output block r: out[i] = (H p)_r[k, j0 + i] over tx blocks t, paths of (r, t).
-template <typename R, int E>
+template <typename R, int E, bool kRowMajor = false>
 __device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const int* cnt, const FrameArgs& A, int r, int k, int j0,
                                            typename Cx<R>::C (&out)[E]) {
   using C = typename Cx<R>::C;
-  const int M = A.M, N = A.N, CS = N + E - 1, Hk = M >> 1;
+  const int M = A.M, N = A.N, Hk = M >> 1;
+  const int CS = kRowMajor ? 1 : N + E - 1;        // column step
+  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;  // row step
   C accA[E], accB[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);
@@ -295,9 +300,10 @@ __device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t 
       const PathRecT<R> rec = pl[p];
       const C D = cmul(rec.hf, tab<R>(A, (rec.dl + (N >> 1)) * M + k));
       const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
-      const C* a = src + ((j0 - rec.dl) & (N - 1)) - rec.dk * CS;  // column k - dk, first row (j0 - dl) mod N
+      // column k - dk, first row (j0 - dl) mod N
+      const C* a = src + (size_t)((j0 - rec.dl) & (N - 1)) * RS - rec.dk * CS;
 #pragma unroll
-      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i]);
+      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i * RS]);
     }
   }
 #pragma unroll
@@ -305,12 +311,14 @@ __device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t 
 }
 
 // Adjoint rows of output block t: out[i] = (H^H u)_t[k, j0 + i] over rx blocks r, paths of (r, t).
-template <typename R, int E>
+template <typename R, int E, bool kRowMajor = false>
 __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const int* cnt, const FrameArgs& A, int t, int k, int j0,
                                            typename Cx<R>::C (&out)[E]) {
   using C = typename Cx<R>::C;
-  const int M = A.M, N = A.N, CS = N + E - 1, Hk = M >> 1;
+  const int M = A.M, N = A.N, Hk = M >> 1;
+  const int CS = kRowMajor ? 1 : N + E - 1;
+  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;
   C accA[E], accB[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);
@@ -325,9 +333,10 @@ __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t 
       const PathRecT<R> rec = pl[p];
       const C D = conjf2(cmul(rec.h, tab<R>(A, (rec.dl + (N >> 1)) * M + k)));
       const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
-      const C* a = src + ((j0 + rec.dl) & (N - 1)) + rec.dk * CS;  // column k + dk, first row (j0 + dl) mod N
+      // column k + dk, first row (j0 + dl) mod N
+      const C* a = src + (size_t)((j0 + rec.dl) & (N - 1)) * RS + rec.dk * CS;
 #pragma unroll
-      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i]);
+      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i * RS]);
     }
   }
 #pragma unroll

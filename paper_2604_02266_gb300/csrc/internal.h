@@ -23,6 +23,10 @@ struct zotfs_plan_s {
   // plain-form scratch (one frame): y_dd, b/x/c/p/t/a vectors, scalars, paths
   void* d_plain;
   size_t plain_bytes;
+  // large-frame kernel: one scratch slot per resident CTA (shapes that do not fit shared memory)
+  char* d_big;
+  size_t big_slot_bytes;
+  int big_slots;
 };
 
 namespace zotfs {
@@ -57,6 +61,16 @@ bool frame_variant_info(int v, int& E, int& NB, int& TMAX, int& real_bytes);
 cudaError_t frame_variant_launch(int v, const FrameArgs& A, int radix, int grid, int T, size_t smem,
                                  cudaStream_t stream);
 cudaError_t frame_variant_occupancy(int v, int T, size_t smem, int& blocks);
+
+// Large-frame kernel (big_variant.cu)
+struct BigCfg {
+  int T, EW;
+  size_t smem, slot_bytes;
+};
+bool choose_big_cfg(int M, int N, int nrx, int ntx, int p_max, BigCfg& cfg);
+cudaError_t big_launch(const BigCfg& cfg, const FrameArgs& A, int radix, int grid, char* scratch,
+                       cudaStream_t stream);
+cudaError_t big_occupancy(const BigCfg& cfg, int& blocks);
 
 // Plain form (plain.cu)
 size_t plain_scratch_bytes(int M, int N, int nrx, int ntx, int p_max);

@@ -1,0 +1,109 @@
+"""GPU parity of the large-frame kernel (vectors in per-CTA global scratch): grids and MIMO
+stacks whose CG vectors do not fit one CTA's shared memory, e.g. 4x4 at 128x64 (32768
+unknowns) and 256x64."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import zak, equalizer as eq
+from tests.gpu_util import TOL_LIN, TOL_LLR, TOL_X, dev, fill_paths, random_pathlist, rel_l2, to_dev
+from tests.test_gpu_rx import _check_frames, _run
+from tests.test_gpu_stages import _cg_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+def Plan(*a, **k):
+    from paper_2604_02266_gb300 import Plan as P
+    return P(*a, **k)
+
+
+@pytest.mark.parametrize("M,N", [(256, 64), (256, 32), (128, 64)])
+def test_dzt_large(M, N):
+    g = np.random.default_rng(M + N)
+    y = (g.standard_normal((3, M * N)) + 1j * g.standard_normal((3, M * N))).astype(np.complex64)
+    plan = Plan(M, N, 1, 1, 16)
+    Y = plan.dzt(to_dev(y)).cpu().numpy()
+    for i in range(3):
+        assert rel_l2(Y[i], zak.vec(zak.dzt(y[i].astype(complex), M, N))) < TOL_LIN
+
+
+@pytest.mark.parametrize("nrx,ntx,M,N", [(4, 4, 128, 64), (1, 1, 256, 64), (2, 2, 128, 64), (4, 4, 64, 32)])
+def test_ss_apply_large(nrx, ntx, M, N):
+    g = np.random.default_rng(nrx * M + N)
+    F = 2
+    plan = Plan(M, N, nrx, ntx, 16)
+    grids = [[[random_pathlist(g, M, N, 12) for _ in range(ntx)] for _ in range(nrx)] for _ in range(F)]
+    flat = [pl for fr in grids for row in fr for pl in row]
+    paths = fill_paths(plan.new_paths(F), flat, plan.p_max)
+    v = (g.standard_normal((F, ntx, M * N)) + 1j * g.standard_normal((F, ntx, M * N))).astype(np.complex64)
+    u = (g.standard_normal((F, nrx, M * N)) + 1j * g.standard_normal((F, nrx, M * N))).astype(np.complex64)
+    fwd = plan.ss_apply(paths, to_dev(v), F).cpu().numpy()
+    adj = plan.ss_apply(paths, to_dev(u), F, adjoint=True).cpu().numpy()
+    for f in range(F):
+        op = eq.StackedOperator(grids[f])
+        assert rel_l2(fwd[f].reshape(-1), op.forward(v[f].reshape(-1).astype(complex))) < TOL_LIN
+        assert rel_l2(adj[f].reshape(-1), op.adjoint(u[f].reshape(-1).astype(complex))) < TOL_LIN
+
+
+@pytest.mark.parametrize("nrx,ntx,M,N", [(1, 1, 128, 64), (1, 1, 256, 64), (2, 2, 128, 64)])
+def test_equalize_large(nrx, ntx, M, N):
+    F, iters = 2, 10
+    b, grids = _cg_case(M, N, F, 20, seed=5100 + M + nrx, nrx=nrx, ntx=ntx)
+    plan = Plan(M, N, nrx, ntx, 16)
+    flat = [pl for gr in grids for row in gr for pl in row]
+    paths = fill_paths(plan.new_paths(F), flat, plan.p_max)
+    x = plan.equalize(to_dev(b["y_data_td"]), paths, to_dev(b["noise_var"]), iters, F).cpu().numpy()
+    for f in range(F):
+        y_dd = np.concatenate([zak.vec(zak.dzt(b["y_data_td"][f, r].astype(complex), M, N)) for r in range(nrx)])
+        ref = eq.cga(grids[f], y_dd, float(b["noise_var"][f]), iters)
+        assert rel_l2(x[f].reshape(-1), ref) < TOL_X
+
+
+def test_rx_4x4_128x64_64qam():
+    """4x4 MIMO, 128x64, 64-QAM: the stacked 32768-unknown system, estimated path lists."""
+    M, N, nrx, ntx, Q, F, iters = 128, 64, 4, 4, 64, 2, 10
+    b = synth.fractional_batch(F, seed=7300, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx, snr_db=(25,))
+    plan = Plan(M, N, nrx, ntx, Q)
+    out = _run(plan, b, iters, F)
+    wx, wl, mm = _check_frames(b, out, range(F), M, N, nrx, ntx, Q, iters, plan.p_max)
+    assert wx < TOL_X and wl < TOL_LLR and mm == 0, (wx, wl, mm)
+
+
+def test_rx_batch_with_large_buckets():
+    """An uneven batch mixing shared-memory and large-frame buckets: each frame equals its
+    result alone."""
+    from paper_2604_02266_gb300 import Batch
+    shapes = [(128, 64, 1, 1, 16), (64, 32, 1, 1, 16), (128, 64, 2, 2, 16), (64, 64, 2, 2, 4), (32, 16, 2, 2, 64)]
+    frames, keep = [], []
+    for i in range(15):
+        M, N, nrx, ntx, Q = shapes[i % len(shapes)]
+        b = synth.fractional_batch(1, seed=8100 + i, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx, snr_db=(5 + 2 * i,))
+        bps = int(np.log2(Q))
+        o = {"x": torch.zeros(ntx, M * N, dtype=torch.complex64, device=dev()),
+             "bits": torch.zeros(ntx, M * N * bps // 8, dtype=torch.uint8, device=dev())}
+        frames.append(dict(M=M, N=N, n_rx=nrx, n_tx=ntx, qam=Q, iters=10, pilot_mode=0, guard=2, p_max=64,
+                           in_dtype=0, noise_var=float(b["noise_var"][0]), theta=float(b["theta"][0]),
+                           a_pilot=float(b["a_pilot"]), y_pilot=to_dev(b["y_pilot_td"][0]),
+                           y_data=to_dev(b["y_data_td"][0]), x_hat=o["x"], bits=o["bits"]))
+        keep.append((b, o))
+    batch = Batch(frames)
+    status = torch.full((len(frames),), -1, dtype=torch.int32, device=dev())
+    batch.run(status)
+    torch.cuda.synchronize()
+    assert set(status.cpu().numpy().tolist()) <= {0, 6}
+    for i, (b, o) in enumerate(keep):
+        M, N, nrx, ntx, Q = shapes[i % len(shapes)]
+        alone = _run(Plan(M, N, nrx, ntx, Q), b, 10, 1)
+        assert torch.equal(alone["x_hat"][0], o["x"]), i
+        assert torch.equal(alone["bits"][0], o["bits"]), i
