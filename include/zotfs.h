@@ -281,6 +281,76 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames,
 zotfs_status zotfs_rx_batch(zotfs_batch batch, int32_t* status, zotfs_stream stream);
 zotfs_status zotfs_batch_destroy(zotfs_batch batch);
 
+/* ------------------------------------------------------------------- serving ---- */
+
+/* A request loop on one GPU with continuous batching.  Frames of mixed shapes, antenna
+ * counts and QAM orders are submitted as they arrive (their received pilot and data frames
+ * already in device memory).  A scheduler thread owned by the server admits pending frames
+ * into "waves" whenever a wave slot is free and the device output arena has room for their
+ * results, and launches each wave's frames (grouped by shape) on the wave's own streams, so
+ * frames admitted while earlier waves run overlap with them on the device.  A frame's
+ * outputs -- hard bits, optionally LLRs, and its path lists -- stay resident in the arena
+ * until the caller releases it.  Not in the paper (which processes one packet at a time). */
+typedef struct zotfs_server_s* zotfs_server;
+
+typedef struct zotfs_server_opts {
+  int32_t p_max;            /* path-list capacity of every frame (1..256) */
+  int32_t max_wave_frames;  /* frames admitted per wave, 1..4096 */
+  int32_t waves_in_flight;  /* concurrent waves, 1..16 */
+  int32_t keep_llr;         /* also keep float32 LLRs per frame */
+  int64_t arena_bytes;      /* device bytes for admitted frames' outputs */
+  int32_t max_M, max_N, max_ant;  /* largest frame accepted (sizes the large-frame scratch) */
+} zotfs_server_opts;
+
+typedef struct zotfs_request {
+  int32_t M, N, n_rx, n_tx, qam, iters;
+  float noise_var, theta, a_pilot;  /* a_pilot <= 0: sqrt(MN) */
+  const void* y_pilot;              /* dev C64 pilots [t][r][MN], resident until completion */
+  const void* y_data;               /* dev C64 data [r][MN] */
+  uint64_t tag;                     /* caller's id, unique among frames not yet released */
+} zotfs_request;
+
+typedef struct zotfs_completion {
+  uint64_t tag;
+  int32_t status;                   /* zotfs_status of the frame */
+  int32_t n_lists;                  /* n_rx * n_tx */
+  int64_t arrival_ns, admit_ns, done_ns;  /* steady-clock times: submit, wave launch, observed done */
+  const uint8_t* bits;              /* dev [n_tx][MN*bps/8], valid until zotfs_server_release */
+  const float* llr;                 /* dev [n_tx][MN][bps] or NULL */
+  const int32_t* path_count;        /* dev [n_lists] */
+  const int16_t* path_dk;           /* dev [n_lists][p_max] */
+  const int16_t* path_dl;
+  const float* path_h;              /* dev [n_lists][p_max] C64 */
+} zotfs_completion;
+
+typedef struct zotfs_server_stats {
+  int64_t submitted, admitted, completed, released, pending, waves;
+  int64_t arena_bytes, arena_in_use, arena_high_water;
+  int64_t rejected_too_large;       /* requests whose outputs can never fit the arena */
+} zotfs_server_stats;
+
+/* Create a server on the current device.  Allocates the arena, the per-wave streams, events,
+ * descriptor buffers and large-frame scratch, and the root-of-unity tables of every shape
+ * up to (max_M, max_N).  Starts the scheduler thread. */
+zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* out);
+/* Queue n requests (thread-safe, never blocks on the GPU; copies the request structs). */
+zotfs_status zotfs_server_submit(zotfs_server server, const zotfs_request* reqs, int n);
+/* Load generator: submit reqs[i] at time arrival_s[i] (seconds, non-decreasing) after the
+ * call starts, spinning on the steady clock; returns once all are submitted. */
+zotfs_status zotfs_server_replay(zotfs_server server, const zotfs_request* reqs, const double* arrival_s, int n);
+/* Copy up to max completed frames (oldest first) into out; returns how many. */
+int zotfs_server_poll(zotfs_server server, zotfs_completion* out, int max);
+/* Copy a completed, unreleased frame's outputs to host memory (synchronous; any destination
+ * may be NULL): bits [n_tx][MN*bps/8], llr [n_tx][MN][bps] (if kept), and the path lists
+ * count [n_lists], dk/dl [n_lists][p_max], h [n_lists][p_max] C64. */
+zotfs_status zotfs_server_read(zotfs_server server, uint64_t tag, uint8_t* bits, float* llr, int32_t* path_count,
+                               int16_t* path_dk, int16_t* path_dl, float* path_h);
+/* Return a completed frame's outputs to the arena. */
+zotfs_status zotfs_server_release(zotfs_server server, uint64_t tag);
+zotfs_status zotfs_server_get_stats(zotfs_server server, zotfs_server_stats* stats);
+/* Stop admitting, wait for in-flight waves, stop the scheduler, free everything. */
+zotfs_status zotfs_server_destroy(zotfs_server server);
+
 /* ----------------------------------------------------------------- misc ------------ */
 
 /* Thread-local message for the most recent failure in this thread ("" if none). */

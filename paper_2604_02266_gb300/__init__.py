@@ -25,7 +25,7 @@ from ._zotfs import (ZotfsError, OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEO
                      ENONFINITE, STATUS_NAMES, C64, C32_F16, C32_BF16, C128, COMPUTE_FP32, COMPUTE_FP64,
                      PILOT_SEPARATE, PILOT_EMBEDDED, PULSE_SINC, PULSE_RECT)
 
-__all__ = ["Plan", "Paths", "Batch", "ZotfsError", "library_path", "launch_count"]
+__all__ = ["Plan", "Paths", "Batch", "Server", "ZotfsError", "library_path", "launch_count"]
 
 _DTYPES = {C64: torch.complex64, C32_F16: torch.float16, C32_BF16: torch.bfloat16, C128: torch.complex128}
 
@@ -259,3 +259,72 @@ class Batch:
         _need_cuda(status)
         Z.check(Z.zotfs_rx_batch(self._h, _p(status), _s(stream)))
         return status
+
+
+class Server:
+    """Continuous-batching request loop (zotfs_server_*).  Requests reference device tensors
+    (pilot and data TD frames, complex64) that must stay alive until their completion."""
+
+    def __init__(self, p_max=64, max_wave_frames=256, waves_in_flight=4, keep_llr=False, arena_bytes=1 << 30,
+                 max_M=256, max_N=64, max_ant=4):
+        o = Z.zotfs_server_opts(p_max, max_wave_frames, waves_in_flight, int(bool(keep_llr)), arena_bytes, max_M,
+                                max_N, max_ant)
+        h = C.c_void_p()
+        Z.check(Z.zotfs_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self.p_max = p_max
+        self._keep = {}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            Z.zotfs_server_destroy(h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def request(tag, y_pilot, y_data, M, N, n_rx, n_tx, qam, iters, noise_var, theta, a_pilot=0.0):
+        _need_cuda(y_pilot, y_data)
+        return Z.zotfs_request(M, N, n_rx, n_tx, qam, iters, noise_var, theta, a_pilot, y_pilot.data_ptr(),
+                               y_data.data_ptr(), tag)
+
+    def submit(self, reqs):
+        arr = (Z.zotfs_request * len(reqs))(*reqs)
+        Z.check(Z.zotfs_server_submit(self._h, arr, len(reqs)))
+
+    def replay(self, reqs, arrival_s):
+        arr = (Z.zotfs_request * len(reqs))(*reqs)
+        ts = (C.c_double * len(reqs))(*[float(t) for t in arrival_s])
+        Z.check(Z.zotfs_server_replay(self._h, arr, ts, len(reqs)))
+
+    def poll(self, max_n=4096):
+        buf = (Z.zotfs_completion * max_n)()
+        k = Z.zotfs_server_poll(self._h, buf, max_n)
+        return [buf[i] for i in range(k)]
+
+    def release(self, tag):
+        Z.check(Z.zotfs_server_release(self._h, tag))
+
+    def stats(self):
+        s = Z.zotfs_server_stats()
+        Z.check(Z.zotfs_server_get_stats(self._h, C.byref(s)))
+        return {n: getattr(s, n) for n, _ in s._fields_}
+
+    def read(self, tag, n_tx, MN, bps, n_lists, llr=False):
+        """Host copies of a completed frame's outputs: dict of numpy arrays."""
+        import numpy as np
+        bits = np.zeros(n_tx * MN * bps // 8, np.uint8)
+        L = np.zeros(n_tx * MN * bps, np.float32) if llr else None
+        pc = np.zeros(n_lists, np.int32)
+        dk = np.zeros(n_lists * self.p_max, np.int16)
+        dl = np.zeros(n_lists * self.p_max, np.int16)
+        h = np.zeros(n_lists * self.p_max, np.complex64)
+        ptr = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+        Z.check(Z.zotfs_server_read(self._h, tag, ptr(bits), ptr(L), ptr(pc), ptr(dk), ptr(dl), ptr(h)))
+        return {"bits": bits, "llr": L, "count": pc, "dk": dk, "dl": dl, "h": h}

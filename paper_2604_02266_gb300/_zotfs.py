@@ -65,6 +65,29 @@ class zotfs_batch_opts(C.Structure):
                 ("n_tuning", C.c_int32), ("tuning", C.POINTER(zotfs_tuning_entry))]
 
 
+class zotfs_server_opts(C.Structure):
+    _fields_ = [("p_max", C.c_int32), ("max_wave_frames", C.c_int32), ("waves_in_flight", C.c_int32),
+                ("keep_llr", C.c_int32), ("arena_bytes", C.c_int64), ("max_M", C.c_int32), ("max_N", C.c_int32),
+                ("max_ant", C.c_int32)]
+
+
+class zotfs_request(C.Structure):
+    _fields_ = [("M", C.c_int32), ("N", C.c_int32), ("n_rx", C.c_int32), ("n_tx", C.c_int32), ("qam", C.c_int32),
+                ("iters", C.c_int32), ("noise_var", C.c_float), ("theta", C.c_float), ("a_pilot", C.c_float),
+                ("y_pilot", C.c_void_p), ("y_data", C.c_void_p), ("tag", C.c_uint64)]
+
+
+class zotfs_completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("n_lists", C.c_int32), ("arrival_ns", C.c_int64),
+                ("admit_ns", C.c_int64), ("done_ns", C.c_int64), ("bits", C.c_void_p), ("llr", C.c_void_p),
+                ("path_count", C.c_void_p), ("path_dk", C.c_void_p), ("path_dl", C.c_void_p), ("path_h", C.c_void_p)]
+
+
+class zotfs_server_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "admitted", "completed", "released", "pending", "waves",
+                                         "arena_bytes", "arena_in_use", "arena_high_water", "rejected_too_large")]
+
+
 _P = C.c_void_p
 _I = C.c_int
 # name -> (restype, argtypes); mirrors include/zotfs.h
@@ -86,6 +109,14 @@ SIGNATURES = {
     "zotfs_batch_create": (_I, [C.POINTER(zotfs_frame_desc), _I, C.POINTER(zotfs_batch_opts), C.POINTER(_P)]),
     "zotfs_rx_batch": (_I, [_P, _P, _P]),
     "zotfs_batch_destroy": (_I, [_P]),
+    "zotfs_server_create": (_I, [C.POINTER(zotfs_server_opts), C.POINTER(_P)]),
+    "zotfs_server_submit": (_I, [_P, C.POINTER(zotfs_request), _I]),
+    "zotfs_server_replay": (_I, [_P, C.POINTER(zotfs_request), C.POINTER(C.c_double), _I]),
+    "zotfs_server_poll": (_I, [_P, C.POINTER(zotfs_completion), _I]),
+    "zotfs_server_read": (_I, [_P, C.c_uint64, _P, _P, _P, _P, _P, _P]),
+    "zotfs_server_release": (_I, [_P, C.c_uint64]),
+    "zotfs_server_get_stats": (_I, [_P, C.POINTER(zotfs_server_stats)]),
+    "zotfs_server_destroy": (_I, [_P]),
     "zotfs_last_error": (C.c_char_p, []),
     "zotfs_last_launch_count": (_I, []),
 }
@@ -142,5 +173,13 @@ zotfs_equalize_static = _mk("zotfs_equalize_static")
 zotfs_batch_create = _mk("zotfs_batch_create")
 zotfs_rx_batch = _mk("zotfs_rx_batch")
 zotfs_batch_destroy = _mk("zotfs_batch_destroy")
+zotfs_server_create = _mk("zotfs_server_create")
+zotfs_server_submit = _mk("zotfs_server_submit")
+zotfs_server_replay = _mk("zotfs_server_replay")
+zotfs_server_poll = _mk("zotfs_server_poll")
+zotfs_server_read = _mk("zotfs_server_read")
+zotfs_server_release = _mk("zotfs_server_release")
+zotfs_server_get_stats = _mk("zotfs_server_get_stats")
+zotfs_server_destroy = _mk("zotfs_server_destroy")
 zotfs_last_error = _mk("zotfs_last_error")
 zotfs_last_launch_count = _mk("zotfs_last_launch_count")

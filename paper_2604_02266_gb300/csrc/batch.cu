@@ -56,7 +56,7 @@ static zotfs_status binval(const std::string& m) {
   return ZOTFS_EINVAL;
 }
 
-static zotfs_status make_tables(int M, int N, float2** dW, float2** dTab) {
+zotfs_status make_shape_tables(int M, int N, float2** dW, float2** dTab) {
   const int MN = M * N;
   std::vector<float2> W(MN), Tab(MN);
   const double two_pi = 6.283185307179586476925286766559;
@@ -72,6 +72,33 @@ static zotfs_status make_tables(int M, int N, float2** dW, float2** dTab) {
   if (e == cudaSuccess) e = cudaMemcpy(*dTab, Tab.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "batch tables");
   return ZOTFS_OK;
+}
+
+void bucket_args(int M, int N, int nrx, int ntx, int pilot_mode, int guard, int p_max, int in_dtype, const float2* W,
+                 const float2* Tab, FrameArgs& A) {
+  std::memset(&A, 0, sizeof(A));
+  A.M = M;
+  A.N = N;
+  A.logM = ilog2(M);
+  A.logN = ilog2(N);
+  A.nrx = nrx;
+  A.ntx = ntx;
+  A.K0 = M / 2;
+  A.L0 = N / 2;
+  A.pilot_mode = pilot_mode;
+  A.guard = guard;
+  A.p_max = p_max;
+  A.in_dtype = in_dtype;
+  A.tap_dtype = ZOTFS_C64;
+  A.qam = 4;
+  A.bps = 2;
+  A.a_pilot = std::sqrt((double)M * N);
+  A.inv_sqrtN = 1.0 / std::sqrt((double)N);
+  A.sqrtN = std::sqrt((double)N);
+  A.pam_d = std::sqrt(3.0 / 6.0);
+  A.W = W;
+  A.Tab = Tab;
+  A.mode = kEstimate | kCG | kDemap | kWritePaths | kWriteX;
 }
 
 static zotfs_status validate_desc(const zotfs_frame_desc& d, int i) {
@@ -141,11 +168,11 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
   }
 
   // group frames into buckets of equal kernel geometry
-  std::map<std::tuple<int, int, int, int, int, int, int, int, int, float>, int> key_to_bucket;
+  std::map<std::tuple<int, int, int, int, int, int, int, int>, int> key_to_bucket;
   for (int i = 0; i < n_frames; ++i) {
     const zotfs_frame_desc& d = D[i];
-    auto key = std::make_tuple(d.M, d.N, d.n_rx, d.n_tx, d.qam, d.pilot_mode, d.guard, d.p_max, d.in_dtype,
-                               d.a_pilot);
+    // QAM order, pilot amplitude, noise, threshold and iteration count are per frame
+    auto key = std::make_tuple(d.M, d.N, d.n_rx, d.n_tx, d.pilot_mode, d.guard, d.p_max, d.in_dtype);
     auto it = key_to_bucket.find(key);
     int bi;
     if (it == key_to_bucket.end()) {
@@ -241,7 +268,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     auto it = b->tables.find(key);
     if (it == b->tables.end()) {
       float2 *W = nullptr, *T = nullptr;
-      st = make_tables(B.M, B.N, &W, &T);
+      st = make_shape_tables(B.M, B.N, &W, &T);
       b->tables[key] = {W, T};
       it = b->tables.find(key);
     }
@@ -302,30 +329,8 @@ zotfs_status zotfs_rx_batch(zotfs_batch b, int32_t* status, zotfs_stream stream)
     e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "counter reset");
     FrameArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.M = B.M;
-    A.N = B.N;
-    A.logM = ilog2(B.M);
-    A.logN = ilog2(B.N);
-    A.nrx = B.nrx;
-    A.ntx = B.ntx;
-    A.K0 = B.M / 2;
-    A.L0 = B.N / 2;
-    A.pilot_mode = B.pilot_mode;
-    A.guard = B.guard;
-    A.p_max = B.p_max;
-    A.in_dtype = B.in_dtype;
-    A.tap_dtype = ZOTFS_C64;
-    A.qam = B.qam;
-    A.bps = ilog2(B.qam);
-    A.a_pilot = B.a_pilot;
-    A.inv_sqrtN = 1.0 / std::sqrt((double)B.N);
-    A.sqrtN = std::sqrt((double)B.N);
-    A.pam_d = std::sqrt(3.0 / (2.0 * (B.qam - 1)));
-    A.W = B.d_W;
-    A.Tab = B.d_Tab;
+    bucket_args(B.M, B.N, B.nrx, B.ntx, B.pilot_mode, B.guard, B.p_max, B.in_dtype, B.d_W, B.d_Tab, A);
     A.n_frames = (int)B.ids.size();
-    A.mode = kEstimate | kCG | kDemap | kWritePaths | kWriteX;
     A.work_counter = counter;
     A.status = status;
     A.descs = b->d_descs;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
           dzt_inplace<R>(stage, A, radix);
           const int li = r * A.ntx + t;
           int trunc;
-          const int P = readoff_compact<R, EW>(stage, A, (R)io.theta, paths + (size_t)li * A.p_max, S, gout, li, trunc);
+          const int P = readoff_compact<R, EW>(stage, A, (R)io.theta, io.a_pilot, paths + (size_t)li * A.p_max, S, gout, li, trunc);
           if (tid == 0) cnt[li] = P;
           if (trunc) st |= kStTrunc;
         }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
       load_grid(io.y_data);
       dzt_inplace<R>(stage, A, radix);
       int trunc;
-      const int P = readoff_compact<R, EW>(stage, A, (R)io.theta, paths, S, gout, 0, trunc);
+      const int P = readoff_compact<R, EW>(stage, A, (R)io.theta, io.a_pilot, paths, S, gout, 0, trunc);
       if (tid == 0) cnt[0] = P;
       if (trunc) st |= kStTrunc;
       have_paths = true;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
         if (A.pilot_mode == ZOTFS_PILOT_EMBEDDED) {
           if ((A.mode & kEstimate) && !have_paths) {
             int trunc;
-            const int P = readoff_compact<R, EW>(stage, A, (R)io.theta, paths, S, gout, 0, trunc);
+            const int P = readoff_compact<R, EW>(stage, A, (R)io.theta, io.a_pilot, paths, S, gout, 0, trunc);
             if (tid == 0) cnt[0] = P;
             if (trunc) st |= kStTrunc;
             __syncthreads();
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
             const int nw = Acol >> logM;
             C val = cmul(rec.h, tw<R>(A, (size_t)((rec.dl * Acol) & (MN - 1))));
             val = cmul(val, tw<R>(A, (size_t)(((nw * A.L0) << logM) & (MN - 1))));
-            val = cscale(val, (R)(A.a_pilot * A.sqrtN));
+            val = cscale(val, (R)(io.a_pilot * A.sqrtN));
             C* y = stage + (size_t)bitrev(lr, A.logN) * M + kr;
             *y = csub(*y, val);
           }
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
     // ------------------------------------------------ demapping
     if ((A.mode & kDemap) && (io.llr || io.bits)) {
       const R inv_lam = (R)1 / (R)io.lam;
-      const int bps = A.bps;
+      const int bps = io.bps;
       uint8_t* lab = reinterpret_cast<uint8_t*>(stage);
       __syncthreads();
       for (int t = 0; t < A.ntx; ++t)
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
             const size_t o = (size_t)t * MN + own(c, i);
             const int q = (int)(o - (size_t)t * MN);
             float l[6];
-            const int hard = qam_llr<R>(Xv[o], bps, (R)A.pam_d, inv_lam, l);
+            const int hard = qam_llr<R>(Xv[o], bps, (R)io.pam_d, inv_lam, l);
             lab[o] = (uint8_t)hard;
             if (io.llr) {
               float2* ol = reinterpret_cast<float2*>(io.llr + ((size_t)t * MN + q) * bps);

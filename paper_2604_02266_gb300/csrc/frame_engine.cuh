@@ -116,6 +116,9 @@ struct FrameIO {
   const char* x_in;     // x_hat input [t][MN] (demap-only mode)
   float lam, theta;
   int iters;
+  int bps;              // bits per QAM symbol of this frame
+  double pam_d;         // PAM half-spacing of this frame's QAM (unit mean energy)
+  double a_pilot;       // pilot amplitude divided out of the read-off
   char* x_hat;          // [t][MN] or NULL
   float* llr;           // [t][MN][bps] or NULL
   uint8_t* bits;        // [t][MN bps / 8] or NULL
@@ -351,13 +354,13 @@ __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t 
 // (ties to the lower q).  Returns P; sets `trunc`.  Every thread owns q in
 // [tid*EQ, tid*EQ + EQ), EQ = MN/T.  When gout is set the list is also stored as list li.
 template <typename R, int EQ>
-__device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const FrameArgs& A, R theta,
+__device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const FrameArgs& A, R theta, double a_pilot,
                                                PathRecT<R>* out, SharedHdr* S, const PathIO* gout, int li,
                                                int& trunc) {
   using C = typename Cx<R>::C;
   using Key = typename Cx<R>::Key;
   const int M = A.M, N = A.N, logM = A.logM, MN = M * N, tid = threadIdx.x;
-  const R scale = (R)A.inv_sqrtN / (R)A.a_pilot;
+  const R scale = (R)A.inv_sqrtN / (R)a_pilot;
   const R th2 = theta * theta;
   C hv[EQ];
   Key mb[EQ];

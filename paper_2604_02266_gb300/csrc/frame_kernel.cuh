@@ -43,6 +43,9 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
     io.lam = d.noise_var;
     io.theta = d.theta;
     io.iters = d.iters;
+    io.bps = 31 - __clz(d.qam);
+    io.pam_d = sqrt(3.0 / (2.0 * (d.qam - 1)));
+    io.a_pilot = d.a_pilot;
     io.x_hat = reinterpret_cast<char*>(d.x_hat);
     io.llr = d.llr;
     io.bits = d.bits;
@@ -66,6 +69,9 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
   io.lam = A.noise_var ? A.noise_var[f] : 0.f;
   io.theta = A.theta ? A.theta[f] : 0.f;
   io.iters = A.iters;
+  io.bps = A.bps;
+  io.pam_d = A.pam_d;
+  io.a_pilot = A.a_pilot;
   io.x_hat = A.x_hat ? static_cast<char*>(A.x_hat) + (size_t)f * A.ntx * MN * csz : nullptr;
   io.llr = A.llr ? A.llr + (size_t)f * A.ntx * MN * A.bps : nullptr;
   io.bits = A.bits ? A.bits + (size_t)f * A.ntx * MN * A.bps / 8 : nullptr;
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           dzt_inplace<R>(ext, A, radix);
           const int li = r * A.ntx + t;
           int trunc;
-          const int P = readoff_compact<R, E>(ext, A, (R)io.theta, paths + (size_t)li * A.p_max, S, gout, li, trunc);
+          const int P = readoff_compact<R, E>(ext, A, (R)io.theta, io.a_pilot, paths + (size_t)li * A.p_max, S, gout, li, trunc);
           if (tid == 0) cnt[li] = P;
           if (trunc) st |= kStTrunc;
         }
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
       } else {
         dzt_inplace<R>(ext, A, radix);
         int trunc;
-        const int P = readoff_compact<R, E>(ext, A, (R)io.theta, paths, S, gout, 0, trunc);
+        const int P = readoff_compact<R, E>(ext, A, (R)io.theta, io.a_pilot, paths, S, gout, 0, trunc);
         if (tid == 0) cnt[0] = P;
         if (trunc) st |= kStTrunc;
       }
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
         if (A.pilot_mode == ZOTFS_PILOT_EMBEDDED) {
           if ((A.mode & kEstimate) && !have_paths) {
             int trunc;
-            const int P = readoff_compact<R, E>(ext, A, (R)io.theta, paths, S, gout, 0, trunc);
+            const int P = readoff_compact<R, E>(ext, A, (R)io.theta, io.a_pilot, paths, S, gout, 0, trunc);
             if (tid == 0) cnt[0] = P;
             if (trunc) st |= kStTrunc;
             __syncthreads();
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             const int nw = Acol >> logM;  // floor division by M
             C val = cmul(rec.h, tw<R>(A, (size_t)((rec.dl * Acol) & (MN - 1))));
             val = cmul(val, tw<R>(A, (size_t)(((nw * A.L0) << logM) & (MN - 1))));
-            val = cscale(val, (R)(A.a_pilot * A.sqrtN));
+            val = cscale(val, (R)(io.a_pilot * A.sqrtN));
             C* y = ext + (size_t)bitrev(lr, A.logN) * M + kr;
             *y = csub(*y, val);
           }
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
     // ------------------------------------------------ demapping
     if ((A.mode & kDemap) && (io.llr || io.bits)) {
       const R inv_lam = (R)1 / (R)io.lam;
-      const int bps = A.bps;
+      const int bps = io.bps;
       uint8_t* lab = reinterpret_cast<uint8_t*>(ext);
       __syncthreads();  // ext no longer read by anyone
 #pragma unroll
@@ -382,7 +388,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           for (int i = 0; i < E; ++i) {
             const int q = (j0 + i) * M + k;
             float l[6];
-            const int hard = qam_llr<R>(x[t][i], bps, (R)A.pam_d, inv_lam, l);
+            const int hard = qam_llr<R>(x[t][i], bps, (R)io.pam_d, inv_lam, l);
             lab[t * MN + q] = (uint8_t)hard;
             if (io.llr) {
               float2* o = reinterpret_cast<float2*>(io.llr + ((size_t)t * MN + q) * bps);

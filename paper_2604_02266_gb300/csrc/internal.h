@@ -72,6 +72,14 @@ cudaError_t big_launch(const BigCfg& cfg, const FrameArgs& A, int radix, int gri
                        cudaStream_t stream);
 cudaError_t big_occupancy(const BigCfg& cfg, int& blocks);
 
+// FrameArgs for a descriptor-driven launch over frames of one geometry (batch.cu); per-frame
+// values (noise, threshold, QAM order, pilot amplitude, iterations, buffers) come from the
+// descriptors.
+void bucket_args(int M, int N, int nrx, int ntx, int pilot_mode, int guard, int p_max, int in_dtype, const float2* W,
+                 const float2* Tab, FrameArgs& A);
+// Root-of-unity tables of one (M, N) shape in FP32 (allocates).
+zotfs_status make_shape_tables(int M, int N, float2** dW, float2** dTab);
+
 // Plain form (plain.cu)
 size_t plain_scratch_bytes(int M, int N, int nrx, int ntx, int p_max);
 zotfs_status run_plain(zotfs_plan_s* plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,

@@ -87,7 +87,7 @@ __global__ void plain_compact_kernel(const __grid_constant__ FrameArgs A, const 
   gout.h = A.ph ? static_cast<char*>(A.ph) + (size_t)fo * A.p_max * dtype_bytes(A.tap_dtype) : nullptr;
   gout.tap_dtype = A.tap_dtype;
   int trunc;
-  const int P = readoff_compact<float, EQ>(X, A, A.theta[f], paths_out + (size_t)list_local * A.p_max, S,
+  const int P = readoff_compact<float, EQ>(X, A, A.theta[f], A.a_pilot, paths_out + (size_t)list_local * A.p_max, S,
                                     write_global ? &gout : nullptr, list_local, trunc);
   if (threadIdx.x == 0) {
     counts[list_local] = P;
