@@ -214,7 +214,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
         if (!o.ctas_per_sm) cps = te.tuning.ctas_per_sm;
       }
     }
-    B.radix = radix == 4 ? 4 : 2;
+    B.radix = radix == 2 ? 2 : (radix == 4 ? 4 : kDefaultRadix);
     B.ctas_per_sm = cps;
     if (!choose_frame_cfg(B.M, B.N, B.nrx, B.ntx, B.p_max, tpf, B.cfg) &&
         !(tpf > 0 && choose_frame_cfg(B.M, B.N, B.nrx, B.ntx, B.p_max, 0, B.cfg))) {

@@ -117,7 +117,7 @@ static zotfs_status check_paths(const zotfs_plan_s* plan, const zotfs_paths* pat
   return ZOTFS_OK;
 }
 
-static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 4 ? 4 : 2; }
+static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 2 ? 2 : 4; }
 
 // Launch the shared-memory frame kernel when the shape fits one CTA, else the large-frame
 // kernel on the plan's scratch slots.
@@ -187,7 +187,7 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
   p->opt.tap_dtype = ZOTFS_C64;
   p->opt.compute = ZOTFS_COMPUTE_FP32;
   p->tune.threads_per_frame = 0;
-  p->tune.fft_radix = 2;
+  p->tune.fft_radix = kDefaultRadix;
   p->tune.ctas_per_sm = 0;
 
   cudaError_t e = cudaGetDevice(&p->device);
@@ -305,7 +305,7 @@ zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* t) {
   if (t->threads_per_frame < 0 || t->threads_per_frame > 1024) return inval("threads_per_frame");
   if (t->ctas_per_sm < 0) return inval("ctas_per_sm");
   zotfs_tuning n = *t;
-  if (n.fft_radix == 0) n.fft_radix = 2;
+  if (n.fft_radix == 0) n.fft_radix = kDefaultRadix;
   if (n.threads_per_frame > 0) {
     FrameCfg cfg;
     if (!choose_frame_cfg(plan->M, plan->N, plan->nrx, plan->ntx, plan->opt.p_max, n.threads_per_frame, cfg,

@@ -25,7 +25,10 @@ __host__ __device__ __forceinline__ size_t big_slot_elems(int M, int N, int nrx,
 __host__ __device__ __forceinline__ size_t big_smem_bytes(int nrx, int ntx, int p_max, int real_bytes) {
   size_t hdr = (sizeof(SharedHdr) + 127) & ~size_t(127);
   const size_t rec = (size_t)4 * real_bytes + 16;
-  return hdr + (size_t)nrx * ntx * p_max * rec + (size_t)nrx * ntx * sizeof(int) * 2;
+  size_t paths = ((size_t)nrx * ntx * p_max * rec + (size_t)nrx * ntx * sizeof(int) * 2 + 127) & ~size_t(127);
+  paths += ((size_t)nrx * ntx * p_max * sizeof(RunRec) + 127) & ~size_t(127);
+  paths += ((size_t)p_max * rec + 127) & ~size_t(127);
+  return hdr + paths;
 }
 
 template <typename R, int EW>
@@ -38,8 +41,14 @@ __global__ void __launch_bounds__(kBigThreads, 1)
   extern __shared__ __align__(128) unsigned char smem[];
   SharedHdr* S = reinterpret_cast<SharedHdr*>(smem);
   const int nlists = A.nrx * A.ntx;
-  PathRec* paths = reinterpret_cast<PathRec*>(smem + ((sizeof(SharedHdr) + 127) & ~size_t(127)));
+  size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
+  PathRec* paths = reinterpret_cast<PathRec*>(smem + off);
   int* cnt = reinterpret_cast<int*>(paths + (size_t)nlists * A.p_max);
+  int* nruns = cnt + nlists;
+  off += ((size_t)nlists * A.p_max * sizeof(PathRec) + (size_t)nlists * sizeof(int) * 2 + 127) & ~size_t(127);
+  RunRec* runs = reinterpret_cast<RunRec*>(smem + off);
+  off += ((size_t)nlists * A.p_max * sizeof(RunRec) + 127) & ~size_t(127);
+  PathRec* sort_tmp = reinterpret_cast<PathRec*>(smem + off);
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM, T = blockDim.x;
   const int nb = A.nrx > A.ntx ? A.nrx : A.ntx;
@@ -118,6 +127,9 @@ __global__ void __launch_bounds__(kBigThreads, 1)
       have_paths = true;
     }
     __syncthreads();
+    if (have_paths)
+      for (int li = 0; li < nlists; ++li)
+        build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, nruns + li);
 
     C v[E];
     // ------------------------------------------------ one operator apply
@@ -133,8 +145,8 @@ __global__ void __launch_bounds__(kBigThreads, 1)
       __syncthreads();
       for (int b = 0; b < nout; ++b)
         for (int c = 0; c < NCH; ++c) {
-          if (A.adjoint) gather_adj<R, E, true>(src, blk, paths, cnt, A, b, k, jw + c * E, v);
-          else gather_fwd<R, E, true>(src, blk, paths, cnt, A, b, k, jw + c * E, v);
+          if (A.adjoint) gather_adj<R, E, true>(src, blk, paths, runs, nruns, A, b, k, jw + c * E, v);
+          else gather_fwd<R, E, true>(src, blk, paths, runs, nruns, A, b, k, jw + c * E, v);
 #pragma unroll
           for (int i = 0; i < E; ++i) reinterpret_cast<C*>(io.u_out)[(size_t)b * MN + own(c, i)] = v[i];
         }
@@ -166,6 +178,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
             if (tid == 0) cnt[0] = P;
             if (trunc) st |= kStTrunc;
             __syncthreads();
+            build_runs<R>(paths, cnt[0], runs, sort_tmp, nruns);
           }
           for (int p = tid; p < cnt[0]; p += T) {
             const PathRec rec = paths[p];
@@ -193,7 +206,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
       R part = 0;
       for (int t = 0; t < A.ntx; ++t)
         for (int c = 0; c < NCH; ++c) {
-          gather_adj<R, E, true>(extT, blk, paths, cnt, A, t, k, jw + c * E, v);
+          gather_adj<R, E, true>(extT, blk, paths, runs, nruns, A, t, k, jw + c * E, v);
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const size_t o = (size_t)t * MN + own(c, i);
@@ -212,7 +225,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
         // t = H p  (extP -> extT)
         for (int r = 0; r < A.nrx; ++r)
           for (int c = 0; c < NCH; ++c) {
-            gather_fwd<R, E, true>(extP, blk, paths, cnt, A, r, k, jw + c * E, v);
+            gather_fwd<R, E, true>(extP, blk, paths, runs, nruns, A, r, k, jw + c * E, v);
             write_ext<R, E, true>(extT + r * blk, A, k, jw + c * E, v);
           }
         __syncthreads();
@@ -220,7 +233,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
         part = 0;
         for (int t = 0; t < A.ntx; ++t)
           for (int c = 0; c < NCH; ++c) {
-            gather_adj<R, E, true>(extT, blk, paths, cnt, A, t, k, jw + c * E, v);
+            gather_adj<R, E, true>(extT, blk, paths, runs, nruns, A, t, k, jw + c * E, v);
 #pragma unroll
             for (int i = 0; i < E; ++i) {
               const size_t o = (size_t)t * MN + own(c, i);

@@ -9,8 +9,8 @@
 // Shared-memory vector layout ("ext").  The vector an operator gathers from is stored as
 // its quasi-periodic extension (footnote of Eq. y_channel_DD):
 //     X_ext[A, r] = X[<A>_M, <r>_N] exp(j2pi floor(A/M) <r>_N / N)
-// for columns A in [-M/2, 3M/2) and rows r in [0, N + E - 1), column-major: element (A, r)
-// at (A + M/2) CS + r with column stride CS = N + E - 1 (odd, so the 32 consecutive columns
+// for columns A in [-M/2, 3M/2) and rows r in [0, N + E + 3), column-major: element (A, r)
+// at (A + M/2) CS + r with column stride CS = N + E + 3 (odd, so the 32 consecutive columns
 // a warp reads fall in distinct banks).
 // With it, path p's contribution to output (k, l) -- the twisted shift of Sec. IV-B with
 // map Eq. map_chMatDD_col, wrap count n and phase phi -- becomes a plain shifted read:
@@ -20,7 +20,10 @@
 // phase exp(j2pi n l_{p,q} / N) of the paper's phi is carried by the stored halo columns,
 // the term (l_p - L0) A by the per-(path, column) coefficient, so each gather is one
 // shared load at a constant offset and two packed FMAs.  Rows are periodic (no phase), so
-// E - 1 halo rows let a thread read its E consecutive source rows without a wrap.
+// E + 3 halo rows let a thread read a window of up to E + 3 consecutive source rows without a
+// wrap.  Paths are applied in runs: paths with equal dk and consecutive dl read overlapping
+// rows, so a run of L <= 4 such paths loads one (L + E - 1)-row window into registers and
+// applies all L paths from it.
 //
 // Everything is templated on the arithmetic type R (float, or double for FP64 plans).
 #pragma once
@@ -28,6 +31,13 @@
 #include "common.cuh"
 
 namespace zotfs {
+
+// A run of paths (indices start .. start + len - 1 of a list sorted by (dk, dl)) with equal
+// dk and consecutive dl = dl0, dl0 + 1, ...
+struct RunRec {
+  short start, len, dk, dl0;
+};
+constexpr int kMaxRun = 4;
 
 template <typename R>
 struct PathRecT {             // one dominant path in shared memory
@@ -137,7 +147,7 @@ struct SharedHdr {       // fixed part of the dynamic shared memory
 };
 
 // Shared-memory bytes needed by a frame kernel launch (host and device agree on this).
-__host__ __device__ __forceinline__ int ext_rows(int N, int E) { return N + E - 1; }  // = column stride CS
+__host__ __device__ __forceinline__ int ext_rows(int N, int E) { return N + E + 3; }  // = column stride CS
 __host__ __device__ __forceinline__ size_t ext_block_elems(int M, int N, int E) {
   return (size_t)ext_rows(N, E) * (size_t)(2 * M);
 }
@@ -147,6 +157,8 @@ __host__ __device__ __forceinline__ size_t frame_smem_bytes(int M, int N, int E,
   const size_t rec = (size_t)4 * real_bytes + 16;  // PathRecT<R>
   size_t paths = (size_t)nrx * ntx * p_max * rec + (size_t)nrx * ntx * sizeof(int) * 2;
   paths = (paths + 127) & ~size_t(127);
+  paths += ((size_t)nrx * ntx * p_max * sizeof(RunRec) + 127) & ~size_t(127);  // run tables
+  paths += ((size_t)p_max * rec + 127) & ~size_t(127);                        // sort scratch
   int nb = nrx > ntx ? nrx : ntx;
   size_t ext = (size_t)nb * ext_block_elems(M, N, E) * 2 * real_bytes;
   return hdr + paths + ext;
@@ -257,7 +269,7 @@ template <typename R, int E, bool kRowMajor = false>
 __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArgs& A, int k, int j0,
                                           const typename Cx<R>::C (&v)[E]) {
   using C = typename Cx<R>::C;
-  const int M = A.M, N = A.N, CS = N + E - 1, Hk = M >> 1, logM = A.logM, MN = M * N;
+  const int M = A.M, N = A.N, CS = N + E + 3, Hk = M >> 1, logM = A.logM, MN = M * N;
   const size_t rstep = kRowMajor ? (size_t)(2 * M) : 1;  // distance between consecutive rows
   // halo column: k < M/2 stores X_ext[k + M] = X[k] W_N[l]; k >= M/2 stores X_ext[k - M] = X[k] W_N[-l]
   const bool low = k < Hk;
@@ -271,7 +283,7 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
     const C hv = cmul(v[i], tw<R>(A, widx));
     mcol[l * rstep] = v[i];
     hcol[l * rstep] = hv;
-    if (l < E - 1) {
+    if (l < E + 3) {
       mcol[(l + N) * rstep] = v[i];
       hcol[(l + N) * rstep] = hv;
     }
@@ -280,70 +292,131 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
 
 // ----------------------------------------------------------- operator gathers
 
-// Forward rows of output block r: out[i] = (H p)_r[k, j0 + i] over tx blocks t, paths of (r, t).
-template <typename R, int E, bool kRowMajor = false>
-__device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
-                                           const int* cnt, const FrameArgs& A, int r, int k, int j0,
-                                           typename Cx<R>::C (&out)[E]) {
+// One run of L paths on E output rows.  kFwd: window rows start at (j0 - dl0 - (L-1)) mod N
+// of column k - dk and path m reads window[L - 1 - m + i]; adjoint: rows start at
+// (j0 + dl0) mod N of column k + dk and path m reads window[m + i].
+template <typename R, int E, int L, bool kFwd, bool kRowMajor>
+__device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl, const RunRec& rr,
+                                          const FrameArgs& A, int k, int j0, typename Cx<R>::C (&accA)[E],
+                                          typename Cx<R>::C (&accB)[E]) {
   using C = typename Cx<R>::C;
-  const int M = A.M, N = A.N, Hk = M >> 1;
-  const int CS = kRowMajor ? 1 : N + E - 1;        // column step
-  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;  // row step
+  const int M = A.M, N = A.N;
+  const int CS = kRowMajor ? 1 : N + E + 3;
+  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;
+  const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
+  const C* a = src + (size_t)row0 * RS + (kFwd ? -rr.dk : rr.dk) * CS;
+  C W[L + E - 1];
+#pragma unroll
+  for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
+#pragma unroll
+  for (int m = 0; m < L; ++m) {
+    const PathRecT<R> rec = pl[rr.start + m];
+    const C t = tab<R>(A, (rr.dl0 + m + (N >> 1)) * M + k);
+    const C D = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+    const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
+#pragma unroll
+    for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, W[(kFwd ? L - 1 - m : m) + i]);
+  }
+}
+
+// Forward rows (kFwd) of output block b: out[i] = (H p)_b[k, j0 + i], summed over the tx blocks
+// and the runs of each (b, t) list; adjoint: out[i] = (H^H u)_b[k, j0 + i] over the rx blocks.
+template <typename R, int E, bool kFwd, bool kRowMajor>
+__device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
+                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int b, int k,
+                                            int j0, typename Cx<R>::C (&out)[E]) {
+  using C = typename Cx<R>::C;
+  // register budget: the window holds L + E - 1 complex values beside 2E accumulators
+  constexpr int kLMax = E >= 32 ? 1 : (E >= 16 ? 2 : kMaxRun);
+  const int Hk = A.M >> 1;
+  const int CS = kRowMajor ? 1 : A.N + E + 3;
   C accA[E], accB[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);
   const C* colk = ext + (size_t)(k + Hk) * CS;
-  for (int t = 0; t < A.ntx; ++t) {
-    const C* src = colk + (size_t)t * blk;
-    const int li = r * A.ntx + t;
+  const int nother = kFwd ? A.ntx : A.nrx;
+  for (int o = 0; o < nother; ++o) {
+    const C* src = colk + (size_t)o * blk;
+    const int li = kFwd ? b * A.ntx + o : o * A.ntx + b;
     const PathRecT<R>* pl = paths + (size_t)li * A.p_max;
-    const int P = cnt[li];
-#pragma unroll 2
-    for (int p = 0; p < P; ++p) {
-      const PathRecT<R> rec = pl[p];
-      const C D = cmul(rec.hf, tab<R>(A, (rec.dl + (N >> 1)) * M + k));
-      const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
-      // column k - dk, first row (j0 - dl) mod N
-      const C* a = src + (size_t)((j0 - rec.dl) & (N - 1)) * RS - rec.dk * CS;
-#pragma unroll
-      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i * RS]);
+    const RunRec* rl = runs + (size_t)li * A.p_max;
+    const int nr = nruns[li];
+    for (int q = 0; q < nr; ++q) {
+      const RunRec rr = rl[q];
+      if constexpr (kLMax == 1) {
+        for (int m = 0; m < rr.len; ++m) {
+          RunRec one = rr;
+          one.start = (short)(rr.start + m);
+          one.dl0 = (short)(rr.dl0 + m);
+          apply_run<R, E, 1, kFwd, kRowMajor>(src, pl, one, A, k, j0, accA, accB);
+        }
+      } else if constexpr (kLMax == 2) {
+        for (int m = 0; m < rr.len; m += 2) {
+          RunRec sub = rr;
+          sub.start = (short)(rr.start + m);
+          sub.dl0 = (short)(rr.dl0 + m);
+          if (rr.len - m >= 2) apply_run<R, E, 2, kFwd, kRowMajor>(src, pl, sub, A, k, j0, accA, accB);
+          else apply_run<R, E, 1, kFwd, kRowMajor>(src, pl, sub, A, k, j0, accA, accB);
+        }
+      } else {
+        switch (rr.len) {
+          case 1: apply_run<R, E, 1, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
+          case 2: apply_run<R, E, 2, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
+          case 3: apply_run<R, E, 3, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
+          default: apply_run<R, E, 4, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
+        }
+      }
     }
   }
 #pragma unroll
   for (int i = 0; i < E; ++i) out[i] = Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
 }
 
-// Adjoint rows of output block t: out[i] = (H^H u)_t[k, j0 + i] over rx blocks r, paths of (r, t).
+template <typename R, int E, bool kRowMajor = false>
+__device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
+                                           const RunRec* runs, const int* nruns, const FrameArgs& A, int r, int k,
+                                           int j0, typename Cx<R>::C (&out)[E]) {
+  gather_runs<R, E, true, kRowMajor>(ext, blk, paths, runs, nruns, A, r, k, j0, out);
+}
 template <typename R, int E, bool kRowMajor = false>
 __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
-                                           const int* cnt, const FrameArgs& A, int t, int k, int j0,
-                                           typename Cx<R>::C (&out)[E]) {
-  using C = typename Cx<R>::C;
-  const int M = A.M, N = A.N, Hk = M >> 1;
-  const int CS = kRowMajor ? 1 : N + E - 1;
-  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;
-  C accA[E], accB[E];
-#pragma unroll
-  for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);
-  const C* colk = ext + (size_t)(k + Hk) * CS;
-  for (int r = 0; r < A.nrx; ++r) {
-    const C* src = colk + (size_t)r * blk;
-    const int li = r * A.ntx + t;
-    const PathRecT<R>* pl = paths + (size_t)li * A.p_max;
-    const int P = cnt[li];
-#pragma unroll 2
-    for (int p = 0; p < P; ++p) {
-      const PathRecT<R> rec = pl[p];
-      const C D = conjf2(cmul(rec.h, tab<R>(A, (rec.dl + (N >> 1)) * M + k)));
-      const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
-      // column k + dk, first row (j0 + dl) mod N
-      const C* a = src + (size_t)((j0 + rec.dl) & (N - 1)) * RS + rec.dk * CS;
-#pragma unroll
-      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, a[i * RS]);
-    }
+                                           const RunRec* runs, const int* nruns, const FrameArgs& A, int t, int k,
+                                           int j0, typename Cx<R>::C (&out)[E]) {
+  gather_runs<R, E, false, kRowMajor>(ext, blk, paths, runs, nruns, A, t, k, j0, out);
+}
+
+// Sort one list's shared-memory copy by (dk, dl) (rank sort through `tmp`, which must hold P
+// records and not alias the list) and cut it into runs of at most kMaxRun paths with equal dk
+// and consecutive dl.  All threads call.  Returns the number of runs.
+template <typename R>
+__device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, PathRecT<R>* tmp, int* nruns_out) {
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const PathRecT<R> me = pl[p];
+    const int key = me.dk * 256 + me.dl;
+    int rank = 0;
+    for (int u = 0; u < P; ++u) rank += (pl[u].dk * 256 + pl[u].dl) < key;
+    tmp[rank] = me;
   }
-#pragma unroll
-  for (int i = 0; i < E; ++i) out[i] = Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) pl[p] = tmp[p];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0, p = 0;
+    while (p < P) {
+      int len = 1;
+      while (p + len < P && len < kMaxRun && pl[p + len].dk == pl[p].dk && pl[p + len].dl == pl[p].dl + len) ++len;
+      RunRec rr;
+      rr.start = (short)p;
+      rr.len = (short)len;
+      rr.dk = (short)pl[p].dk;
+      rr.dl0 = (short)pl[p].dl;
+      runs[n++] = rr;
+      p += len;
+    }
+    *nruns_out = n;
+  }
+  __syncthreads();
+  return *nruns_out;
 }
 
 // ------------------------------------------------------------ read-off + compaction

@@ -96,7 +96,12 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
   size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
   PathRec* paths = reinterpret_cast<PathRec*>(smem + off);
   int* cnt = reinterpret_cast<int*>(paths + (size_t)nlists * A.p_max);
+  int* nruns = cnt + nlists;
   off += ((size_t)nlists * A.p_max * sizeof(PathRec) + (size_t)nlists * sizeof(int) * 2 + 127) & ~size_t(127);
+  RunRec* runs = reinterpret_cast<RunRec*>(smem + off);
+  off += ((size_t)nlists * A.p_max * sizeof(RunRec) + 127) & ~size_t(127);
+  PathRec* sort_tmp = reinterpret_cast<PathRec*>(smem + off);
+  off += ((size_t)A.p_max * sizeof(PathRec) + 127) & ~size_t(127);
   C* ext = reinterpret_cast<C*>(smem + off);
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM;
@@ -183,6 +188,9 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
       if (io.status && tid == 0) *io.status = status_from_bits(st);
       break;  // barrier phases are no longer trustworthy: stop this CTA
     }
+    if (have_paths)
+      for (int li = 0; li < nlists; ++li)
+        build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, nruns + li);
 
     C v[NB][E];  // operator outputs / inputs per antenna block
 
@@ -200,8 +208,8 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         if (b < nout) {
-          if (A.adjoint) gather_adj<R, E>(ext, blk, paths, cnt, A, b, k, j0, v[b]);
-          else gather_fwd<R, E>(ext, blk, paths, cnt, A, b, k, j0, v[b]);
+          if (A.adjoint) gather_adj<R, E>(ext, blk, paths, runs, nruns, A, b, k, j0, v[b]);
+          else gather_fwd<R, E>(ext, blk, paths, runs, nruns, A, b, k, j0, v[b]);
 #pragma unroll
           for (int i = 0; i < E; ++i) reinterpret_cast<C*>(io.u_out)[(size_t)b * MN + (size_t)(j0 + i) * M + k] = v[b][i];
         }
@@ -246,6 +254,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             if (tid == 0) cnt[0] = P;
             if (trunc) st |= kStTrunc;
             __syncthreads();
+            build_runs<R>(paths, cnt[0], runs, sort_tmp, nruns);
           }
           // remove the pilot's response a_pilot H e_(K0,L0) (grid still scaled by sqrt(N))
           for (int p = tid; p < cnt[0]; p += blockDim.x) {
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (t < A.ntx) {
-          gather_adj<R, E>(ext, blk, paths, cnt, A, t, k, j0, c[t]);
+          gather_adj<R, E>(ext, blk, paths, runs, nruns, A, t, k, j0, c[t]);
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             p[t][i] = c[t][i];
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
         // t = H p
 #pragma unroll
         for (int r = 0; r < NB; ++r)
-          if (r < A.nrx) gather_fwd<R, E>(ext, blk, paths, cnt, A, r, k, j0, v[r]);
+          if (r < A.nrx) gather_fwd<R, E>(ext, blk, paths, runs, nruns, A, r, k, j0, v[r]);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < NB; ++r)
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
         for (int t = 0; t < NB; ++t)
           if (t < A.ntx) {
-            gather_adj<R, E>(ext, blk, paths, cnt, A, t, k, j0, v[t]);
+            gather_adj<R, E>(ext, blk, paths, runs, nruns, A, t, k, j0, v[t]);
 #pragma unroll
             for (int i = 0; i < E; ++i) {
               v[t][i].x = fma(lam, p[t][i].x, v[t][i].x);

@@ -266,14 +266,14 @@ cudaError_t launch_wave(zotfs_server_s* s, Wave& w) {
       int occ = 1;
       frame_variant_occupancy(fc.variant, fc.T, fc.smem, occ);
       const int grid = std::max(1, std::min(nf, s->sm_count * std::max(occ, 1)));
-      e = frame_variant_launch(fc.variant, A, 2, grid, fc.T, fc.smem, st);
+      e = frame_variant_launch(fc.variant, A, kDefaultRadix, grid, fc.T, fc.smem, st);
     } else {
       BigCfg bc;
       if (!choose_big_cfg(M, N, nrx, ntx, s->o.p_max, bc)) return cudaErrorInvalidValue;
       bc.slot_bytes = s->big_slot_bytes;
       const int share = big_share[big_idx++];
       const int grid = std::min(nf, share);
-      e = big_launch(bc, A, 2, grid, w.d_big + (size_t)big_next * s->big_slot_bytes, st);
+      e = big_launch(bc, A, kDefaultRadix, grid, w.d_big + (size_t)big_next * s->big_slot_bytes, st);
       big_next += share;
     }
     if (e != cudaSuccess) return e;
