@@ -46,6 +46,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device=None):
+    """The maximum of a per-rank host number over all ranks (all_reduce MAX; the slowest
+    rank's time defines the whole job's), or x itself on one rank."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, ws, steps, seconds):
+    """Units per second of the whole job: every rank processes its own shard of
+    units_per_rank_step units per step (weak scaling), timed by the slowest rank."""
+    return units_per_rank_step * ws * steps / seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -266,12 +284,8 @@ def impl_zotfs(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    dev_s = float(step_ms.sum()) / 1e3
-    if ws > 1:
-        t = torch.tensor([dev_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_s = float(t.item())
-    value = FRAMES * ws * args.steps / dev_s
+    dev_s = max_over_ranks(float(step_ms.sum()) / 1e3, ws, dev)
+    value = whole_job_rate(FRAMES, ws, args.steps, dev_s)
 
     # ---- end to end: pinned host frames in, hard bits out, every step
     hp = torch.from_numpy(batch["y_pilot_td"]).pin_memory()
@@ -296,12 +310,8 @@ def impl_zotfs(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": FRAMES * ws * args.steps / e2e_s, "unit": "frames/s",
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws, dev)
+    e2e = {"value": whole_job_rate(FRAMES, ws, args.steps, e2e_s), "unit": "frames/s",
            "h2d_bytes_per_step": int(hp.numel() * hp.element_size() + hd.numel() * hd.element_size()),
            "d2h_bytes_per_step": int(hbits.numel() + hstat.numel() * 4)}
 
@@ -375,6 +385,116 @@ def impl_zotfs(args):
     return 0
 
 
+# ----------------------------------------------------------------- serving workload
+
+SERVE_M, SERVE_N, SERVE_ANT, SERVE_Q = (32, 64, 128, 256), (16, 32, 64), (1, 2, 4), (4, 16, 64)
+SERVE_WORKLOAD = ("serving loop: Poisson arrivals, M in {32,64,128,256}, N in {16,32,64}, 1x1/2x2/4x4, QAM in "
+                  "{4,16,64}, all uniform, 8-path fractional channels, SNR 0..30 dB, 10 CG iterations, "
+                  "0.5 ms deadline from arrival, outputs kept in a device arena until released")
+DEADLINE_MS = 0.5
+
+
+def impl_serve(args):
+    """Continuous-batching server under Poisson load: one run per offered rate, reporting the
+    completed frames/s, Mbit/s and the arrival-to-completion latency percentiles against the
+    slot deadline.  Requests draw their frames from a device-resident pool of synthetic
+    frames per (M, N, antennas, QAM) class."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Server
+
+    classes = [(m, n, a, q) for m in SERVE_M for n in SERVE_N for a in SERVE_ANT for q in SERVE_Q]
+    pool = {}
+    for ci, (m, n, a, q) in enumerate(classes):
+        b = synth.fractional_batch(args.pool, seed=SEED + 7919 * ci, M=m, N=n, Q=q, n_rx=a, n_tx=a, n_paths=8)
+        pool[(m, n, a, q)] = (torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev),
+                              b["noise_var"].astype(float), b["theta"].astype(float))
+    srv = Server(p_max=64, max_wave_frames=args.wave_frames, waves_in_flight=args.waves, keep_llr=False,
+                 arena_bytes=4 << 30, max_M=256, max_N=64, max_ant=4)
+
+    def make(n, g, tag0):
+        reqs, meta = [], []
+        for i in range(n):
+            m, nn, a, q = classes[int(g.integers(0, len(classes)))]
+            j = int(g.integers(0, args.pool))
+            yp, yd, nv, th = pool[(m, nn, a, q)]
+            reqs.append(Server.request(tag0 + i, yp[j], yd[j], m, nn, a, a, q, ITERS, nv[j], th[j]))
+            meta.append((m, nn, a, q))
+        return reqs, meta
+
+    def drain(n, timeout_s):
+        got = {}
+        t0 = time.time()
+        while len(got) < n:
+            cs = srv.poll()
+            for c in cs:
+                got[c.tag] = (c.status, c.arrival_ns, c.admit_ns, c.done_ns)
+                srv.release(c.tag)
+            if time.time() - t0 > timeout_s:
+                raise RuntimeError(f"serving run stalled: {len(got)} of {n} frames completed")
+            if not cs:
+                time.sleep(50e-6)
+        return got
+
+    g = np.random.default_rng(SEED)
+    try:
+        # warm-up: every class once (kernel attributes, first launches)
+        warm = [Server.request(10**9 + i, pool[c][0][0], pool[c][1][0], *c[:3], c[2], c[3], ITERS,
+                               pool[c][2][0], pool[c][3][0]) for i, c in enumerate(classes)]
+        srv.submit(warm)
+        drain(len(warm), 300)
+        runs = []
+        tag0 = 0
+        for rate in args.rates:
+            n = max(1, int(rate * args.duration))
+            reqs, meta = make(n, g, tag0)
+            arrivals = np.cumsum(g.exponential(1.0 / rate, size=n))
+            th = threading.Thread(target=srv.replay, args=(reqs, arrivals))
+            th.start()
+            got = drain(n, 600)
+            th.join()
+            rows = [got[tag0 + i] for i in range(n)]
+            tag0 += n
+            st = np.array([r[0] for r in rows])
+            arr = np.array([r[1] for r in rows], dtype=np.int64)
+            adm = np.array([r[2] for r in rows], dtype=np.int64)
+            done = np.array([r[3] for r in rows], dtype=np.int64)
+            lat = (done - arr) * 1e-6
+            wall = (done.max() - arr.min()) * 1e-9
+            bits = sum(a * m * nn * int(np.log2(q)) for (m, nn, a, q) in meta)
+            by_ant = {}
+            for a in SERVE_ANT:
+                sel = np.array([mt[2] == a for mt in meta])
+                if sel.any():
+                    by_ant[f"{a}x{a}"] = {"p50_ms": float(np.percentile(lat[sel], 50)),
+                                          "p99_ms": float(np.percentile(lat[sel], 99)),
+                                          "deadline_met": float((lat[sel] <= DEADLINE_MS).mean())}
+            runs.append({"offered_frames_s": rate, "frames": n, "completed_frames_s": n / wall,
+                         "mbit_s": bits / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "deadline_met": float((lat <= DEADLINE_MS).mean()),
+                         "queue_p99_ms": float(np.percentile((adm - arr) * 1e-6, 99)),
+                         "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()), "by_antennas": by_ant})
+        stats = srv.stats()
+    finally:
+        srv.close()
+    head = runs[0]
+    line = {"metric": "served Zak-OTFS frames/s + p50/p99 latency vs 0.5 ms deadline", "value": head["completed_frames_s"],
+            "unit": "frames/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "duration_s": args.duration, "pool_frames_per_class": args.pool,
+                       "max_wave_frames": args.wave_frames, "waves_in_flight": args.waves},
+            "runs": runs, "server_stats": stats}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,11 +508,21 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=48, help="oracle sample for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=8, help="oracle frames per step with --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve"],
+                    help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop")
+    ap.add_argument("--rates", type=lambda v: [float(x) for x in v.split(",")], default=[200000.0, 20000.0],
+                    help="serve: offered frames/s, one run each")
+    ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals per rate")
+    ap.add_argument("--pool", type=int, default=2, help="serve: synthetic frames per (M, N, antennas, QAM) class")
+    ap.add_argument("--wave-frames", type=int, default=256, help="serve: frames admitted per wave")
+    ap.add_argument("--waves", type=int, default=4, help="serve: waves in flight")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return impl_reference(args)
+    if args.workload == "serve":
+        return impl_serve(args)
     return impl_zotfs(args)
 
 

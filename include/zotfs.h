@@ -281,6 +281,47 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames,
 zotfs_status zotfs_rx_batch(zotfs_batch batch, int32_t* status, zotfs_stream stream);
 zotfs_status zotfs_batch_destroy(zotfs_batch batch);
 
+/* ------------------------------------------------- CUDA graphs and autotuning ---- */
+
+/* An instantiated CUDA graph of one batch run (the persistent kernel of every bucket, with
+ * its counter reset and the fork/join between the batch's streams).  Replaying it costs one
+ * graph launch instead of a memset, a kernel launch and two events per bucket.  Not in the
+ * paper. */
+typedef struct zotfs_graph_s* zotfs_graph;
+
+/* Capture zotfs_rx_batch(batch, status, .) on a private stream (thread-local capture mode)
+ * and instantiate it.  The batch, its descriptors' buffers and `status` must outlive the
+ * graph; the batch must not run elsewhere while the graph runs.  Allocates. */
+zotfs_status zotfs_batch_capture(zotfs_batch batch, int32_t* status, zotfs_graph* out);
+/* Replay the graph on `stream` (stream-ordered, no host synchronisation). */
+zotfs_status zotfs_graph_launch(zotfs_graph graph, zotfs_stream stream);
+zotfs_status zotfs_graph_destroy(zotfs_graph graph);
+
+typedef struct zotfs_autotune_opts {
+  int32_t warmup;      /* untimed runs per candidate; 0: 2 */
+  int32_t reps;        /* timed runs per candidate; 0: 5 */
+  int32_t max_frames;  /* frames of each shape group used for timing; 0: all */
+} zotfs_autotune_opts;
+
+typedef struct zotfs_tuning_result {
+  zotfs_tuning_entry best;  /* the fastest launch shape of one (M, N, n_rx, n_tx) group */
+  float ms_best;            /* mean time of one run of the group's frames with it */
+  float ms_default;         /* the same with the library's default launch shape */
+  int32_t n_candidates;     /* launch shapes timed */
+  int32_t n_frames;         /* frames of the group that were timed */
+} zotfs_tuning_result;
+
+/* The autotuner.  Groups `descs` by (M, N, n_rx, n_tx); for each group enumerates every
+ * launch shape that fits -- threads per frame (M <= T, T | MN, one of the compiled rows-per-
+ * thread variants), FFT radix 2 or 4, and CTAs per SM from 1 to the occupancy limit (the
+ * number of frames each SM works on at once) -- builds a batch of the group's frames for
+ * each, times `reps` runs with CUDA events on `stream` after `warmup` runs, and returns the
+ * fastest per group in out[0 .. *n_out) (at most max_out groups; ZOTFS_EINVAL if there are
+ * more).  The results go into zotfs_batch_opts.tuning.  It runs the receiver on the
+ * descriptors' buffers, so their outputs are overwritten.  Synchronises `stream`; allocates. */
+zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const zotfs_autotune_opts* opts,
+                            zotfs_tuning_result* out, int max_out, int* n_out, zotfs_stream stream);
+
 /* ------------------------------------------------------------------- serving ---- */
 
 /* A request loop on one GPU with continuous batching.  Frames of mixed shapes, antenna

@@ -25,7 +25,8 @@ from ._zotfs import (ZotfsError, OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEO
                      ENONFINITE, STATUS_NAMES, C64, C32_F16, C32_BF16, C128, COMPUTE_FP32, COMPUTE_FP64,
                      PILOT_SEPARATE, PILOT_EMBEDDED, PULSE_SINC, PULSE_RECT)
 
-__all__ = ["Plan", "Paths", "Batch", "Server", "ZotfsError", "library_path", "launch_count"]
+__all__ = ["Plan", "Paths", "Batch", "Graph", "Server", "ZotfsError", "autotune", "save_tuning", "load_tuning",
+           "library_path", "launch_count"]
 
 _DTYPES = {C64: torch.complex64, C32_F16: torch.float16, C32_BF16: torch.bfloat16, C128: torch.complex128}
 
@@ -219,21 +220,28 @@ class Batch:
 
     _PTR_FIELDS = ("y_pilot", "y_data", "x_hat", "llr", "bits", "path_count", "path_dk", "path_dl", "path_h")
 
-    def __init__(self, frames, threads_per_frame=0, ctas_per_sm=0, fft_radix=0, tuning=None):
+    @classmethod
+    def descriptors(cls, frames):
+        """zotfs_frame_desc array for a list of frame dicts, and the tensors it points into."""
         n = len(frames)
         arr = (Z.zotfs_frame_desc * max(n, 1))()
-        self._keep = []
+        keep = []
         for i, fr in enumerate(frames):
             d = arr[i]
             d.K0 = d.L0 = -1
             for key, val in fr.items():
-                if key in self._PTR_FIELDS:
+                if key in cls._PTR_FIELDS:
                     if val is not None:
                         _need_cuda(val)
-                        self._keep.append(val)
+                        keep.append(val)
                         setattr(d, key, val.data_ptr())
                 else:
                     setattr(d, key, val)
+        return arr, keep
+
+    def __init__(self, frames, threads_per_frame=0, ctas_per_sm=0, fft_radix=0, tuning=None):
+        n = len(frames)
+        arr, self._keep = self.descriptors(frames)
         entries = tuning or []
         tarr = (Z.zotfs_tuning_entry * max(len(entries), 1))()
         for i, (shape, tun) in enumerate(entries):
@@ -259,6 +267,79 @@ class Batch:
         _need_cuda(status)
         Z.check(Z.zotfs_rx_batch(self._h, _p(status), _s(stream)))
         return status
+
+    def capture(self, status):
+        """A CUDA graph of one run of this batch (zotfs_batch_capture)."""
+        return Graph(self, status)
+
+
+class Graph:
+    """An instantiated CUDA graph of one batch run; ``launch`` replays it on a stream."""
+
+    def __init__(self, batch, status):
+        _need_cuda(status)
+        h = C.c_void_p()
+        Z.check(Z.zotfs_batch_capture(batch._h, _p(status), C.byref(h)))
+        self._h = h
+        self._keep = (batch, status)
+
+    def launch(self, stream=None):
+        Z.check(Z.zotfs_graph_launch(self._h, _s(stream)))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            Z.zotfs_graph_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(frames, warmup=0, reps=0, max_frames=0, stream=None):
+    """Time every launch shape per (M, N, n_rx, n_tx) group of ``frames`` (zotfs_autotune) and
+    return one dict per group: the shape, the chosen tuning, and the default and best times.
+    The frames' output tensors are overwritten."""
+    arr, keep = Batch.descriptors(frames)
+    groups = len({(f["M"], f["N"], f["n_rx"], f["n_tx"]) for f in frames})
+    res = (Z.zotfs_tuning_result * max(groups, 1))()
+    n = C.c_int(0)
+    opts = Z.zotfs_autotune_opts(warmup, reps, max_frames)
+    Z.check(Z.zotfs_autotune(arr, len(frames), C.byref(opts), res, groups, C.byref(n), _s(stream)))
+    out = []
+    for i in range(n.value):
+        r = res[i]
+        b = r.best
+        out.append({"M": b.M, "N": b.N, "n_rx": b.n_rx, "n_tx": b.n_tx,
+                    "threads_per_frame": b.tuning.threads_per_frame, "fft_radix": b.tuning.fft_radix,
+                    "ctas_per_sm": b.tuning.ctas_per_sm, "ms_best": r.ms_best, "ms_default": r.ms_default,
+                    "n_candidates": r.n_candidates, "n_frames": r.n_frames})
+    del keep
+    return out
+
+
+def save_tuning(path, results, device_name=None):
+    """Persist autotuner results as JSON (one entry per shape group)."""
+    import json
+    with open(path, "w") as fh:
+        json.dump({"format": "zotfs-tuning-1", "device": device_name, "entries": list(results)}, fh, indent=1)
+
+
+def load_tuning(path):
+    """Read a JSON tuning file into the ``tuning=`` argument of Batch: [((M, N, n_rx, n_tx), dict)]."""
+    import json
+    with open(path) as fh:
+        doc = json.load(fh)
+    if doc.get("format") != "zotfs-tuning-1":
+        raise ValueError(f"{path}: not a zotfs tuning file")
+    out = []
+    for e in doc["entries"]:
+        shape = (int(e["M"]), int(e["N"]), int(e["n_rx"]), int(e["n_tx"]))
+        out.append((shape, {k: int(e.get(k, 0)) for k in ("threads_per_frame", "fft_radix", "ctas_per_sm")}))
+    return out
 
 
 class Server:

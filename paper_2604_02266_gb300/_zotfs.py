@@ -65,6 +65,15 @@ class zotfs_batch_opts(C.Structure):
                 ("n_tuning", C.c_int32), ("tuning", C.POINTER(zotfs_tuning_entry))]
 
 
+class zotfs_autotune_opts(C.Structure):
+    _fields_ = [("warmup", C.c_int32), ("reps", C.c_int32), ("max_frames", C.c_int32)]
+
+
+class zotfs_tuning_result(C.Structure):
+    _fields_ = [("best", zotfs_tuning_entry), ("ms_best", C.c_float), ("ms_default", C.c_float),
+                ("n_candidates", C.c_int32), ("n_frames", C.c_int32)]
+
+
 class zotfs_server_opts(C.Structure):
     _fields_ = [("p_max", C.c_int32), ("max_wave_frames", C.c_int32), ("waves_in_flight", C.c_int32),
                 ("keep_llr", C.c_int32), ("arena_bytes", C.c_int64), ("max_M", C.c_int32), ("max_N", C.c_int32),
@@ -109,6 +118,11 @@ SIGNATURES = {
     "zotfs_batch_create": (_I, [C.POINTER(zotfs_frame_desc), _I, C.POINTER(zotfs_batch_opts), C.POINTER(_P)]),
     "zotfs_rx_batch": (_I, [_P, _P, _P]),
     "zotfs_batch_destroy": (_I, [_P]),
+    "zotfs_batch_capture": (_I, [_P, _P, C.POINTER(_P)]),
+    "zotfs_graph_launch": (_I, [_P, _P]),
+    "zotfs_graph_destroy": (_I, [_P]),
+    "zotfs_autotune": (_I, [C.POINTER(zotfs_frame_desc), _I, C.POINTER(zotfs_autotune_opts),
+                            C.POINTER(zotfs_tuning_result), _I, C.POINTER(_I), _P]),
     "zotfs_server_create": (_I, [C.POINTER(zotfs_server_opts), C.POINTER(_P)]),
     "zotfs_server_submit": (_I, [_P, C.POINTER(zotfs_request), _I]),
     "zotfs_server_replay": (_I, [_P, C.POINTER(zotfs_request), C.POINTER(C.c_double), _I]),
@@ -173,6 +187,10 @@ zotfs_equalize_static = _mk("zotfs_equalize_static")
 zotfs_batch_create = _mk("zotfs_batch_create")
 zotfs_rx_batch = _mk("zotfs_rx_batch")
 zotfs_batch_destroy = _mk("zotfs_batch_destroy")
+zotfs_batch_capture = _mk("zotfs_batch_capture")
+zotfs_graph_launch = _mk("zotfs_graph_launch")
+zotfs_graph_destroy = _mk("zotfs_graph_destroy")
+zotfs_autotune = _mk("zotfs_autotune")
 zotfs_server_create = _mk("zotfs_server_create")
 zotfs_server_submit = _mk("zotfs_server_submit")
 zotfs_server_replay = _mk("zotfs_server_replay")

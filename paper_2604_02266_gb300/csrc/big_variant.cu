@@ -1,4 +1,6 @@
 // Instantiations of the large-frame kernel (FP32; EW = rows per thread = MN / T).
+#include <mutex>
+
 #include "frame_big.cuh"
 #include "internal.h"
 
@@ -28,10 +30,27 @@ bool choose_big_cfg(int M, int N, int nrx, int ntx, int p_max, BigCfg& cfg) {
   return cfg.smem <= 227 * 1024;
 }
 
+// Raise a large-frame kernel's dynamic shared-memory limit to at least `smem` on the current
+// device; the limit only grows (see grant_smem of the frame kernels).
+static cudaError_t big_grant_smem(int EW, size_t smem) {
+  static std::mutex mu;
+  static int granted[3][64] = {{0}};
+  const int slot = EW == 8 ? 0 : (EW == 16 ? 1 : 2);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && granted[slot][dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(big_kern(EW), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev < 64) granted[slot][dev] = (int)smem;
+  return e;
+}
+
 cudaError_t big_launch(const BigCfg& cfg, const FrameArgs& A, int radix, int grid, char* scratch,
                        cudaStream_t stream) {
   BigKern k = big_kern(cfg.EW);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+  if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = big_grant_smem(cfg.EW, cfg.smem);
   if (e != cudaSuccess) return e;
   k<<<grid, cfg.T, cfg.smem, stream>>>(A, radix, scratch, cfg.slot_bytes);
   return cudaGetLastError();
@@ -39,7 +58,8 @@ cudaError_t big_launch(const BigCfg& cfg, const FrameArgs& A, int radix, int gri
 
 cudaError_t big_occupancy(const BigCfg& cfg, int& blocks) {
   BigKern k = big_kern(cfg.EW);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+  if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = big_grant_smem(cfg.EW, cfg.smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, cfg.T, cfg.smem);
 }

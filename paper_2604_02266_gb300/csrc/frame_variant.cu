@@ -1,5 +1,7 @@
 // One instantiation of the frame kernel, selected by ZOTFS_VARIANT at compile time so the
 // variants build in parallel.  The table in frame_table.cu lists them.
+#include <mutex>
+
 #include "frame_kernel.cuh"
 
 #ifndef ZOTFS_VARIANT
@@ -72,21 +74,31 @@ void VFUN(_info)(int& E, int& NB, int& TMAX, int& real_bytes) {
   real_bytes = (int)sizeof(V_R);
 }
 
-cudaError_t VFUN(_launch)(const FrameArgs& A, int radix, int grid, int T, size_t smem, cudaStream_t stream) {
-  static int configured_smem[64] = {0};  // per device: the max dynamic smem already granted
+// Raise the kernel's dynamic shared-memory limit to at least `smem` on the current device.
+// The limit only ever grows (a lower value set later would break launches that rely on the
+// higher one), and the server's scheduler thread launches concurrently with user threads.
+static cudaError_t grant_smem(size_t smem) {
+  static std::mutex mu;
+  static int granted[64] = {0};
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && configured_smem[dev] < (int)smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured_smem[dev] = (int)smem;
-  }
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 64 && granted[dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev < 64) granted[dev] = (int)smem;
+  return e;
+}
+
+cudaError_t VFUN(_launch)(const FrameArgs& A, int radix, int grid, int T, size_t smem, cudaStream_t stream) {
+  cudaError_t e = grant_smem(smem);
+  if (e != cudaSuccess) return e;
   frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB><<<grid, T, smem, stream>>>(A, radix);
   return cudaGetLastError();
 }
 
 cudaError_t VFUN(_occupancy)(int T, size_t smem, int& blocks) {
-  cudaError_t e = cudaFuncSetAttribute(kern(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = grant_smem(smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern(), T, smem);
 }

@@ -296,7 +296,10 @@ zotfs_status run_plain(zotfs_plan_s* plan, const void* y_pilot_td, const void* y
   void (*compact)(const FrameArgs, const float2*, int, int, int, PathRec*, int*, int*, int) =
       EQ == 1 ? plain_compact_kernel<1> : EQ == 2 ? plain_compact_kernel<2> : EQ == 4 ? plain_compact_kernel<4>
       : EQ == 8 ? plain_compact_kernel<8> : plain_compact_kernel<16>;
-  cudaError_t e = cudaFuncSetAttribute(compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+  // above the default 48 KB only when MN >= 8192, where Tc = 1024 fixes csmem per instance
+  cudaError_t e = csmem > 48 * 1024
+                      ? cudaFuncSetAttribute(compact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem)
+                      : cudaSuccess;
   if (e != cudaSuccess) return cuda_fail(e, "plain compact smem");
   const float inv_sqrtN = (float)(1.0 / std::sqrt((double)N));
   const int nx = ntx * MN;

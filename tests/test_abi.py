@@ -57,6 +57,8 @@ def test_struct_layouts_match_header_sizes(libpath):
     assert ctypes.sizeof(Z.zotfs_tuning) == 12
     assert ctypes.sizeof(Z.zotfs_frame_desc) == 15 * 4 + 4 + 9 * 8  # 15 scalars, pad, 9 pointers
     assert ctypes.sizeof(Z.zotfs_batch_opts) == 4 * 4 + 8
+    assert ctypes.sizeof(Z.zotfs_autotune_opts) == 12
+    assert ctypes.sizeof(Z.zotfs_tuning_result) == 4 * 4 + 12 + 4 * 4
 
 
 def test_argument_errors_without_gpu(libpath):
@@ -76,3 +78,13 @@ def test_argument_errors_without_gpu(libpath):
     out = ctypes.c_void_p()
     assert Z.zotfs_batch_create(d, 1, None, ctypes.byref(out)) == Z.EINVAL
     assert b"qam" in Z.zotfs_last_error()
+    assert Z.zotfs_batch_capture(None, None, ctypes.byref(out)) == Z.EINVAL
+    assert Z.zotfs_graph_launch(None, None) == Z.EINVAL
+    assert Z.zotfs_graph_destroy(None) == Z.OK
+    n = ctypes.c_int(7)
+    assert Z.zotfs_autotune(d, 1, None, None, 0, None, None) == Z.EINVAL  # n_out NULL
+    assert Z.zotfs_autotune(d, 1, None, None, 1, ctypes.byref(n), None) == Z.EINVAL  # out NULL
+    assert n.value == 0
+    bad = Z.zotfs_autotune_opts(-1, 0, 0)
+    res = (Z.zotfs_tuning_result * 1)()
+    assert Z.zotfs_autotune(d, 1, ctypes.byref(bad), res, 1, ctypes.byref(n), None) == Z.EINVAL

@@ -1,0 +1,159 @@
+"""GPU tests of CUDA-graph launches (zotfs_batch_capture / zotfs_graph_launch, and zotfs_rx
+captured by torch.cuda.CUDAGraph) and of the launch-shape autotuner (zotfs_autotune) with its
+JSON persistence.  A replayed graph gives bitwise the results of the eager call; a batch
+built with tuned launch shapes still matches the FP64 oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from tests.gpu_util import TOL_LLR, TOL_X, dev, to_dev
+from tests.test_gpu_rx import _check_frames
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+def _frames(shapes, n, seed, in_dtype=0):
+    """n frames cycling through `shapes` (M, N, n_rx, n_tx, Q) with their output tensors."""
+    g = np.random.default_rng(seed)
+    frames, keep = [], []
+    for i in range(n):
+        M, N, nrx, ntx, Q = shapes[i % len(shapes)]
+        b = synth.fractional_batch(1, seed=seed * 100 + i, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx,
+                                   snr_db=(int(g.integers(0, 31)),))
+        bps = int(np.log2(Q))
+        o = {"x": torch.zeros(ntx, M * N, dtype=torch.complex64, device=dev()),
+             "llr": torch.zeros(ntx, M * N, bps, device=dev()),
+             "bits": torch.zeros(ntx, M * N * bps // 8, dtype=torch.uint8, device=dev()),
+             "pc": torch.zeros(nrx * ntx, dtype=torch.int32, device=dev()),
+             "pdk": torch.zeros(nrx * ntx * 64, dtype=torch.int16, device=dev()),
+             "pdl": torch.zeros(nrx * ntx * 64, dtype=torch.int16, device=dev()),
+             "ph": torch.zeros(nrx * ntx * 64, dtype=torch.complex64, device=dev())}
+        yp, yd = to_dev(b["y_pilot_td"][0]), to_dev(b["y_data_td"][0])
+        frames.append(dict(M=M, N=N, n_rx=nrx, n_tx=ntx, qam=Q, iters=10, pilot_mode=0, guard=2, p_max=64,
+                           in_dtype=in_dtype, noise_var=float(b["noise_var"][0]), theta=float(b["theta"][0]),
+                           a_pilot=float(b["a_pilot"]), y_pilot=yp, y_data=yd, x_hat=o["x"], llr=o["llr"],
+                           bits=o["bits"], path_count=o["pc"], path_dk=o["pdk"], path_dl=o["pdl"], path_h=o["ph"]))
+        keep.append((b, o))
+    return frames, keep
+
+
+def _snapshot(keep):
+    return [{k: v.clone() for k, v in o.items()} for _, o in keep]
+
+
+def _zero(keep):
+    for _, o in keep:
+        for v in o.values():
+            v.zero_()
+
+
+SHAPES = [(64, 32, 1, 1, 16), (32, 16, 2, 2, 4), (128, 16, 1, 1, 64), (16, 16, 4, 4, 16)]
+
+
+def test_batch_graph_replay_equals_eager():
+    from paper_2604_02266_gb300 import Batch
+    frames, keep = _frames(SHAPES, 24, seed=31)
+    batch = Batch(frames)
+    status = torch.full((len(frames),), -1, dtype=torch.int32, device=dev())
+    batch.run(status)
+    torch.cuda.synchronize()
+    eager, st_eager = _snapshot(keep), status.clone()
+    _zero(keep)
+    status.fill_(-1)
+    graph = batch.capture(status)
+    try:
+        for rep in range(3):  # every replay rewrites the same outputs
+            graph.launch()
+            torch.cuda.synchronize()
+            assert torch.equal(status, st_eager), rep
+            for i, (_, o) in enumerate(keep):
+                for key in o:
+                    assert torch.equal(o[key], eager[i][key]), (rep, i, key)
+            _zero(keep)
+            status.fill_(-1)
+    finally:
+        graph.close()
+
+
+def test_plan_rx_in_torch_cuda_graph():
+    """zotfs_rx is stream-ordered without host synchronisation or allocation, so a caller
+    can capture it in its own CUDA graph; new inputs copied into the static buffers are
+    picked up by each replay."""
+    from paper_2604_02266_gb300 import Plan
+    M, N, Q, F = 64, 32, 16, 16
+    b1 = synth.fractional_batch(F, seed=41, M=M, N=N, Q=Q)
+    b2 = synth.fractional_batch(F, seed=42, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    yp, yd = to_dev(b1["y_pilot_td"]), to_dev(b1["y_data_td"])
+    nv, th = to_dev(b1["noise_var"]), to_dev(b1["theta"])
+    out = plan._rx_outputs(F, dev(), True, True, True)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside the capture
+        plan.rx(yp, yd, nv, th, 10, F, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.rx(yp, yd, nv, th, 10, F, out=out)
+    for b in (b2, b1):
+        yp.copy_(to_dev(b["y_pilot_td"]))
+        yd.copy_(to_dev(b["y_data_td"]))
+        nv.copy_(to_dev(b["noise_var"]))
+        th.copy_(to_dev(b["theta"]))
+        g.replay()
+        torch.cuda.synchronize()
+        ref = Plan(M, N, 1, 1, Q).rx(to_dev(b["y_pilot_td"]), to_dev(b["y_data_td"]), to_dev(b["noise_var"]),
+                                     to_dev(b["theta"]), 10, F, want_paths=True, want_x=True, want_llr=True)
+        torch.cuda.synchronize()
+        got = dict(zip(("paths", "x_hat", "llr", "bits", "status"), out))
+        for key in ("x_hat", "llr", "bits", "status"):
+            assert torch.equal(got[key], ref[key]), key
+        assert torch.equal(got["paths"].count, ref["paths"].count)
+
+
+def test_autotune_json_roundtrip_and_tuned_parity(tmp_path):
+    from paper_2604_02266_gb300 import Batch, autotune, load_tuning, save_tuning
+    shapes = [(64, 32, 1, 1, 16), (32, 16, 2, 2, 16)]
+    frames, keep = _frames(shapes, 16, seed=51)
+    res = autotune(frames, warmup=1, reps=2)
+    assert len(res) == 2
+    for r in res:
+        assert (r["M"], r["N"], r["n_rx"], r["n_tx"], 16) in shapes
+        assert r["n_candidates"] >= 2 and r["n_frames"] == 8
+        assert 0 < r["ms_best"] <= r["ms_default"]
+        assert r["fft_radix"] in (0, 2, 4) and r["ctas_per_sm"] >= 0 and r["threads_per_frame"] >= 0
+        if r["threads_per_frame"]:
+            assert r["threads_per_frame"] % r["M"] == 0 and (r["M"] * r["N"]) % r["threads_per_frame"] == 0
+    path = tmp_path / "tuning.json"
+    save_tuning(str(path), res, torch.cuda.get_device_name())
+    tuning = load_tuning(str(path))
+    assert [t[0] for t in tuning] == [(r["M"], r["N"], r["n_rx"], r["n_tx"]) for r in res]
+    _zero(keep)
+    batch = Batch(frames, tuning=tuning)
+    status = torch.full((len(frames),), -1, dtype=torch.int32, device=dev())
+    batch.run(status)
+    torch.cuda.synchronize()
+    assert set(status.cpu().numpy().tolist()) <= {0, 6}
+    from paper_2604_02266_gb300 import Paths
+    for i in (0, 1, 2, 3):
+        b, o = keep[i]
+        M, N, nrx, ntx, Q = shapes[i % 2]
+        paths = Paths(nrx * ntx, 64, device=dev())
+        paths.count.copy_(o["pc"])
+        paths.dk.copy_(o["pdk"])
+        paths.dl.copy_(o["pdl"])
+        paths.h.copy_(o["ph"])
+        out = {"paths": paths, "x_hat": o["x"][None], "llr": o["llr"][None], "bits": o["bits"][None]}
+        wx, wl, mm = _check_frames(b, out, [0], M, N, nrx, ntx, Q, 10, 64)
+        assert wx < TOL_X and wl < TOL_LLR and mm == 0, (i, wx, wl, mm)
