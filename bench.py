@@ -410,10 +410,13 @@ def impl_serve(args):
     import synth
     from paper_2604_02266_gb300 import Server
 
-    classes = [(m, n, a, q) for m in SERVE_M for n in SERVE_N for a in SERVE_ANT for q in SERVE_Q]
+    if args.serve_mix == "c2":  # the headline frame shape only: 64x32 SISO 16-QAM, 6 paths
+        classes, n_paths = [(M, N, 1, Q)], 6
+    else:
+        classes, n_paths = [(m, n, a, q) for m in SERVE_M for n in SERVE_N for a in SERVE_ANT for q in SERVE_Q], 8
     pool = {}
     for ci, (m, n, a, q) in enumerate(classes):
-        b = synth.fractional_batch(args.pool, seed=SEED + 7919 * ci, M=m, N=n, Q=q, n_rx=a, n_tx=a, n_paths=8)
+        b = synth.fractional_batch(args.pool, seed=SEED + 7919 * ci, M=m, N=n, Q=q, n_rx=a, n_tx=a, n_paths=n_paths)
         pool[(m, n, a, q)] = (torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev),
                               b["noise_var"].astype(float), b["theta"].astype(float))
     srv = Server(p_max=64, max_wave_frames=args.wave_frames, waves_in_flight=args.waves, keep_llr=False,
@@ -485,12 +488,109 @@ def impl_serve(args):
     finally:
         srv.close()
     head = runs[0]
+    workload = SERVE_WORKLOAD if args.serve_mix == "c5" else (
+        "serving loop: Poisson arrivals of 64x32 SISO 16-QAM frames, separate pilot frame, 6-path fractional "
+        "channel, SNR 0..30 dB, 10 CG iterations, 0.5 ms deadline from arrival")
     line = {"metric": "served Zak-OTFS frames/s + p50/p99 latency vs 0.5 ms deadline", "value": head["completed_frames_s"],
             "unit": "frames/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": SERVE_WORKLOAD, "duration_s": args.duration, "pool_frames_per_class": args.pool,
-                       "max_wave_frames": args.wave_frames, "waves_in_flight": args.waves},
+            "config": {"workload": workload, "mix": args.serve_mix, "duration_s": args.duration,
+                       "pool_frames_per_class": args.pool, "max_wave_frames": args.wave_frames,
+                       "waves_in_flight": args.waves},
             "runs": runs, "server_stats": stats}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------- mixed-precision uneven batch
+
+MIXED_M, MIXED_N = (32, 64, 128), (16, 32, 64)
+MIXED_FRAMES = 8192
+
+
+def impl_mixed(args):
+    """8192 frames of uneven shapes (M in {32,64,128} x N in {16,32,64}, SISO or 2x2 with
+    probability 1/2), received frames stored FP16 or BF16, one uneven batch per storage type:
+    autotuned launch shapes, and the whole batch replayed as one CUDA graph per step."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import C32_BF16, C32_F16, Batch, autotune, save_tuning
+
+    g = np.random.default_rng(SEED)
+    cls = [(int(g.choice(MIXED_M)), int(g.choice(MIXED_N)), 1 if g.random() < 0.5 else 2) for _ in range(MIXED_FRAMES)]
+    groups = {}
+    for i, c in enumerate(cls):
+        groups.setdefault(c, []).append(i)
+    data = {}
+    for gi, (c, ids) in enumerate(sorted(groups.items())):
+        m, n, a = c
+        data[c] = synth.fractional_batch(len(ids), seed=SEED + 104729 * gi, M=m, N=n, Q=Q, n_rx=a, n_tx=a)
+    out = {"storage": {}}
+    for name, code, tdt in (("fp16", C32_F16, torch.float16), ("bf16", C32_BF16, torch.bfloat16)):
+        frames, keep = [], []
+        for c, ids in sorted(groups.items()):
+            m, n, a = c
+            b = data[c]
+            yp = torch.view_as_real(torch.from_numpy(b["y_pilot_td"])).to(tdt).to(dev).contiguous()
+            yd = torch.view_as_real(torch.from_numpy(b["y_data_td"])).to(tdt).to(dev).contiguous()
+            bits = torch.zeros(len(ids), a, m * n * int(np.log2(Q)) // 8, dtype=torch.uint8, device=dev)
+            keep += [yp, yd, bits]
+            for j in range(len(ids)):
+                frames.append(dict(M=m, N=n, n_rx=a, n_tx=a, qam=Q, iters=ITERS, pilot_mode=0, guard=2, p_max=64,
+                                   in_dtype=code, noise_var=float(b["noise_var"][j]), theta=float(b["theta"][j]),
+                                   a_pilot=float(b["a_pilot"]), y_pilot=yp[j], y_data=yd[j], bits=bits[j]))
+        status = torch.zeros(len(frames), dtype=torch.int32, device=dev)
+        tuning = autotune(frames, warmup=1, reps=3, max_frames=args.tune_frames)
+        if args.tuning_file:
+            save_tuning(args.tuning_file.replace("{dtype}", name), tuning, torch.cuda.get_device_name(dev))
+        entries = [((t["M"], t["N"], t["n_rx"], t["n_tx"]), t) for t in tuning]
+
+        def timed(run, steps):
+            for _ in range(args.warmup):
+                run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                run()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps
+
+        plain_batch = Batch(frames)
+        ms_default = timed(lambda: plain_batch.run(status), args.mixed_steps)
+        del plain_batch
+        tuned = Batch(frames, tuning=entries)
+        ms_eager = timed(lambda: tuned.run(status), args.mixed_steps)
+        graph = tuned.capture(status)
+        ms_graph = timed(graph.launch, args.mixed_steps)
+        st = status.cpu().numpy()
+        graph.close()
+        bits_per_step = sum(len(ids) * a * m * n * int(np.log2(Q)) for (m, n, a), ids in groups.items())
+        out["storage"][name] = {
+            "frames_s": len(frames) / ms_graph * 1e3, "mbit_s": bits_per_step / ms_graph / 1e3,
+            "ms_per_step_graph": ms_graph, "ms_per_step_tuned_eager": ms_eager, "ms_per_step_default_eager": ms_default,
+            "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()),
+            "tuning": [{k: t[k] for k in ("M", "N", "n_rx", "n_tx", "threads_per_frame", "fft_radix", "ctas_per_sm",
+                                          "ms_best", "ms_default")} for t in tuning]}
+        del tuned, frames, keep
+    head = out["storage"]["fp16"]
+    line = {"metric": "equalized Zak-OTFS frames/s, uneven mixed-precision batch", "value": head["frames_s"],
+            "unit": "frames/s", "n_gpus": 1, "steps": args.mixed_steps, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step_graph"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 compute, fp16/bf16 storage", "data": "synthetic",
+            "config": {"workload": "8192 frames, M in {32,64,128} x N in {16,32,64} uniform, SISO or 2x2 with "
+                                   "probability 1/2, 16-QAM, 6-path fractional channels, SNR 0..30 dB, 10 CG "
+                                   "iterations, frames stored FP16 / BF16, autotuned launch shapes, one CUDA graph "
+                                   "per step", "frames": MIXED_FRAMES, "classes": len(groups)},
+            **out}
     print(json.dumps(line))
     return 0
 
@@ -508,12 +608,18 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=48, help="oracle sample for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=8, help="oracle frames per step with --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve"],
-                    help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop")
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed"],
+                    help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
+                         "mixed: the uneven FP16/BF16 batch under CUDA graphs")
+    ap.add_argument("--mixed-steps", type=int, default=20, help="mixed: timed steps per storage type")
+    ap.add_argument("--tune-frames", type=int, default=64, help="mixed: frames per shape group the autotuner times")
+    ap.add_argument("--tuning-file", default="", help="mixed: write the autotuner's JSON here ({dtype} expands)")
     ap.add_argument("--rates", type=lambda v: [float(x) for x in v.split(",")], default=[200000.0, 20000.0],
                     help="serve: offered frames/s, one run each")
     ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--pool", type=int, default=2, help="serve: synthetic frames per (M, N, antennas, QAM) class")
+    ap.add_argument("--serve-mix", default="c5", choices=["c5", "c2"],
+                    help="serve: c5 = mixed shapes/antennas/QAM, c2 = 64x32 SISO 16-QAM frames only")
     ap.add_argument("--wave-frames", type=int, default=256, help="serve: frames admitted per wave")
     ap.add_argument("--waves", type=int, default=4, help="serve: waves in flight")
     args = ap.parse_args()
@@ -523,6 +629,8 @@ def main():
         return impl_reference(args)
     if args.workload == "serve":
         return impl_serve(args)
+    if args.workload == "mixed":
+        return impl_mixed(args)
     return impl_zotfs(args)
 
 
