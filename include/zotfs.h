@@ -264,6 +264,7 @@ typedef struct zotfs_batch_opts {
   int32_t fft_radix;          /* 0: per-bucket choice, else 2 or 4 */
   int32_t n_tuning;           /* entries in `tuning` (host array, read during create only) */
   const zotfs_tuning_entry* tuning;
+  int32_t max_sms;            /* SMs the batch's grids are sized for; 0: all of the device's */
 } zotfs_batch_opts;
 
 /* Build a batch from host descriptors: validates every frame, groups frames into buckets
@@ -317,8 +318,11 @@ typedef struct zotfs_tuning_result {
  * number of frames each SM works on at once) -- builds a batch of the group's frames for
  * each, times `reps` runs with CUDA events on `stream` after `warmup` runs, and returns the
  * fastest per group in out[0 .. *n_out) (at most max_out groups; ZOTFS_EINVAL if there are
- * more).  The results go into zotfs_batch_opts.tuning.  It runs the receiver on the
- * descriptors' buffers, so their outputs are overwritten.  Synchronises `stream`; allocates. */
+ * more).  Each group is timed on the share of the SMs that zotfs_batch_create would give it
+ * in a batch of all of `descs` (its share of the work, scaled down with the frames when
+ * max_frames samples the group), so it is tuned at the frames-per-SM it will run at.  The
+ * results go into zotfs_batch_opts.tuning.  It runs the receiver on the descriptors'
+ * buffers, so their outputs are overwritten.  Synchronises `stream`; allocates. */
 zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const zotfs_autotune_opts* opts,
                             zotfs_tuning_result* out, int max_out, int* n_out, zotfs_stream stream);
 

@@ -239,7 +239,7 @@ class Batch:
                     setattr(d, key, val)
         return arr, keep
 
-    def __init__(self, frames, threads_per_frame=0, ctas_per_sm=0, fft_radix=0, tuning=None):
+    def __init__(self, frames, threads_per_frame=0, ctas_per_sm=0, fft_radix=0, tuning=None, max_sms=0):
         n = len(frames)
         arr, self._keep = self.descriptors(frames)
         entries = tuning or []
@@ -248,7 +248,7 @@ class Batch:
             tarr[i].M, tarr[i].N, tarr[i].n_rx, tarr[i].n_tx = shape
             tarr[i].tuning = Z.zotfs_tuning(tun.get("threads_per_frame", 0), tun.get("fft_radix", 0),
                                             tun.get("ctas_per_sm", 0))
-        opts = Z.zotfs_batch_opts(threads_per_frame, ctas_per_sm, fft_radix, len(entries), tarr)
+        opts = Z.zotfs_batch_opts(threads_per_frame, ctas_per_sm, fft_radix, len(entries), tarr, max_sms)
         h = C.c_void_p()
         Z.check(Z.zotfs_batch_create(arr, n, C.byref(opts), C.byref(h)))
         self._h = h

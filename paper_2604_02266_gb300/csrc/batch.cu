@@ -56,6 +56,13 @@ static zotfs_status binval(const std::string& m) {
   return ZOTFS_EINVAL;
 }
 
+// Work model of one frame for sizing the buckets' grids: the gathers of the CG (two applies
+// per iteration and one for b, over all antenna pairs and up to p_max paths) plus the
+// transforms.
+double frame_work(const zotfs_frame_desc& d) {
+  return (double)d.M * d.N * d.n_rx * d.n_tx * d.p_max * (2.0 * d.iters + 1.0) + 8.0 * d.M * d.N;
+}
+
 zotfs_status make_shape_tables(int M, int N, float2** dW, float2** dTab) {
   const int MN = M * N;
   std::vector<float2> W(MN), Tab(MN);
@@ -141,6 +148,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
   if (opts) o = *opts;
   if (o.fft_radix != 0 && o.fft_radix != 2 && o.fft_radix != 4) return binval("fft_radix must be 0, 2 or 4");
   if (o.n_tuning < 0 || (o.n_tuning > 0 && !o.tuning)) return binval("tuning table");
+  if (o.max_sms < 0) return binval("max_sms < 0");
 
   std::vector<zotfs_frame_desc> D(descs, descs + n_frames);
   for (int i = 0; i < n_frames; ++i) {
@@ -195,8 +203,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     }
     Bucket& B = b->buckets[bi];
     B.ids.push_back(i);
-    // work model: gathers of the CG (2 applies per iteration over all antenna pairs)
-    B.work += (double)d.M * d.N * d.n_rx * d.n_tx * d.p_max * (2.0 * d.iters + 1.0) + 8.0 * d.M * d.N;
+    B.work += frame_work(d);
   }
 
   // per-bucket kernel configuration
@@ -240,11 +247,12 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     total_work += B.work;
   }
   // grids: each bucket gets SMs in proportion to its work (at least one CTA)
+  const int avail = o.max_sms > 0 ? std::min(o.max_sms, b->sm_count) : b->sm_count;
   for (size_t bi = 0; bi < b->buckets.size() && st == ZOTFS_OK; ++bi) {
     Bucket& B = b->buckets[bi];
     const double share = total_work > 0 ? B.work / total_work : 1.0;
-    int sms = (int)std::ceil(share * b->sm_count);
-    sms = std::max(1, std::min(sms, b->sm_count));
+    int sms = (int)std::ceil(share * avail);
+    sms = std::max(1, std::min(sms, avail));
     B.grid = std::max(1, std::min((int)B.ids.size(), sms * occ[bi]));
   }
   // device copies: descriptors, frame ids per bucket, counters, per-shape tables

@@ -81,6 +81,8 @@ cudaError_t big_occupancy(const BigCfg& cfg, int& blocks);
 // descriptors.
 void bucket_args(int M, int N, int nrx, int ntx, int pilot_mode, int guard, int p_max, int in_dtype, const float2* W,
                  const float2* Tab, FrameArgs& A);
+// Work model of one frame (grid sizing of uneven batches; the autotuner's SM shares).
+double frame_work(const zotfs_frame_desc& d);
 // Root-of-unity tables of one (M, N) shape in FP32 (allocates).
 zotfs_status make_shape_tables(int M, int N, float2** dW, float2** dTab);
 

@@ -1,6 +1,7 @@
 // CUDA-graph capture of a batch run, and the launch-shape autotuner: both sit on top of the
 // batch API (zotfs_batch_create / zotfs_rx_batch) and add no device code of their own.
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <string>
 #include <tuple>
@@ -50,12 +51,13 @@ std::vector<Candidate> candidates(int M, int N, int nrx, int ntx, int p_max) {
 
 // Mean milliseconds of one zotfs_rx_batch run of `D` with the given launch shape, or < 0 on
 // failure (the error string is kept).
-float time_shape(const std::vector<zotfs_frame_desc>& D, const Candidate& c, int warmup, int reps,
+float time_shape(const std::vector<zotfs_frame_desc>& D, const Candidate& c, int max_sms, int warmup, int reps,
                  int32_t* d_status, cudaStream_t stream, cudaEvent_t e0, cudaEvent_t e1) {
   zotfs_batch_opts o{};
   o.threads_per_frame = c.threads;
   o.fft_radix = c.radix;
   o.ctas_per_sm = c.ctas;
+  o.max_sms = max_sms;
   zotfs_batch b = nullptr;
   if (zotfs_batch_create(D.data(), (int)D.size(), &o, &b) != ZOTFS_OK) return -1.f;
   float ms = -1.f;
@@ -145,9 +147,12 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
   const int warmup = o.warmup ? o.warmup : 2;
   const int reps = o.reps ? o.reps : 5;
 
-  // groups in order of first appearance
+  // groups in order of first appearance, with their share of the whole batch's work
   std::map<std::tuple<int, int, int, int>, int> key_to_group;
   std::vector<std::vector<zotfs_frame_desc>> groups;
+  std::vector<double> work;
+  std::vector<int> total;
+  double all_work = 0.0;
   for (int i = 0; i < n_frames; ++i) {
     const zotfs_frame_desc& d = descs[i];
     auto key = std::make_tuple(d.M, d.N, d.n_rx, d.n_tx);
@@ -155,11 +160,20 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     if (it == key_to_group.end()) {
       it = key_to_group.emplace(key, (int)groups.size()).first;
       groups.emplace_back();
+      work.push_back(0.0);
+      total.push_back(0);
     }
-    auto& G = groups[it->second];
-    if (o.max_frames == 0 || (int)G.size() < o.max_frames) G.push_back(d);
+    const int g = it->second;
+    work[g] += frame_work(d);
+    all_work += frame_work(d);
+    ++total[g];
+    if (o.max_frames == 0 || (int)groups[g].size() < o.max_frames) groups[g].push_back(d);
   }
   if ((int)groups.size() > max_out) return tinval("more shape groups than max_out");
+  int device = 0, sm_count = 0;
+  cudaError_t qe = cudaGetDevice(&device);
+  if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (qe != cudaSuccess) return cuda_fail(qe, "device query");
 
   int32_t* d_status = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -181,7 +195,11 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     R.best.n_rx = d0.n_rx;
     R.best.n_tx = d0.n_tx;
     R.n_frames = (int)G.size();
-    R.ms_default = time_shape(G, Candidate{0, 0, 0}, warmup, reps, d_status, stream, e0, e1);
+    // the SMs this group gets in the full batch, scaled to the frames timed
+    const double share = all_work > 0 ? work[gi] / all_work : 1.0;
+    const double sms_full = std::ceil(share * sm_count);
+    const int sms = std::max(1, std::min(sm_count, (int)std::lround(sms_full * G.size() / (double)total[gi])));
+    R.ms_default = time_shape(G, Candidate{0, 0, 0}, sms, warmup, reps, d_status, stream, e0, e1);
     if (R.ms_default < 0.f) {
       st = ZOTFS_EINVAL;
       set_error(std::string("autotune: default launch shape failed: ") + zotfs_last_error());
@@ -189,7 +207,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     }
     R.ms_best = R.ms_default;
     for (const Candidate& c : candidates(d0.M, d0.N, d0.n_rx, d0.n_tx, p_max)) {
-      const float ms = time_shape(G, c, warmup, reps, d_status, stream, e0, e1);
+      const float ms = time_shape(G, c, sms, warmup, reps, d_status, stream, e0, e1);
       ++R.n_candidates;
       if (ms >= 0.f && ms < R.ms_best) {
         R.ms_best = ms;
