@@ -252,10 +252,15 @@ typedef struct zotfs_frame_desc {
 
 typedef struct zotfs_batch_s* zotfs_batch;
 
-/* Launch shape for one bucket of an uneven batch (frames of equal M, N, n_rx, n_tx). */
+/* Launch shape for one bucket of an uneven batch (frames of equal M, N, n_rx, n_tx), and
+ * optionally its measured cost: SM-milliseconds per frame with that shape (the autotuner
+ * fills it in).  When every bucket of a batch has a cost > 0, the buckets' grids are sized
+ * in proportion to frames x cost instead of the library's work model, so buckets that run
+ * less efficiently per unit of work still finish together. */
 typedef struct zotfs_tuning_entry {
   int32_t M, N, n_rx, n_tx;
   zotfs_tuning tuning;
+  float cost;
 } zotfs_tuning_entry;
 
 typedef struct zotfs_batch_opts {

@@ -57,7 +57,7 @@ class zotfs_frame_desc(C.Structure):
 
 class zotfs_tuning_entry(C.Structure):
     _fields_ = [("M", C.c_int32), ("N", C.c_int32), ("n_rx", C.c_int32), ("n_tx", C.c_int32),
-                ("tuning", zotfs_tuning)]
+                ("tuning", zotfs_tuning), ("cost", C.c_float)]
 
 
 class zotfs_batch_opts(C.Structure):

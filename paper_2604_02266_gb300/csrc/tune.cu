@@ -216,6 +216,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
         R.best.tuning.ctas_per_sm = c.ctas;
       }
     }
+    R.best.cost = R.ms_best * (float)sms / (float)G.size();  // SM-ms per frame
     out[gi] = R;
     *n_out = (int)gi + 1;
   }
