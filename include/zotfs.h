@@ -314,20 +314,20 @@ typedef struct zotfs_tuning_result {
   float ms_best;            /* mean time of one run of the group's frames with it */
   float ms_default;         /* the same with the library's default launch shape */
   int32_t n_candidates;     /* launch shapes timed */
-  int32_t n_frames;         /* frames of the group that were timed */
+  int32_t n_frames;         /* frames in the group's timing set (repeats included) */
 } zotfs_tuning_result;
 
 /* The autotuner.  Groups `descs` by (M, N, n_rx, n_tx); for each group enumerates every
  * launch shape that fits -- threads per frame (M <= T, T | MN, one of the compiled rows-per-
  * thread variants), FFT radix 2 or 4, and CTAs per SM from 1 to the occupancy limit (the
- * number of frames each SM works on at once) -- builds a batch of the group's frames for
- * each, times `reps` runs with CUDA events on `stream` after `warmup` runs, and returns the
- * fastest per group in out[0 .. *n_out) (at most max_out groups; ZOTFS_EINVAL if there are
- * more).  Each group is timed on the share of the SMs that zotfs_batch_create would give it
- * in a batch of all of `descs` (its share of the work, scaled down with the frames when
- * max_frames samples the group), so it is tuned at the frames-per-SM it will run at.  The
- * results go into zotfs_batch_opts.tuning.  It runs the receiver on the descriptors'
- * buffers, so their outputs are overwritten.  Synchronises `stream`; allocates. */
+ * number of frames each SM works on at once) -- and times `reps` runs of each with CUDA
+ * events on `stream` after `warmup` runs.  Each group is timed in the throughput regime of a
+ * large batch: its frames (the first max_frames of them) are repeated to 8 frames per SM,
+ * reading the caller's received frames and writing hard bits to the tuner's own scratch, so
+ * the descriptors' outputs are not touched.  Returns the fastest shape per group, with its
+ * cost in SM-milliseconds per frame, in out[0 .. *n_out) (at most max_out groups;
+ * ZOTFS_EINVAL if there are more); the entries go into zotfs_batch_opts.tuning.
+ * Synchronises `stream`; allocates. */
 zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const zotfs_autotune_opts* opts,
                             zotfs_tuning_result* out, int max_out, int* n_out, zotfs_stream stream);
 

@@ -23,6 +23,9 @@ zotfs_status tinval(const std::string& m) {
   return ZOTFS_EINVAL;
 }
 
+// Frames per SM (per unit of occupancy, times two) in the autotuner's timing sets.
+constexpr int kTuneFramesPerSm = 4;
+
 struct Candidate {
   int threads, radix, ctas;
 };
@@ -147,12 +150,9 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
   const int warmup = o.warmup ? o.warmup : 2;
   const int reps = o.reps ? o.reps : 5;
 
-  // groups in order of first appearance, with their share of the whole batch's work
+  // groups in order of first appearance
   std::map<std::tuple<int, int, int, int>, int> key_to_group;
   std::vector<std::vector<zotfs_frame_desc>> groups;
-  std::vector<double> work;
-  std::vector<int> total;
-  double all_work = 0.0;
   for (int i = 0; i < n_frames; ++i) {
     const zotfs_frame_desc& d = descs[i];
     auto key = std::make_tuple(d.M, d.N, d.n_rx, d.n_tx);
@@ -160,26 +160,31 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     if (it == key_to_group.end()) {
       it = key_to_group.emplace(key, (int)groups.size()).first;
       groups.emplace_back();
-      work.push_back(0.0);
-      total.push_back(0);
     }
-    const int g = it->second;
-    work[g] += frame_work(d);
-    all_work += frame_work(d);
-    ++total[g];
-    if (o.max_frames == 0 || (int)groups[g].size() < o.max_frames) groups[g].push_back(d);
+    auto& G = groups[it->second];
+    if (o.max_frames == 0 || (int)G.size() < o.max_frames) G.push_back(d);
   }
   if ((int)groups.size() > max_out) return tinval("more shape groups than max_out");
   int device = 0, sm_count = 0;
-  cudaError_t qe = cudaGetDevice(&device);
-  if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device);
-  if (qe != cudaSuccess) return cuda_fail(qe, "device query");
+  cudaError_t e = cudaGetDevice(&device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
 
+  // Each group is timed in the throughput regime it runs at inside a large batch: its sampled
+  // frames are repeated until every SM holds several frames per resident CTA.  The repeats
+  // read the same received frames but write hard bits to the tuner's own scratch (no x_hat,
+  // LLR or path outputs), so the caller's outputs are left alone.
+  const int target = 2 * kTuneFramesPerSm * sm_count;
+  size_t most_bits = 0;
+  for (auto& G : groups)
+    for (const auto& d : G)
+      most_bits = std::max(most_bits, (size_t)d.n_tx * d.M * d.N * 6 / 8);
   int32_t* d_status = nullptr;
+  uint8_t* d_bits = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  size_t most = 0;
-  for (auto& G : groups) most = std::max(most, G.size());
-  cudaError_t e = cudaMalloc(&d_status, sizeof(int32_t) * std::max<size_t>(most, 1));
+  const size_t slot = (most_bits + 255) & ~size_t(255);
+  e = cudaMalloc(&d_status, sizeof(int32_t) * (size_t)target);
+  if (e == cudaSuccess && !groups.empty()) e = cudaMalloc(&d_bits, slot * (size_t)target);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   zotfs_status st = e == cudaSuccess ? ZOTFS_OK : cuda_fail(e, "autotune setup");
@@ -189,17 +194,23 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     const zotfs_frame_desc& d0 = G[0];
     int p_max = 0;
     for (const auto& d : G) p_max = std::max(p_max, d.p_max);
+    std::vector<zotfs_frame_desc> T(target);
+    for (int i = 0; i < target; ++i) {
+      T[i] = G[(size_t)i % G.size()];
+      T[i].x_hat = nullptr;
+      T[i].llr = nullptr;
+      T[i].path_count = nullptr;
+      T[i].path_dk = T[i].path_dl = nullptr;
+      T[i].path_h = nullptr;
+      T[i].bits = d_bits + (size_t)i * slot;
+    }
     zotfs_tuning_result R{};
     R.best.M = d0.M;
     R.best.N = d0.N;
     R.best.n_rx = d0.n_rx;
     R.best.n_tx = d0.n_tx;
-    R.n_frames = (int)G.size();
-    // the SMs this group gets in the full batch, scaled to the frames timed
-    const double share = all_work > 0 ? work[gi] / all_work : 1.0;
-    const double sms_full = std::ceil(share * sm_count);
-    const int sms = std::max(1, std::min(sm_count, (int)std::lround(sms_full * G.size() / (double)total[gi])));
-    R.ms_default = time_shape(G, Candidate{0, 0, 0}, sms, warmup, reps, d_status, stream, e0, e1);
+    R.n_frames = target;
+    R.ms_default = time_shape(T, Candidate{0, 0, 0}, 0, warmup, reps, d_status, stream, e0, e1);
     if (R.ms_default < 0.f) {
       st = ZOTFS_EINVAL;
       set_error(std::string("autotune: default launch shape failed: ") + zotfs_last_error());
@@ -207,7 +218,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     }
     R.ms_best = R.ms_default;
     for (const Candidate& c : candidates(d0.M, d0.N, d0.n_rx, d0.n_tx, p_max)) {
-      const float ms = time_shape(G, c, sms, warmup, reps, d_status, stream, e0, e1);
+      const float ms = time_shape(T, c, 0, warmup, reps, d_status, stream, e0, e1);
       ++R.n_candidates;
       if (ms >= 0.f && ms < R.ms_best) {
         R.ms_best = ms;
@@ -216,12 +227,13 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
         R.best.tuning.ctas_per_sm = c.ctas;
       }
     }
-    R.best.cost = R.ms_best * (float)sms / (float)G.size();  // SM-ms per frame
+    R.best.cost = R.ms_best * (float)sm_count / (float)target;  // SM-milliseconds per frame
     out[gi] = R;
     *n_out = (int)gi + 1;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  if (d_bits) cudaFree(d_bits);
   if (d_status) cudaFree(d_status);
   return st;
 }

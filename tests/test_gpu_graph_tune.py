@@ -130,7 +130,7 @@ def test_autotune_json_roundtrip_and_tuned_parity(tmp_path):
     assert len(res) == 2
     for r in res:
         assert (r["M"], r["N"], r["n_rx"], r["n_tx"], 16) in shapes
-        assert r["n_candidates"] >= 2 and r["n_frames"] == 8
+        assert r["n_candidates"] >= 2 and r["n_frames"] >= 8 * 16
         assert 0 < r["ms_best"] <= r["ms_default"] and r["cost"] > 0
         assert r["fft_radix"] in (0, 2, 4) and r["ctas_per_sm"] >= 0 and r["threads_per_frame"] >= 0
         if r["threads_per_frame"]:
