@@ -302,8 +302,9 @@ class Graph:
 
 def autotune(frames, warmup=0, reps=0, max_frames=0, stream=None):
     """Time every launch shape per (M, N, n_rx, n_tx) group of ``frames`` (zotfs_autotune) and
-    return one dict per group: the shape, the chosen tuning, and the default and best times.
-    The frames' output tensors are overwritten."""
+    return one dict per group: the shape, the chosen tuning, its cost (SM-ms per frame) and
+    the default and best times of the group's timing set.  The frames' outputs are not
+    written (the tuner writes to its own scratch)."""
     arr, keep = Batch.descriptors(frames)
     groups = len({(f["M"], f["N"], f["n_rx"], f["n_tx"]) for f in frames})
     res = (Z.zotfs_tuning_result * max(groups, 1))()
