@@ -579,7 +579,7 @@ def impl_mixed(args):
             "ms_per_step_graph": ms_graph, "ms_per_step_tuned_eager": ms_eager, "ms_per_step_default_eager": ms_default,
             "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()),
             "tuning": [{k: t[k] for k in ("M", "N", "n_rx", "n_tx", "threads_per_frame", "fft_radix", "ctas_per_sm",
-                                          "cost", "ms_best", "ms_default")} for t in tuning]}
+                                          "sm_ms_per_frame", "ms_best", "ms_default")} for t in tuning]}
         del tuned, frames, keep
     head = out["storage"]["fp16"]
     line = {"metric": "equalized Zak-OTFS frames/s, uneven mixed-precision batch", "value": head["frames_s"],

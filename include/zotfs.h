@@ -252,15 +252,10 @@ typedef struct zotfs_frame_desc {
 
 typedef struct zotfs_batch_s* zotfs_batch;
 
-/* Launch shape for one bucket of an uneven batch (frames of equal M, N, n_rx, n_tx), and
- * optionally its measured cost: SM-milliseconds per frame with that shape (the autotuner
- * fills it in).  When every bucket of a batch has a cost > 0, the buckets' grids are sized
- * in proportion to frames x cost instead of the library's work model, so buckets that run
- * less efficiently per unit of work still finish together. */
+/* Launch shape for one bucket of an uneven batch (frames of equal M, N, n_rx, n_tx). */
 typedef struct zotfs_tuning_entry {
   int32_t M, N, n_rx, n_tx;
   zotfs_tuning tuning;
-  float cost;
 } zotfs_tuning_entry;
 
 typedef struct zotfs_batch_opts {
@@ -313,6 +308,7 @@ typedef struct zotfs_tuning_result {
   zotfs_tuning_entry best;  /* the fastest launch shape of one (M, N, n_rx, n_tx) group */
   float ms_best;            /* mean time of one run of the group's frames with it */
   float ms_default;         /* the same with the library's default launch shape */
+  float sm_ms_per_frame;    /* ms_best x SMs / frames timed: the group's measured cost */
   int32_t n_candidates;     /* launch shapes timed */
   int32_t n_frames;         /* frames in the group's timing set (repeats included) */
 } zotfs_tuning_result;

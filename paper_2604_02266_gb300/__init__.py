@@ -248,7 +248,6 @@ class Batch:
             tarr[i].M, tarr[i].N, tarr[i].n_rx, tarr[i].n_tx = shape
             tarr[i].tuning = Z.zotfs_tuning(tun.get("threads_per_frame", 0), tun.get("fft_radix", 0),
                                             tun.get("ctas_per_sm", 0))
-            tarr[i].cost = float(tun.get("cost", 0.0))
         opts = Z.zotfs_batch_opts(threads_per_frame, ctas_per_sm, fft_radix, len(entries), tarr, max_sms)
         h = C.c_void_p()
         Z.check(Z.zotfs_batch_create(arr, n, C.byref(opts), C.byref(h)))
@@ -317,7 +316,7 @@ def autotune(frames, warmup=0, reps=0, max_frames=0, stream=None):
         b = r.best
         out.append({"M": b.M, "N": b.N, "n_rx": b.n_rx, "n_tx": b.n_tx,
                     "threads_per_frame": b.tuning.threads_per_frame, "fft_radix": b.tuning.fft_radix,
-                    "ctas_per_sm": b.tuning.ctas_per_sm, "cost": b.cost, "ms_best": r.ms_best,
+                    "ctas_per_sm": b.tuning.ctas_per_sm, "sm_ms_per_frame": r.sm_ms_per_frame, "ms_best": r.ms_best,
                     "ms_default": r.ms_default,
                     "n_candidates": r.n_candidates, "n_frames": r.n_frames})
     del keep
@@ -341,9 +340,7 @@ def load_tuning(path):
     out = []
     for e in doc["entries"]:
         shape = (int(e["M"]), int(e["N"]), int(e["n_rx"]), int(e["n_tx"]))
-        tun = {k: int(e.get(k, 0)) for k in ("threads_per_frame", "fft_radix", "ctas_per_sm")}
-        tun["cost"] = float(e.get("cost", 0.0))
-        out.append((shape, tun))
+        out.append((shape, {k: int(e.get(k, 0)) for k in ("threads_per_frame", "fft_radix", "ctas_per_sm")}))
     return out
 
 

@@ -57,7 +57,7 @@ class zotfs_frame_desc(C.Structure):
 
 class zotfs_tuning_entry(C.Structure):
     _fields_ = [("M", C.c_int32), ("N", C.c_int32), ("n_rx", C.c_int32), ("n_tx", C.c_int32),
-                ("tuning", zotfs_tuning), ("cost", C.c_float)]
+                ("tuning", zotfs_tuning)]
 
 
 class zotfs_batch_opts(C.Structure):
@@ -71,7 +71,7 @@ class zotfs_autotune_opts(C.Structure):
 
 class zotfs_tuning_result(C.Structure):
     _fields_ = [("best", zotfs_tuning_entry), ("ms_best", C.c_float), ("ms_default", C.c_float),
-                ("n_candidates", C.c_int32), ("n_frames", C.c_int32)]
+                ("sm_ms_per_frame", C.c_float), ("n_candidates", C.c_int32), ("n_frames", C.c_int32)]
 
 
 class zotfs_server_opts(C.Structure):

@@ -23,7 +23,6 @@ struct Bucket {
   float a_pilot;
   std::vector<int> ids;
   double work = 0.0;
-  double cost = 0.0;  // measured SM-milliseconds per frame (tuning table), 0 if unknown
   FrameCfg cfg{};
   int radix = 2;
   int ctas_per_sm = 0;
@@ -220,7 +219,6 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
         if (!o.threads_per_frame) tpf = te.tuning.threads_per_frame;
         if (!o.fft_radix) radix = te.tuning.fft_radix;
         if (!o.ctas_per_sm) cps = te.tuning.ctas_per_sm;
-        if (te.cost > 0.f && std::isfinite(te.cost)) B.cost = te.cost;
       }
     }
     B.radix = radix == 2 ? 2 : (radix == 4 ? 4 : kDefaultRadix);
@@ -249,16 +247,6 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     total_work += B.work;
   }
   // grids: each bucket gets SMs in proportion to its work (at least one CTA)
-  // measured costs replace the work model when every bucket has one
-  bool all_cost = st == ZOTFS_OK && !b->buckets.empty();
-  for (const Bucket& B : b->buckets) all_cost = all_cost && B.cost > 0.0;
-  if (all_cost) {
-    total_work = 0.0;
-    for (Bucket& B : b->buckets) {
-      B.work = B.cost * (double)B.ids.size();
-      total_work += B.work;
-    }
-  }
   const int avail = o.max_sms > 0 ? std::min(o.max_sms, b->sm_count) : b->sm_count;
   for (size_t bi = 0; bi < b->buckets.size() && st == ZOTFS_OK; ++bi) {
     Bucket& B = b->buckets[bi];

@@ -227,7 +227,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
         R.best.tuning.ctas_per_sm = c.ctas;
       }
     }
-    R.best.cost = R.ms_best * (float)sm_count / (float)target;  // SM-milliseconds per frame
+    R.sm_ms_per_frame = R.ms_best * (float)sm_count / (float)target;
     out[gi] = R;
     *n_out = (int)gi + 1;
   }

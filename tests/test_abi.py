@@ -58,8 +58,8 @@ def test_struct_layouts_match_header_sizes(libpath):
     assert ctypes.sizeof(Z.zotfs_frame_desc) == 15 * 4 + 4 + 9 * 8  # 15 scalars, pad, 9 pointers
     assert ctypes.sizeof(Z.zotfs_batch_opts) == 4 * 4 + 8 + 8  # int max_sms + tail padding
     assert ctypes.sizeof(Z.zotfs_autotune_opts) == 12
-    assert ctypes.sizeof(Z.zotfs_tuning_entry) == 4 * 4 + 12 + 4
-    assert ctypes.sizeof(Z.zotfs_tuning_result) == 4 * 4 + 12 + 4 + 4 * 4
+    assert ctypes.sizeof(Z.zotfs_tuning_entry) == 4 * 4 + 12
+    assert ctypes.sizeof(Z.zotfs_tuning_result) == 4 * 4 + 12 + 5 * 4
 
 
 def test_argument_errors_without_gpu(libpath):

@@ -131,7 +131,7 @@ def test_autotune_json_roundtrip_and_tuned_parity(tmp_path):
     for r in res:
         assert (r["M"], r["N"], r["n_rx"], r["n_tx"], 16) in shapes
         assert r["n_candidates"] >= 2 and r["n_frames"] >= 8 * 16
-        assert 0 < r["ms_best"] <= r["ms_default"] and r["cost"] > 0
+        assert 0 < r["ms_best"] <= r["ms_default"] and r["sm_ms_per_frame"] > 0
         assert r["fft_radix"] in (0, 2, 4) and r["ctas_per_sm"] >= 0 and r["threads_per_frame"] >= 0
         if r["threads_per_frame"]:
             assert r["threads_per_frame"] % r["M"] == 0 and (r["M"] * r["N"]) % r["threads_per_frame"] == 0
@@ -139,7 +139,6 @@ def test_autotune_json_roundtrip_and_tuned_parity(tmp_path):
     save_tuning(str(path), res, torch.cuda.get_device_name())
     tuning = load_tuning(str(path))
     assert [t[0] for t in tuning] == [(r["M"], r["N"], r["n_rx"], r["n_tx"]) for r in res]
-    assert [t[1]["cost"] for t in tuning] == pytest.approx([r["cost"] for r in res])
     _zero(keep)
     batch = Batch(frames, tuning=tuning)
     status = torch.full((len(frames),), -1, dtype=torch.int32, device=dev())
