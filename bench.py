@@ -190,6 +190,54 @@ def run_oracle(batch, frames):
     return time.perf_counter() - t0
 
 
+def _oracle_chunk(yp, yd, nv, th, a_pilot):
+    """Worker: the FP64 oracle receiver on a chunk of frames (returns the frame count)."""
+    from oracle import receiver
+    for f in range(len(yd)):
+        receiver.receive(yp[f], yd[f], M, N, 1, 1, Q, float(nv[f]), float(th[f]), ITERS, a_pilot, p_max=64)
+    return len(yd)
+
+
+class OraclePool:
+    """The FP64 oracle over frames on the host's cores: a pool of spawned worker processes,
+    one frame chunk each, single-threaded BLAS per worker.  Started before timing."""
+
+    def __init__(self, workers):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = workers
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.ex = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+            list(self.ex.map(abs, range(workers)))  # start every worker
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self, batch, frames):
+        """Seconds to run the oracle on `frames` (indices into batch) across the pool."""
+        chunks = np.array_split(np.asarray(frames), self.workers)
+        args = [(batch["y_pilot_td"][c].astype(complex), batch["y_data_td"][c].astype(complex),
+                 batch["noise_var"][c], batch["theta"][c], batch["a_pilot"]) for c in chunks if len(c)]
+        t0 = time.perf_counter()
+        done = sum(f.result() for f in [self.ex.submit(_oracle_chunk, *a) for a in args])
+        secs = time.perf_counter() - t0
+        assert done == len(frames)
+        return secs
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def host_cores():
+    return max(1, min(16, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()))
+
+
 def oracle_sample(n_frames, sample):
     idx = np.linspace(0, n_frames - 1, sample).astype(int)
     return idx
@@ -201,19 +249,27 @@ def impl_reference(args):
         return 0
     import synth
     batch = synth.fractional_batch(FRAMES, seed=SEED, M=M, N=N, Q=Q)
-    sample = args.ref_frames
+    cores = host_cores()
+    # frames per step: ref_frames per core, fewer for long runs so that the whole timed run
+    # stays near a minute of the pool's time (one frame is ~0.1 s of one core)
+    sample = max(1, min(args.ref_frames * cores, (60 * cores) // max(1, args.steps)))
     idx = oracle_sample(FRAMES, sample)
-    for _ in range(args.warmup):
-        run_oracle(batch, idx[:2])
-    times = [run_oracle(batch, idx) for _ in range(args.steps)]
+    pool = OraclePool(cores)
+    try:
+        for _ in range(args.warmup):
+            pool.run(batch, idx[:min(cores, len(idx))])
+        times = [pool.run(batch, idx) for _ in range(args.steps)]
+    finally:
+        pool.close()
     fps = sample * args.steps / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_step": sample},
-        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} of the {FRAMES} frames per step (evenly spaced), full FP64 receiver"},
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} of the {FRAMES} frames per step (evenly spaced), full FP64 receiver, "
+                                   f"{cores} worker processes"},
         "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -348,10 +404,21 @@ def impl_zotfs(args):
     # ---- FP64 oracle on the host cores (bounded sample)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        idx = oracle_sample(FRAMES, args.oracle_frames)
-        secs = run_oracle(batch, idx)
-        cpu = {"value": len(idx) / secs, "unit": "frames/s", "cores": 1, "kind": "oracle",
-               "sample": f"{len(idx)} of the {FRAMES} frames (evenly spaced), full FP64 receiver, single thread"}
+        cores = host_cores()
+        idx = oracle_sample(FRAMES, args.oracle_frames * cores)
+        pool = OraclePool(cores)
+        try:
+            pool.run(batch, idx[:cores])  # warm-up
+            secs = pool.run(batch, idx)
+        finally:
+            pool.close()
+        one = oracle_sample(FRAMES, args.oracle_frames)
+        secs1 = run_oracle(batch, one)
+        cpu = {"value": len(idx) / secs, "unit": "frames/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(idx)} of the {FRAMES} frames (evenly spaced), full FP64 receiver, {cores} worker "
+                         f"processes (one frame chunk each); single core on {len(one)} frames: "
+                         f"{len(one) / secs1:.2f} frames/s",
+               "single_core_value": len(one) / secs1}
 
     if rank == 0:
         bps = int(np.log2(Q))
@@ -598,15 +665,16 @@ def impl_mixed(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 2000; 20 with --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="zotfs", choices=["zotfs", "reference"])
     ap.add_argument("--threads", type=int, default=0, help="threads per frame (tuning)")
     ap.add_argument("--radix", type=int, default=0, help="FFT radix (tuning)")
     ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM (tuning)")
     ap.add_argument("--plain-frames", type=int, default=32)
-    ap.add_argument("--oracle-frames", type=int, default=48, help="oracle sample for cpu_baseline")
-    ap.add_argument("--ref-frames", type=int, default=8, help="oracle frames per step with --impl reference")
+    ap.add_argument("--oracle-frames", type=int, default=24, help="oracle sample per host core for cpu_baseline")
+    ap.add_argument("--ref-frames", type=int, default=4, help="oracle frames per host core per step (--impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed"],
                     help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
@@ -623,6 +691,8 @@ def main():
     ap.add_argument("--wave-frames", type=int, default=256, help="serve: frames admitted per wave")
     ap.add_argument("--waves", type=int, default=4, help="serve: waves in flight")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 2000
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
