@@ -62,21 +62,28 @@ static int real_bytes_of(const zotfs_plan_s* plan) { return plan->opt.compute ==
 bool choose_frame_cfg(int M, int N, int nrx, int ntx, int p_max, int threads_override, FrameCfg& cfg,
                       int real_bytes) {
   const int MN = M * N, nb = nrx > ntx ? nrx : ntx;
-  static const int kPref[] = {0, 1, 3, 2, 4, 5, 6, 7};
+  // coefficient-table variants first; each only where its tables still leave room for the
+  // variant's designed CTAs per SM (228 KB of shared memory per SM, 1 KB reserved per CTA)
+  static const int kPref[] = {8, 0, 9, 1, 10, 3, 2, 4, 5, 6, 7};
   const size_t kSmemCap = 227 * 1024;
   for (int idx : kPref) {
-    int E, NB, TMAX, rb;
-    if (!frame_variant_info(idx, E, NB, TMAX, rb)) continue;
+    int E, NB, TMAX, rb, minb, coef;
+    if (!frame_variant_info(idx, E, NB, TMAX, rb, minb, coef)) continue;
     if (rb != real_bytes) continue;
     if (NB < nb || E > N || (N % E) != 0) continue;
     const int T = MN / E;
     if (T < 32 || (T % 32) != 0 || T > TMAX || (T % M) != 0) continue;
     if (threads_override > 0 && T != threads_override) continue;
-    const size_t smem = frame_smem_bytes(M, N, E, nrx, ntx, p_max, real_bytes);
+    const size_t smem = frame_smem_bytes(M, N, E, nrx, ntx, p_max, real_bytes, coef != 0);
     if (smem > kSmemCap) continue;
+    if (coef) {
+      const size_t per_cta = 228 * 1024 / (size_t)minb - 1024;
+      if (smem > per_cta) continue;
+    }
     cfg.E = E;
     cfg.NB = NB;
     cfg.T = T;
+    cfg.coef = coef != 0;
     cfg.variant = idx;
     cfg.smem = smem;
     return true;

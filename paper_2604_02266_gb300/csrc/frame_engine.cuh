@@ -151,14 +151,20 @@ __host__ __device__ __forceinline__ int ext_rows(int N, int E) { return N + E + 
 __host__ __device__ __forceinline__ size_t ext_block_elems(int M, int N, int E) {
   return (size_t)ext_rows(N, E) * (size_t)(2 * M);
 }
+// Bytes of the per-(path, delay column) coefficient tables: forward and adjoint forms, one
+// complex value per path and column k for every antenna pair.
+__host__ __device__ __forceinline__ size_t coef_table_bytes(int M, int nrx, int ntx, int p_max, int real_bytes) {
+  return ((size_t)2 * nrx * ntx * p_max * M * 2 * real_bytes + 127) & ~size_t(127);
+}
 __host__ __device__ __forceinline__ size_t frame_smem_bytes(int M, int N, int E, int nrx, int ntx, int p_max,
-                                                            int real_bytes) {
+                                                            int real_bytes, bool coef = false) {
   size_t hdr = (sizeof(SharedHdr) + 127) & ~size_t(127);
   const size_t rec = (size_t)4 * real_bytes + 16;  // PathRecT<R>
   size_t paths = (size_t)nrx * ntx * p_max * rec + (size_t)nrx * ntx * sizeof(int) * 2;
   paths = (paths + 127) & ~size_t(127);
   paths += ((size_t)nrx * ntx * p_max * sizeof(RunRec) + 127) & ~size_t(127);  // run tables
   paths += ((size_t)p_max * rec + 127) & ~size_t(127);                        // sort scratch
+  if (coef) paths += coef_table_bytes(M, nrx, ntx, p_max, real_bytes);
   int nb = nrx > ntx ? nrx : ntx;
   size_t ext = (size_t)nb * ext_block_elems(M, N, E) * 2 * real_bytes;
   return hdr + paths + ext;
@@ -295,10 +301,15 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
 // One run of L paths on E output rows.  kFwd: window rows start at (j0 - dl0 - (L-1)) mod N
 // of column k - dk and path m reads window[L - 1 - m + i]; adjoint: rows start at
 // (j0 + dl0) mod N of column k + dk and path m reads window[m + i].
-template <typename R, int E, int L, bool kFwd, bool kRowMajor>
-__device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl, const RunRec& rr,
-                                          const FrameArgs& A, int k, int j0, typename Cx<R>::C (&accA)[E],
-                                          typename Cx<R>::C (&accB)[E]) {
+//
+// Coefficients: with kCoef they come from the frame's table `ct` (this list's column-k entry
+// of path 0; path p at ct[p M]) -- hf W[dl k] for kFwd, h W[dl k] for the adjoint, whose
+// conjugate the caller's final combine applies -- else they are formed here from the path
+// record and the twiddle table.
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
+__device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
+                                          const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
+                                          int j0, typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
   using C = typename Cx<R>::C;
   const int M = A.M, N = A.N;
   const int CS = kRowMajor ? 1 : N + E + 3;
@@ -308,11 +319,17 @@ __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const Pa
   C W[L + E - 1];
 #pragma unroll
   for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
+  const C* cr = kCoef ? ct + (size_t)rr.start * M : nullptr;
 #pragma unroll
   for (int m = 0; m < L; ++m) {
-    const PathRecT<R> rec = pl[rr.start + m];
-    const C t = tab<R>(A, (rr.dl0 + m + (N >> 1)) * M + k);
-    const C D = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+    C D;
+    if constexpr (kCoef) {
+      D = cr[(size_t)m * M];
+    } else {
+      const PathRecT<R> rec = pl[rr.start + m];
+      const C t = tab<R>(A, (rr.dl0 + m + (N >> 1)) * M + k);
+      D = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+    }
     const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
 #pragma unroll
     for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, W[(kFwd ? L - 1 - m : m) + i]);
@@ -321,10 +338,10 @@ __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const Pa
 
 // Forward rows (kFwd) of output block b: out[i] = (H p)_b[k, j0 + i], summed over the tx blocks
 // and the runs of each (b, t) list; adjoint: out[i] = (H^H u)_b[k, j0 + i] over the rx blocks.
-template <typename R, int E, bool kFwd, bool kRowMajor>
+template <typename R, int E, bool kFwd, bool kRowMajor, bool kCoef>
 __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
-                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int b, int k,
-                                            int j0, typename Cx<R>::C (&out)[E]) {
+                                            const RunRec* runs, const int* nruns, const typename Cx<R>::C* coef,
+                                            const FrameArgs& A, int b, int k, int j0, typename Cx<R>::C (&out)[E]) {
   using C = typename Cx<R>::C;
   // register budget: the window holds L + E - 1 complex values beside 2E accumulators
   constexpr int kLMax = E >= 32 ? 1 : (E >= 16 ? 2 : kMaxRun);
@@ -340,6 +357,7 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
     const int li = kFwd ? b * A.ntx + o : o * A.ntx + b;
     const PathRecT<R>* pl = paths + (size_t)li * A.p_max;
     const RunRec* rl = runs + (size_t)li * A.p_max;
+    const C* ct = kCoef ? coef + (size_t)li * A.p_max * A.M + k : nullptr;
     const int nr = nruns[li];
     for (int q = 0; q < nr; ++q) {
       const RunRec rr = rl[q];
@@ -348,41 +366,65 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
           RunRec one = rr;
           one.start = (short)(rr.start + m);
           one.dl0 = (short)(rr.dl0 + m);
-          apply_run<R, E, 1, kFwd, kRowMajor>(src, pl, one, A, k, j0, accA, accB);
+          apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, one, A, k, j0, accA, accB);
         }
       } else if constexpr (kLMax == 2) {
         for (int m = 0; m < rr.len; m += 2) {
           RunRec sub = rr;
           sub.start = (short)(rr.start + m);
           sub.dl0 = (short)(rr.dl0 + m);
-          if (rr.len - m >= 2) apply_run<R, E, 2, kFwd, kRowMajor>(src, pl, sub, A, k, j0, accA, accB);
-          else apply_run<R, E, 1, kFwd, kRowMajor>(src, pl, sub, A, k, j0, accA, accB);
+          if (rr.len - m >= 2) apply_run<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
+          else apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
         }
       } else {
         switch (rr.len) {
-          case 1: apply_run<R, E, 1, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
-          case 2: apply_run<R, E, 2, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
-          case 3: apply_run<R, E, 3, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
-          default: apply_run<R, E, 4, kFwd, kRowMajor>(src, pl, rr, A, k, j0, accA, accB); break;
+          case 1: apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
+          case 2: apply_run<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
+          case 3: apply_run<R, E, 3, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
+          default: apply_run<R, E, 4, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
         }
       }
     }
   }
+  // accA = sum D.x W, accB = sum D.y W: D W = (A.x - B.y, A.y + B.x); for the adjoint's table
+  // entries c (D = conj(c)): (A.x + B.y, A.y - B.x)
 #pragma unroll
-  for (int i = 0; i < E; ++i) out[i] = Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
+  for (int i = 0; i < E; ++i)
+    out[i] = (kCoef && !kFwd) ? Cx<R>::make(accA[i].x + accB[i].y, accA[i].y - accB[i].x)
+                              : Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
 }
 
-template <typename R, int E, bool kRowMajor = false>
+// coefF / coefA: the frame's coefficient tables (kCoef), else unused.
+template <typename R, int E, bool kRowMajor = false, bool kCoef = false>
 __device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int r, int k,
-                                           int j0, typename Cx<R>::C (&out)[E]) {
-  gather_runs<R, E, true, kRowMajor>(ext, blk, paths, runs, nruns, A, r, k, j0, out);
+                                           int j0, typename Cx<R>::C (&out)[E],
+                                           const typename Cx<R>::C* coefF = nullptr) {
+  gather_runs<R, E, true, kRowMajor, kCoef>(ext, blk, paths, runs, nruns, coefF, A, r, k, j0, out);
 }
-template <typename R, int E, bool kRowMajor = false>
+template <typename R, int E, bool kRowMajor = false, bool kCoef = false>
 __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int t, int k,
-                                           int j0, typename Cx<R>::C (&out)[E]) {
-  gather_runs<R, E, false, kRowMajor>(ext, blk, paths, runs, nruns, A, t, k, j0, out);
+                                           int j0, typename Cx<R>::C (&out)[E],
+                                           const typename Cx<R>::C* coefA = nullptr) {
+  gather_runs<R, E, false, kRowMajor, kCoef>(ext, blk, paths, runs, nruns, coefA, A, t, k, j0, out);
+}
+
+// The coefficient tables of one list (after build_runs: sorted order), all threads:
+// cf[p M + k] = hf_p W[dl_p k] (forward), ca[p M + k] = h_p W[dl_p k] (adjoint, conjugated
+// at use) -- the per-(path, column) factors of Eq. sparse_mvm / Eq. sparse_herm_mvm that do
+// not change over the CG iterations.
+template <typename R>
+__device__ __forceinline__ void coef_tables(const PathRecT<R>* pl, int P, const FrameArgs& A, typename Cx<R>::C* cf,
+                                            typename Cx<R>::C* ca) {
+  const int M = A.M, N = A.N;
+  for (int e = threadIdx.x; e < P * M; e += blockDim.x) {
+    const int p = e >> A.logM, k = e & (M - 1);
+    const PathRecT<R> rec = pl[p];
+    const typename Cx<R>::C t = tab<R>(A, (rec.dl + (N >> 1)) * M + k);
+    cf[e] = cmul(rec.hf, t);
+    ca[e] = cmul(rec.h, t);
+  }
 }
 
 // Sort one list's shared-memory copy by (dk, dl) (rank sort through `tmp`, which must hold P

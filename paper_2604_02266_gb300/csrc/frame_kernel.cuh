@@ -86,7 +86,10 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
   return io;
 }
 
-template <typename R, int E, int NB, int TMAX, int MINB>
+// COEF: keep per-(path, column) coefficient tables in shared memory for the frame's lists
+// (forward and adjoint forms), so the CG's gathers read one value per path instead of a path
+// record, a twiddle-table entry and a complex product.
+template <typename R, int E, int NB, int TMAX, int MINB, bool COEF>
 __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant__ FrameArgs A, int radix) {
   using C = typename Cx<R>::C;
   using PathRec = PathRecT<R>;
@@ -102,6 +105,25 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
   off += ((size_t)nlists * A.p_max * sizeof(RunRec) + 127) & ~size_t(127);
   PathRec* sort_tmp = reinterpret_cast<PathRec*>(smem + off);
   off += ((size_t)A.p_max * sizeof(PathRec) + 127) & ~size_t(127);
+  C* coefF = nullptr;
+  C* coefA = nullptr;
+  if constexpr (COEF) {
+    coefF = reinterpret_cast<C*>(smem + off);
+    coefA = coefF + (size_t)nlists * A.p_max * A.M;
+    off += coef_table_bytes(A.M, A.nrx, A.ntx, A.p_max, (int)sizeof(R));
+  }
+  // sorted path lists -> runs (and coefficient tables); all threads
+  auto finalize_lists = [&]() {
+    for (int li = 0; li < nlists; ++li)
+      build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, nruns + li);
+    if constexpr (COEF) {
+      for (int li = 0; li < nlists; ++li) {
+        const size_t o = (size_t)li * A.p_max * A.M;
+        coef_tables<R>(paths + (size_t)li * A.p_max, cnt[li], A, coefF + o, coefA + o);
+      }
+      __syncthreads();
+    }
+  };
   C* ext = reinterpret_cast<C*>(smem + off);
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM;
@@ -188,9 +210,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
       if (io.status && tid == 0) *io.status = status_from_bits(st);
       break;  // barrier phases are no longer trustworthy: stop this CTA
     }
-    if (have_paths)
-      for (int li = 0; li < nlists; ++li)
-        build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, nruns + li);
+    if (have_paths) finalize_lists();
 
     C v[NB][E];  // operator outputs / inputs per antenna block
 
@@ -208,8 +228,8 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         if (b < nout) {
-          if (A.adjoint) gather_adj<R, E>(ext, blk, paths, runs, nruns, A, b, k, j0, v[b]);
-          else gather_fwd<R, E>(ext, blk, paths, runs, nruns, A, b, k, j0, v[b]);
+          if (A.adjoint) gather_adj<R, E, false, COEF>(ext, blk, paths, runs, nruns, A, b, k, j0, v[b], coefA);
+          else gather_fwd<R, E, false, COEF>(ext, blk, paths, runs, nruns, A, b, k, j0, v[b], coefF);
 #pragma unroll
           for (int i = 0; i < E; ++i) reinterpret_cast<C*>(io.u_out)[(size_t)b * MN + (size_t)(j0 + i) * M + k] = v[b][i];
         }
@@ -254,7 +274,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             if (tid == 0) cnt[0] = P;
             if (trunc) st |= kStTrunc;
             __syncthreads();
-            build_runs<R>(paths, cnt[0], runs, sort_tmp, nruns);
+            finalize_lists();
           }
           // remove the pilot's response a_pilot H e_(K0,L0) (grid still scaled by sqrt(N))
           for (int p = tid; p < cnt[0]; p += blockDim.x) {
@@ -289,7 +309,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (t < A.ntx) {
-          gather_adj<R, E>(ext, blk, paths, runs, nruns, A, t, k, j0, c[t]);
+          gather_adj<R, E, false, COEF>(ext, blk, paths, runs, nruns, A, t, k, j0, c[t], coefA);
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             p[t][i] = c[t][i];
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
         // t = H p
 #pragma unroll
         for (int r = 0; r < NB; ++r)
-          if (r < A.nrx) gather_fwd<R, E>(ext, blk, paths, runs, nruns, A, r, k, j0, v[r]);
+          if (r < A.nrx) gather_fwd<R, E, false, COEF>(ext, blk, paths, runs, nruns, A, r, k, j0, v[r], coefF);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < NB; ++r)
@@ -319,7 +339,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
         for (int t = 0; t < NB; ++t)
           if (t < A.ntx) {
-            gather_adj<R, E>(ext, blk, paths, runs, nruns, A, t, k, j0, v[t]);
+            gather_adj<R, E, false, COEF>(ext, blk, paths, runs, nruns, A, t, k, j0, v[t], coefA);
 #pragma unroll
             for (int i = 0; i < E; ++i) {
               v[t][i].x = fma(lam, p[t][i].x, v[t][i].x);

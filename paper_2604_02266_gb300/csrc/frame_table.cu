@@ -4,7 +4,7 @@
 namespace zotfs {
 
 #define DECL(i)                                                                                      \
-  void frame_v##i##_info(int& E, int& NB, int& TMAX, int& real_bytes);                                               \
+  void frame_v##i##_info(int& E, int& NB, int& TMAX, int& real_bytes, int& minb, int& coef);                      \
   cudaError_t frame_v##i##_launch(const FrameArgs& A, int radix, int grid, int T, size_t smem,      \
                                   cudaStream_t stream);                                              \
   cudaError_t frame_v##i##_occupancy(int T, size_t smem, int& blocks);
@@ -16,10 +16,13 @@ DECL(4)
 DECL(5)
 DECL(6)
 DECL(7)
+DECL(8)
+DECL(9)
+DECL(10)
 #undef DECL
 
 struct Entry {
-  void (*info)(int&, int&, int&, int&);
+  void (*info)(int&, int&, int&, int&, int&, int&);
   cudaError_t (*launch)(const FrameArgs&, int, int, int, size_t, cudaStream_t);
   cudaError_t (*occ)(int, size_t, int&);
 };
@@ -29,13 +32,15 @@ static const Entry kTable[] = {
     {frame_v2_info, frame_v2_launch, frame_v2_occupancy}, {frame_v3_info, frame_v3_launch, frame_v3_occupancy},
     {frame_v4_info, frame_v4_launch, frame_v4_occupancy}, {frame_v5_info, frame_v5_launch, frame_v5_occupancy},
     {frame_v6_info, frame_v6_launch, frame_v6_occupancy}, {frame_v7_info, frame_v7_launch, frame_v7_occupancy},
+    {frame_v8_info, frame_v8_launch, frame_v8_occupancy}, {frame_v9_info, frame_v9_launch, frame_v9_occupancy},
+    {frame_v10_info, frame_v10_launch, frame_v10_occupancy},
 };
 
 int frame_variant_count() { return (int)(sizeof(kTable) / sizeof(kTable[0])); }
 
-bool frame_variant_info(int v, int& E, int& NB, int& TMAX, int& real_bytes) {
+bool frame_variant_info(int v, int& E, int& NB, int& TMAX, int& real_bytes, int& minb, int& coef) {
   if (v < 0 || v >= frame_variant_count()) return false;
-  kTable[v].info(E, NB, TMAX, real_bytes);
+  kTable[v].info(E, NB, TMAX, real_bytes, minb, coef);
   return true;
 }
 

@@ -50,12 +50,33 @@
 #define V_TMAX 256
 #define V_MINB 1
 #define V_R double
+#elif ZOTFS_VARIANT == 8
+#define V_E 8
+#define V_NB 1
+#define V_TMAX 256
+#define V_MINB 2
+#define V_COEF 1
+#elif ZOTFS_VARIANT == 9
+#define V_E 8
+#define V_NB 1
+#define V_TMAX 512
+#define V_MINB 1
+#define V_COEF 1
+#elif ZOTFS_VARIANT == 10
+#define V_E 16
+#define V_NB 1
+#define V_TMAX 256
+#define V_MINB 1
+#define V_COEF 1
 #else
 #error "unknown ZOTFS_VARIANT"
 #endif
 
 #ifndef V_R
 #define V_R float
+#endif
+#ifndef V_COEF
+#define V_COEF 0
 #endif
 
 #define ZCAT2(a, b) a##b
@@ -65,13 +86,15 @@
 namespace zotfs {
 
 using KernT = void (*)(const FrameArgs, int);
-static KernT kern() { return frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB>; }
+static KernT kern() { return frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB, (V_COEF != 0)>; }
 
-void VFUN(_info)(int& E, int& NB, int& TMAX, int& real_bytes) {
+void VFUN(_info)(int& E, int& NB, int& TMAX, int& real_bytes, int& minb, int& coef) {
   E = V_E;
   NB = V_NB;
   TMAX = V_TMAX;
   real_bytes = (int)sizeof(V_R);
+  minb = V_MINB;
+  coef = V_COEF;
 }
 
 // Raise the kernel's dynamic shared-memory limit to at least `smem` on the current device.
@@ -93,7 +116,7 @@ static cudaError_t grant_smem(size_t smem) {
 cudaError_t VFUN(_launch)(const FrameArgs& A, int radix, int grid, int T, size_t smem, cudaStream_t stream) {
   cudaError_t e = grant_smem(smem);
   if (e != cudaSuccess) return e;
-  frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB><<<grid, T, smem, stream>>>(A, radix);
+  kern()<<<grid, T, smem, stream>>>(A, radix);
   return cudaGetLastError();
 }
 

@@ -49,6 +49,7 @@ void fill_plan_args(const zotfs_plan_s* plan, FrameArgs& A);
 // variant fits (the caller then reports ZOTFS_EUNSUPPORTED or uses the big-frame path).
 struct FrameCfg {
   int E, NB, T;   // template rows/thread, blocks, threads per CTA
+  bool coef;      // the variant keeps coefficient tables in shared memory
   int variant;    // index into the instantiation table
   size_t smem;
 };
@@ -61,7 +62,7 @@ zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameA
 
 // Variant table implemented in frame_variants.cu
 int frame_variant_count();
-bool frame_variant_info(int v, int& E, int& NB, int& TMAX, int& real_bytes);
+bool frame_variant_info(int v, int& E, int& NB, int& TMAX, int& real_bytes, int& minb, int& coef);
 cudaError_t frame_variant_launch(int v, const FrameArgs& A, int radix, int grid, int T, size_t smem,
                                  cudaStream_t stream);
 cudaError_t frame_variant_occupancy(int v, int T, size_t smem, int& blocks);
