@@ -144,6 +144,7 @@ struct SharedHdr {       // fixed part of the dynamic shared memory
   int isc[4];
   int scan[40];
   double red[32];
+  int hist[128];         // radix-select histogram of the read-off (kept zero between uses)
 };
 
 // Shared-memory bytes needed by a frame kernel launch (host and device agree on this).
@@ -503,29 +504,60 @@ __device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const
   trunc = 0;
   if (total > A.p_max) {
     trunc = 1;
+    // The K-th largest |h|^2 among the passing taps, exactly: radix select on the bit
+    // patterns of the non-negative values (ordered like the values), 7 bits per pass from
+    // the top.  Each pass histograms the taps that share the bits fixed so far; warp 0 finds
+    // the bin holding the K-th largest from the top, fixes its bits and clears the bins.
     const int K = A.p_max;
-    Key lo = 0, hi = Cx<R>::key_inf();  // bit patterns of non-negative values are ordered
-    while (lo < hi) {
-      const Key mid = lo + ((hi - lo + 1) >> 1);
-      int c = 0;
+    constexpr int kKeyBits = 8 * (int)sizeof(Key) - 1;  // the sign bit is 0
+    Key prefix = 0, fixed = 0;
+    int kleft = K;  // rank of the wanted value among the taps that match `prefix`
+    const int lane = tid & 31;
+    for (int b = tid; b < 128; b += blockDim.x) S->hist[b] = 0;
+    __syncthreads();
+    for (int hb = kKeyBits; hb > 0; hb -= 7) {
+      const int w = hb < 7 ? hb : 7, sh = hb - w;
 #pragma unroll
       for (int i = 0; i < EQ; ++i)
-        if (((pass >> i) & 1u) && mb[i] >= mid) ++c;
-      c = block_sum_i(c, S->scan);
-      if (c >= K) lo = mid; else hi = mid - 1;
+        if (((pass >> i) & 1u) && ((mb[i] ^ prefix) & fixed) == 0)
+          atomicAdd(&S->hist[(int)((mb[i] >> sh) & (Key)127)], 1);
+      __syncthreads();
+      if (tid < 32) {
+        int c[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          c[j] = S->hist[4 * lane + j];
+          S->hist[4 * lane + j] = 0;
+          sum += c[j];
+        }
+        int suf = sum;  // inclusive suffix sum over lanes >= lane
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int n = __shfl_down_sync(0xffffffffu, suf, o);
+          if (lane + o < 32) suf += n;
+        }
+        int acc = suf - sum;  // taps in the bins above this lane's four
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+          if (acc < kleft && acc + c[j] >= kleft) {
+            S->isc[2] = 4 * lane + j;
+            S->isc[3] = kleft - acc;
+          }
+          acc += c[j];
+        }
+      }
+      __syncthreads();
+      const int bin = S->isc[2];
+      kleft = S->isc[3];
+      prefix |= (Key)bin << sh;
+      fixed |= (Key)((1u << w) - 1u) << sh;
     }
-    const Key vK = lo;  // the K-th largest |h|^2 among the passing taps
-    int gt = 0;
+    const Key vK = prefix;  // the K-th largest |h|^2 among the passing taps
     uint32_t eq = 0;
 #pragma unroll
-    for (int i = 0; i < EQ; ++i) {
-      if ((pass >> i) & 1u) {
-        if (mb[i] > vK) ++gt;
-        else if (mb[i] == vK) eq |= 1u << i;
-      }
-    }
-    const int n_gt = block_sum_i(gt, S->scan);
-    const int need = K - n_gt;  // ties at vK kept in ascending q
+    for (int i = 0; i < EQ; ++i)
+      if (((pass >> i) & 1u) && mb[i] == vK) eq |= 1u << i;
+    const int need = kleft;  // taps equal to vK that are kept, in ascending q
     int eq_total;
     int eq_base = block_exclusive_scan(__popc(eq), S->scan, eq_total);
     keep = 0;
