@@ -359,33 +359,37 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
     const PathRecT<R>* pl = paths + (size_t)li * A.p_max;
     const RunRec* rl = runs + (size_t)li * A.p_max;
     const C* ct = kCoef ? coef + (size_t)li * A.p_max * A.M + k : nullptr;
-    const int nr = nruns[li];
-    for (int q = 0; q < nr; ++q) {
-      const RunRec rr = rl[q];
-      if constexpr (kLMax == 1) {
-        for (int m = 0; m < rr.len; ++m) {
-          RunRec one = rr;
-          one.start = (short)(rr.start + m);
-          one.dl0 = (short)(rr.dl0 + m);
-          apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, one, A, k, j0, accA, accB);
-        }
-      } else if constexpr (kLMax == 2) {
-        for (int m = 0; m < rr.len; m += 2) {
+    // runs are stored longest first: n4 of length 4, then n3, n2 and n1 (packed counts)
+    const int packed = nruns[li];
+    const int n4 = packed & 127, n3 = (packed >> 7) & 127, n2 = (packed >> 14) & 255, n1 = (packed >> 22) & 511;
+    int q = 0;
+    if constexpr (kLMax == 4) {
+      for (const int e4 = n4; q < e4; ++q) apply_run<R, E, 4, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+      for (const int e3 = n4 + n3; q < e3; ++q) apply_run<R, E, 3, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+    } else {
+      for (const int e3 = n4 + n3; q < e3; ++q) {  // split into runs of at most kLMax paths
+        const RunRec rr = rl[q];
+        for (int m = 0; m < rr.len; m += kLMax) {
           RunRec sub = rr;
           sub.start = (short)(rr.start + m);
           sub.dl0 = (short)(rr.dl0 + m);
-          if (rr.len - m >= 2) apply_run<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
+          if (kLMax == 2 && rr.len - m >= 2) apply_run<R, E, (kLMax == 2 ? 2 : 1), kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
           else apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
-        }
-      } else {
-        switch (rr.len) {
-          case 1: apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
-          case 2: apply_run<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
-          case 3: apply_run<R, E, 3, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
-          default: apply_run<R, E, 4, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, accA, accB); break;
         }
       }
     }
+    if constexpr (kLMax >= 2) {
+      for (const int e2 = n4 + n3 + n2; q < e2; ++q) apply_run<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+    } else {
+      for (const int e2 = n4 + n3 + n2; q < e2; ++q) {
+        RunRec sub = rl[q];
+        apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
+        sub.start = (short)(sub.start + 1);
+        sub.dl0 = (short)(sub.dl0 + 1);
+        apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
+      }
+    }
+    for (const int e1 = n4 + n3 + n2 + n1; q < e1; ++q) apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
   }
   // accA = sum D.x W, accB = sum D.y W: D W = (A.x - B.y, A.y + B.x); for the adjoint's table
   // entries c (D = conj(c)): (A.x + B.y, A.y - B.x)
@@ -430,7 +434,9 @@ __device__ __forceinline__ void coef_tables(const PathRecT<R>* pl, int P, const 
 
 // Sort one list's shared-memory copy by (dk, dl) (rank sort through `tmp`, which must hold P
 // records and not alias the list) and cut it into runs of at most kMaxRun paths with equal dk
-// and consecutive dl.  All threads call.  Returns the number of runs.
+// and consecutive dl, stored longest first; *nruns_out packs the counts of runs of length
+// 4, 3, 2 and 1 into bits 0-6, 7-13, 14-21 and 22-30 (P <= 256).  All threads call.
+// Returns the number of runs.
 template <typename R>
 __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, PathRecT<R>* tmp, int* nruns_out) {
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
@@ -444,22 +450,37 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
   for (int p = threadIdx.x; p < P; p += blockDim.x) pl[p] = tmp[p];
   __syncthreads();
   if (threadIdx.x == 0) {
-    int n = 0, p = 0;
-    while (p < P) {
+    auto run_len = [&](int p) {
       int len = 1;
       while (p + len < P && len < kMaxRun && pl[p + len].dk == pl[p].dk && pl[p + len].dl == pl[p].dl + len) ++len;
+      return len;
+    };
+    int count[kMaxRun + 1] = {0, 0, 0, 0, 0};
+    for (int p = 0; p < P;) {
+      const int len = run_len(p);
+      ++count[len];
+      p += len;
+    }
+    int slot[kMaxRun + 1];
+    slot[4] = 0;
+    slot[3] = count[4];
+    slot[2] = slot[3] + count[3];
+    slot[1] = slot[2] + count[2];
+    for (int p = 0; p < P;) {
+      const int len = run_len(p);
       RunRec rr;
       rr.start = (short)p;
       rr.len = (short)len;
       rr.dk = (short)pl[p].dk;
       rr.dl0 = (short)pl[p].dl;
-      runs[n++] = rr;
+      runs[slot[len]++] = rr;
       p += len;
     }
-    *nruns_out = n;
+    *nruns_out = count[4] | (count[3] << 7) | (count[2] << 14) | (count[1] << 22);
   }
   __syncthreads();
-  return *nruns_out;
+  const int packed = *nruns_out;
+  return (packed & 127) + ((packed >> 7) & 127) + ((packed >> 14) & 255) + ((packed >> 22) & 511);
 }
 
 // ------------------------------------------------------------ read-off + compaction
