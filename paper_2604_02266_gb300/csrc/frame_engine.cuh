@@ -449,34 +449,53 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
   __syncthreads();
   for (int p = threadIdx.x; p < P; p += blockDim.x) pl[p] = tmp[p];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    auto run_len = [&](int p) {
-      int len = 1;
-      while (p + len < P && len < kMaxRun && pl[p + len].dk == pl[p].dk && pl[p + len].dl == pl[p].dl + len) ++len;
-      return len;
+  if (threadIdx.x < 32) {  // warp 0 cuts and places the runs, 32 paths per step
+    const int lane = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
+    auto linked = [&](int q) {  // path q continues path q - 1's Doppler sequence
+      return pl[q - 1].dk == pl[q].dk && pl[q - 1].dl + 1 == pl[q].dl;
     };
+    int lens[8];  // run length starting at path 32 c + lane (0: not a run start); P <= 256
     int count[kMaxRun + 1] = {0, 0, 0, 0, 0};
-    for (int p = 0; p < P;) {
-      const int len = run_len(p);
-      ++count[len];
-      p += len;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int p = 32 * c + lane;
+      int len = 0;
+      if (p < P) {
+        int q = p;
+        while (q > 0 && linked(q)) --q;  // start of p's maximal sequence
+        if (((p - q) & (kMaxRun - 1)) == 0) {
+          len = 1;
+          while (len < kMaxRun && p + len < P && linked(p + len)) ++len;
+        }
+      }
+      lens[c] = len;
+#pragma unroll
+      for (int L = 1; L <= kMaxRun; ++L) count[L] += __popc(__ballot_sync(0xffffffffu, len == L));
     }
     int slot[kMaxRun + 1];
     slot[4] = 0;
     slot[3] = count[4];
     slot[2] = slot[3] + count[3];
     slot[1] = slot[2] + count[2];
-    for (int p = 0; p < P;) {
-      const int len = run_len(p);
-      RunRec rr;
-      rr.start = (short)p;
-      rr.len = (short)len;
-      rr.dk = (short)pl[p].dk;
-      rr.dl0 = (short)pl[p].dl;
-      runs[slot[len]++] = rr;
-      p += len;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int p = 32 * c + lane;
+#pragma unroll
+      for (int L = 1; L <= kMaxRun; ++L) {
+        const unsigned m = __ballot_sync(0xffffffffu, lens[c] == L);
+        if (lens[c] == L) {
+          RunRec rr;
+          rr.start = (short)p;
+          rr.len = (short)L;
+          rr.dk = (short)pl[p].dk;
+          rr.dl0 = (short)pl[p].dl;
+          runs[slot[L] + __popc(m & lt)] = rr;
+        }
+        slot[L] += __popc(m);
+      }
     }
-    *nruns_out = count[4] | (count[3] << 7) | (count[2] << 14) | (count[1] << 22);
+    if (lane == 0) *nruns_out = count[4] | (count[3] << 7) | (count[2] << 14) | (count[1] << 22);
   }
   __syncthreads();
   const int packed = *nruns_out;
