@@ -28,6 +28,7 @@ __host__ __device__ __forceinline__ size_t big_smem_bytes(int nrx, int ntx, int 
   size_t paths = ((size_t)nrx * ntx * p_max * rec + (size_t)nrx * ntx * sizeof(int) * 2 + 127) & ~size_t(127);
   paths += ((size_t)nrx * ntx * p_max * sizeof(RunRec) + 127) & ~size_t(127);
   paths += ((size_t)p_max * rec + 127) & ~size_t(127);
+  paths += ((size_t)((p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);
   return hdr + paths;
 }
 
@@ -49,6 +50,8 @@ __global__ void __launch_bounds__(kBigThreads, 1)
   RunRec* runs = reinterpret_cast<RunRec*>(smem + off);
   off += ((size_t)nlists * A.p_max * sizeof(RunRec) + 127) & ~size_t(127);
   PathRec* sort_tmp = reinterpret_cast<PathRec*>(smem + off);
+  off += ((size_t)A.p_max * sizeof(PathRec) + 127) & ~size_t(127);
+  int* sort_keys = reinterpret_cast<int*>(smem + off);
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM, T = blockDim.x;
   const int nb = A.nrx > A.ntx ? A.nrx : A.ntx;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
     __syncthreads();
     if (have_paths)
       for (int li = 0; li < nlists; ++li)
-        build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, nruns + li);
+        build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, sort_keys, nruns + li);
 
     C v[E];
     // ------------------------------------------------ one operator apply
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
             if (tid == 0) cnt[0] = P;
             if (trunc) st |= kStTrunc;
             __syncthreads();
-            build_runs<R>(paths, cnt[0], runs, sort_tmp, nruns);
+            build_runs<R>(paths, cnt[0], runs, sort_tmp, sort_keys, nruns);
           }
           for (int p = tid; p < cnt[0]; p += T) {
             const PathRec rec = paths[p];

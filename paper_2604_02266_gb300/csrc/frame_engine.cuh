@@ -165,6 +165,7 @@ __host__ __device__ __forceinline__ size_t frame_smem_bytes(int M, int N, int E,
   paths = (paths + 127) & ~size_t(127);
   paths += ((size_t)nrx * ntx * p_max * sizeof(RunRec) + 127) & ~size_t(127);  // run tables
   paths += ((size_t)p_max * rec + 127) & ~size_t(127);                        // sort scratch
+  paths += ((size_t)((p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);     // sort keys
   if (coef) paths += coef_table_bytes(M, nrx, ntx, p_max, real_bytes);
   int nb = nrx > ntx ? nrx : ntx;
   size_t ext = (size_t)nb * ext_block_elems(M, N, E) * 2 * real_bytes;
@@ -423,6 +424,7 @@ template <typename R>
 __device__ __forceinline__ void coef_tables(const PathRecT<R>* pl, int P, const FrameArgs& A, typename Cx<R>::C* cf,
                                             typename Cx<R>::C* ca) {
   const int M = A.M, N = A.N;
+#pragma unroll 2
   for (int e = threadIdx.x; e < P * M; e += blockDim.x) {
     const int p = e >> A.logM, k = e & (M - 1);
     const PathRecT<R> rec = pl[p];
@@ -433,43 +435,53 @@ __device__ __forceinline__ void coef_tables(const PathRecT<R>* pl, int P, const 
 }
 
 // Sort one list's shared-memory copy by (dk, dl) (rank sort through `tmp`, which must hold P
-// records and not alias the list) and cut it into runs of at most kMaxRun paths with equal dk
-// and consecutive dl, stored longest first; *nruns_out packs the counts of runs of length
-// 4, 3, 2 and 1 into bits 0-6, 7-13, 14-21 and 22-30 (P <= 256).  All threads call.
-// Returns the number of runs.
+// records and not alias the list; `keys` is scratch for max(P, 4) ints rounded up to a
+// multiple of 4) and cut it into runs of at most kMaxRun paths with equal dk and consecutive
+// dl, stored longest first; *nruns_out packs the counts of runs of length 4, 3, 2 and 1 into
+// bits 0-6, 7-13, 14-21 and 22-30 (P <= 256).  All threads call.  Returns the number of runs.
 template <typename R>
-__device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, PathRecT<R>* tmp, int* nruns_out) {
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    const PathRecT<R> me = pl[p];
-    const int key = me.dk * 256 + me.dl;
+__device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, PathRecT<R>* tmp, int* keys,
+                                          int* nruns_out) {
+  const int P4 = (P + 3) & ~3;
+  for (int p = threadIdx.x; p < P4; p += blockDim.x) keys[p] = p < P ? pl[p].dk * 256 + pl[p].dl : 0x7fffffff;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {  // keys are distinct: ranks are a permutation
+    const int key = keys[p];
     int rank = 0;
-    for (int u = 0; u < P; ++u) rank += (pl[u].dk * 256 + pl[u].dl) < key;
-    tmp[rank] = me;
+    for (int u = 0; u < P4; u += 4) {
+      const int4 kv = *reinterpret_cast<const int4*>(keys + u);
+      rank += (kv.x < key) + (kv.y < key) + (kv.z < key) + (kv.w < key);
+    }
+    tmp[rank] = pl[p];
   }
   __syncthreads();
   for (int p = threadIdx.x; p < P; p += blockDim.x) pl[p] = tmp[p];
   __syncthreads();
-  if (threadIdx.x < 32) {  // warp 0 cuts and places the runs, 32 paths per step
+  if (threadIdx.x < 32) {  // warp 0 cuts and places the runs from bit masks, 32 paths per word
     const int lane = threadIdx.x;
-    const unsigned lt = (1u << lane) - 1u;
-    auto linked = [&](int q) {  // path q continues path q - 1's Doppler sequence
-      return pl[q - 1].dk == pl[q].dk && pl[q - 1].dl + 1 == pl[q].dl;
-    };
-    int lens[8];  // run length starting at path 32 c + lane (0: not a run start); P <= 256
-    int count[kMaxRun + 1] = {0, 0, 0, 0, 0};
+    const unsigned lt = (1u << lane) - 1u, le = lt | (1u << lane);
+    unsigned link[9];  // bit (p mod 32) of word p / 32: path p continues path p - 1's sequence
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int p = 32 * c + lane;
-      int len = 0;
-      if (p < P) {
-        int q = p;
-        while (q > 0 && linked(q)) --q;  // start of p's maximal sequence
-        if (((p - q) & (kMaxRun - 1)) == 0) {
-          len = 1;
-          while (len < kMaxRun && p + len < P && linked(p + len)) ++len;
-        }
-      }
+      const bool l = p > 0 && p < P && pl[p - 1].dk == pl[p].dk && pl[p - 1].dl + 1 == pl[p].dl;
+      link[c] = __ballot_sync(0xffffffffu, l);
+    }
+    link[8] = 0u;
+    int lens[8];  // run length starting at path 32 c + lane (0: not a run start)
+    int count[kMaxRun + 1] = {0, 0, 0, 0, 0};
+    int last_start = 0;  // start of the sequence that is open at the end of the previous word
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int p = 32 * c + lane;
+      const unsigned heads = ~link[c];  // paths that begin a maximal sequence
+      const unsigned below = heads & le;
+      const int seq = below ? 32 * c + 31 - __clz(below) : last_start;
+      const unsigned long long win = ((unsigned long long)link[c + 1] << 32 | link[c]) >> (lane + 1);
+      const int follow = __ffsll(~win & 7ull) ? __ffsll(~win & 7ull) - 1 : 3;  // linked successors, <= 3
+      const int len = (p < P && ((p - seq) & (kMaxRun - 1)) == 0) ? 1 + follow : 0;
       lens[c] = len;
+      if (heads) last_start = 32 * c + 31 - __clz(heads);
 #pragma unroll
       for (int L = 1; L <= kMaxRun; ++L) count[L] += __popc(__ballot_sync(0xffffffffu, len == L));
     }

@@ -105,6 +105,8 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
   off += ((size_t)nlists * A.p_max * sizeof(RunRec) + 127) & ~size_t(127);
   PathRec* sort_tmp = reinterpret_cast<PathRec*>(smem + off);
   off += ((size_t)A.p_max * sizeof(PathRec) + 127) & ~size_t(127);
+  int* sort_keys = reinterpret_cast<int*>(smem + off);
+  off += ((size_t)((A.p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);
   C* coefF = nullptr;
   C* coefA = nullptr;
   if constexpr (COEF) {
@@ -115,7 +117,8 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
   // sorted path lists -> runs (and coefficient tables); all threads
   auto finalize_lists = [&]() {
     for (int li = 0; li < nlists; ++li)
-      build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, nruns + li);
+      build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, sort_keys,
+                    nruns + li);
     if constexpr (COEF) {
       for (int li = 0; li < nlists; ++li) {
         const size_t o = (size_t)li * A.p_max * A.M;
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
     if ((A.mode & kDemap) && (io.llr || io.bits)) {
       const R inv_lam = (R)1 / (R)io.lam;
       const int bps = io.bps;
-      uint8_t* lab = reinterpret_cast<uint8_t*>(ext);
+      uint8_t* lab = reinterpret_cast<uint8_t*>(ext);  // labels, bit j of the symbol at bit j
       __syncthreads();  // ext no longer read by anyone
 #pragma unroll
       for (int t = 0; t < NB; ++t)
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             const int q = (j0 + i) * M + k;
             float l[6];
             const int hard = qam_llr<R>(x[t][i], bps, (R)io.pam_d, inv_lam, l);
-            lab[t * MN + q] = (uint8_t)hard;
+            lab[t * MN + q] = (uint8_t)(__brev((unsigned)hard) >> (32 - bps));  // label bits LSB first
             if (io.llr) {
               float2* o = reinterpret_cast<float2*>(io.llr + ((size_t)t * MN + q) * bps);
               o[0] = make_float2(l[0], l[1]);
@@ -428,19 +431,20 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           }
       __syncthreads();
       if (io.bits) {
-        const int bytes_per_block = MN * bps / 8;
-        const int total = A.ntx * bytes_per_block;
-        for (int B = tid; B < total; B += blockDim.x) {
-          const int t = B / bytes_per_block;
-          const int b0 = (B - t * bytes_per_block) * 8;
-          int byte = 0;
+        // 8 consecutive symbols fill exactly bps bytes (bits LSB first, symbol by symbol)
+        const int groups = A.ntx * MN / 8;
+        for (int g = tid; g < groups; g += blockDim.x) {
+          const unsigned long long l8 = reinterpret_cast<const unsigned long long*>(lab)[g];
+          unsigned long long w = 0;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int bit = b0 + j;
-            const int q = bit / bps, jj = bit - q * bps;
-            byte |= ((lab[t * MN + q] >> (bps - 1 - jj)) & 1) << j;
+          for (int s8 = 0; s8 < 8; ++s8) w |= ((l8 >> (8 * s8)) & 0xffull) << (bps * s8);
+          uint8_t* o = io.bits + (size_t)g * bps;
+          if ((reinterpret_cast<uintptr_t>(o) & 1u) == 0) {
+            uint16_t* o2 = reinterpret_cast<uint16_t*>(o);
+            for (int h = 0; h < bps / 2; ++h) o2[h] = (uint16_t)(w >> (16 * h));
+          } else {
+            for (int h = 0; h < bps; ++h) o[h] = (uint8_t)(w >> (8 * h));
           }
-          io.bits[B] = (uint8_t)byte;
         }
       }
       __syncthreads();
