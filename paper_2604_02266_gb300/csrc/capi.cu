@@ -91,6 +91,79 @@ bool choose_frame_cfg(int M, int N, int nrx, int ntx, int p_max, int threads_ove
   return false;
 }
 
+namespace {
+
+// One CTA of 1024 threads: keys are 31-bit (theta's bit pattern, or 2^30 - total paths),
+// bucketed into 256 ranges between the smallest and largest key, counted, scanned and
+// scattered (ascending key = decreasing expected work).
+__global__ void __launch_bounds__(1024) frame_order_kernel(const float* theta, const int32_t* count, int nlists,
+                                                           int n, int* order) {
+  __shared__ unsigned lo_s, hi_s;
+  __shared__ int hist[256];
+  auto key = [&](int i) -> unsigned {
+    if (theta) {
+      const float t = theta[i];
+      return (t > 0.f && isfinite(t)) ? __float_as_uint(t) : 0x7f800000u;
+    }
+    int tot = 0;
+    for (int l = 0; l < nlists; ++l) tot += count[(size_t)i * nlists + l];
+    return (1u << 30) - (unsigned)min(max(tot, 0), 1 << 29);
+  };
+  if (threadIdx.x == 0) {
+    lo_s = 0xffffffffu;
+    hi_s = 0u;
+  }
+  if (threadIdx.x < 256) hist[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned lo = 0xffffffffu, hi = 0u;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned k = key(i);
+    lo = min(lo, k);
+    hi = max(hi, k);
+  }
+  atomicMin(&lo_s, lo);
+  atomicMax(&hi_s, hi);
+  __syncthreads();
+  lo = lo_s;
+  const unsigned range = hi_s - lo;
+  const int shift = range < 256u ? 0 : 32 - __clz(range) - 8;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hist[min(255u, (key(i) - lo) >> shift)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int b = 0; b < 256; ++b) {
+      const int c = hist[b];
+      hist[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&hist[min(255u, (key(i) - lo) >> shift)], 1)] = i;
+}
+
+}  // namespace
+
+cudaError_t launch_frame_order(const float* theta, const int32_t* count, int nlists, int n, int* order,
+                               cudaStream_t stream) {
+  frame_order_kernel<<<1, 1024, 0, stream>>>(theta, count, nlists, n, order);
+  return cudaGetLastError();
+}
+
+// Frames are taken heaviest-first when a launch needs more than one round of resident CTAs
+// (the last round then holds the lightest frames): returns the order array to use, or NULL.
+static const int* maybe_order(zotfs_plan_s* plan, const FrameArgs& A, int resident, cudaStream_t stream) {
+  if (A.descs || A.frame_ids || A.n_frames <= resident || A.n_frames > kOrderCap) return nullptr;
+  const bool by_theta = (A.mode & kEstimate) && A.theta;
+  const bool by_count = !(A.mode & kEstimate) && (A.mode & kLoadPaths) && A.pcount;
+  if (!by_theta && !by_count) return nullptr;
+  int* order = plan->d_order + (size_t)(plan->order_next++ % kOrderSlots) * kOrderCap;
+  if (launch_frame_order(by_theta ? A.theta : nullptr, by_count ? A.pcount : nullptr, A.nrx * A.ntx, A.n_frames,
+                         order, stream) != cudaSuccess)
+    return nullptr;  // run in index order
+  ++g_launches;
+  return order;
+}
+
 zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameArgs& A, int radix, int ctas_per_sm,
                                  cudaStream_t stream) {
   int* counter = plan->d_counters + (plan->counter_next++ & 63);
@@ -106,6 +179,7 @@ zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameA
   }
   if (ctas_per_sm > 0 && ctas_per_sm < blocks) blocks = ctas_per_sm;
   long long grid = (long long)plan->sm_count * blocks;
+  if (const int* order = maybe_order(plan, A, (int)grid, stream)) A.frame_ids = order;
   if (grid > A.n_frames) grid = A.n_frames;
   e = frame_variant_launch(cfg.variant, A, radix, (int)grid, cfg.T, cfg.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "frame kernel launch");
@@ -225,6 +299,7 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
   if (e == cudaSuccess) e = cudaMalloc(&p->d_W64, sizeof(double2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab64, sizeof(double2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(int) * 64);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int) * kOrderCap * kOrderSlots);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_plain, p->plain_bytes);
   {
     FrameCfg fc;
@@ -264,6 +339,7 @@ zotfs_status zotfs_plan_destroy(zotfs_plan plan) {
   if (plan->d_W64) cudaFree(plan->d_W64);
   if (plan->d_Tab64) cudaFree(plan->d_Tab64);
   if (plan->d_counters) cudaFree(plan->d_counters);
+  if (plan->d_order) cudaFree(plan->d_order);
   if (plan->d_plain) cudaFree(plan->d_plain);
   if (plan->d_big) cudaFree(plan->d_big);
   delete plan;

@@ -102,7 +102,8 @@ struct FrameArgs {
   int32_t* status;
   void* u_out;
   // uneven batches: per-frame buffers come from descriptors (frame f of this launch is
-  // descriptor frame_ids[f]); NULL for the single-shape calls
+  // descriptor frame_ids[f]); single-shape calls: frame_ids, if set, is the order in which
+  // the CTAs take the frames (a permutation of [0, n_frames))
   const zotfs_frame_desc* descs;
   const int* frame_ids;
 };

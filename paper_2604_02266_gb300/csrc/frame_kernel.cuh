@@ -59,6 +59,7 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
     io.status = A.status ? A.status + A.frame_ids[f] : nullptr;
     return io;
   }
+  if (A.frame_ids) f = A.frame_ids[f];
   io.y_pilot = A.y_pilot ? static_cast<const char*>(A.y_pilot) + (size_t)f * A.ntx * A.nrx * in_bytes : nullptr;
   const size_t data_bytes = A.y_is_dd ? (size_t)MN * csz : in_bytes;
   io.y_data = A.y_data ? static_cast<const char*>(A.y_data) + (size_t)f * A.nrx * data_bytes : nullptr;

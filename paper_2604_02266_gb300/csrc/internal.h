@@ -20,6 +20,10 @@ struct zotfs_plan_s {
   double2* d_Tab64;
   int* d_counters;
   int counter_next;
+  // frame orders for multi-round launches (heaviest expected work first): a ring of
+  // kOrderSlots arrays of kOrderCap frame indices
+  int* d_order;
+  int order_next;
   // plain-form scratch (one frame): y_dd, b/x/c/p/t/a vectors, scalars, paths
   void* d_plain;
   size_t plain_bytes;
@@ -41,6 +45,15 @@ bool is_pow2(int v);
 // FFT radix of the in-shared-memory Zak transform when the caller leaves it open (radix 4
 // with a closing radix-2 stage measured a few per cent faster than pure radix 2 at 64x32).
 constexpr int kDefaultRadix = 4;
+
+constexpr int kOrderCap = 16384, kOrderSlots = 4;
+
+// Launch a kernel that writes into `order` a permutation of [0, n) listing frames by
+// decreasing expected work: by increasing threshold theta (a lower threshold keeps more
+// taps) when `theta` is given, else by decreasing total path count over the frame's
+// `nlists` lists in `count`.  Frames with equal keys keep no particular order.
+cudaError_t launch_frame_order(const float* theta, const int32_t* count, int nlists, int n, int* order,
+                               cudaStream_t stream);
 
 // Fill the constant parts of FrameArgs from a plan.
 void fill_plan_args(const zotfs_plan_s* plan, FrameArgs& A);
