@@ -255,6 +255,15 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     sms = std::max(1, std::min(sms, avail));
     B.grid = std::max(1, std::min((int)B.ids.size(), sms * occ[bi]));
   }
+  // each bucket's CTAs take its frames heaviest first (lowest threshold first: more taps pass
+  // it; then more iterations), so the last frames to start are the lightest
+  for (Bucket& B : b->buckets)
+    std::stable_sort(B.ids.begin(), B.ids.end(), [&](int i, int j) {
+      const float ti = std::isfinite(D[i].theta) ? D[i].theta : INFINITY;
+      const float tj = std::isfinite(D[j].theta) ? D[j].theta : INFINITY;
+      if (ti != tj) return ti < tj;
+      return D[i].iters > D[j].iters;
+    });
   // device copies: descriptors, frame ids per bucket, counters, per-shape tables
   std::vector<int> ids;
   for (Bucket& B : b->buckets) {
