@@ -662,6 +662,52 @@ def impl_mixed(args):
     return 0
 
 
+# --------------------------------------------------------------------- MIMO workload
+
+def impl_mimo(args):
+    """256 frames of a 4x4 stack at 128x64, 64-QAM (16 path lists per frame, 32768 stacked
+    unknowns per CG): the large-frame kernel, whose vectors live in L2-resident scratch."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Plan, launch_count
+    Mm, Nm, Qm, A, F = 128, 64, 64, 4, 256
+    b = synth.fractional_batch(F, seed=SEED + 3, M=Mm, N=Nm, Q=Qm, n_rx=A, n_tx=A)
+    plan = Plan(Mm, Nm, A, A, Qm)
+    yp, yd = torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev)
+    nv, th = torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev)
+    outs = plan._rx_outputs(F, dev, True, False, False)
+    for _ in range(args.warmup):
+        plan.rx(yp, yd, nv, th, ITERS, F, out=outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = args.mimo_steps
+    e0.record()
+    for _ in range(steps):
+        plan.rx(yp, yd, nv, th, ITERS, F, out=outs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    P = outs[0].count.cpu().numpy()
+    st = outs[4].cpu().numpy()
+    line = {"metric": "equalized Zak-OTFS frames/s, 4x4 MIMO 128x64 64-QAM", "value": F / ms * 1e3, "unit": "frames/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256 frames, 4x4 antennas, M=128, N=64, 64-QAM, 16 independent 6-path fractional "
+                                   "channels per frame, separate pilot frame per tx antenna, SNR 0..30 dB, 10 CG "
+                                   "iterations over 32768 stacked unknowns, complex FP32 with FP64 CG scalars"},
+            "mbit_s": F * A * Mm * Nm * 6 / ms / 1e3, "paths_per_list": {"mean": float(P.mean()), "max": int(P.max())},
+            "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()), "gpu_launches": launch_count()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -676,9 +722,10 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=24, help="oracle sample per host core for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=4, help="oracle frames per host core per step (--impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo"],
                     help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
-                         "mixed: the uneven FP16/BF16 batch under CUDA graphs")
+                         "mixed: the uneven FP16/BF16 batch under CUDA graphs; mimo: 4x4 128x64 64-QAM frames")
+    ap.add_argument("--mimo-steps", type=int, default=5, help="mimo: timed steps")
     ap.add_argument("--mixed-steps", type=int, default=20, help="mixed: timed steps per storage type")
     ap.add_argument("--tune-frames", type=int, default=64, help="mixed: frames per shape group the autotuner times")
     ap.add_argument("--tuning-file", default="", help="mixed: write the autotuner's JSON here ({dtype} expands)")
@@ -701,6 +748,8 @@ def main():
         return impl_serve(args)
     if args.workload == "mixed":
         return impl_mixed(args)
+    if args.workload == "mimo":
+        return impl_mimo(args)
     return impl_zotfs(args)
 
 
