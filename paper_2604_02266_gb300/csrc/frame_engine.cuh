@@ -606,25 +606,33 @@ __device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const
       fixed |= (Key)((1u << w) - 1u) << sh;
     }
     const Key vK = prefix;  // the K-th largest |h|^2 among the passing taps
-    uint32_t eq = 0;
+    const int need = kleft;  // taps equal to vK that are kept: the first `need` in ascending q
+    uint32_t gt = 0, eq = 0;
 #pragma unroll
     for (int i = 0; i < EQ; ++i)
-      if (((pass >> i) & 1u) && mb[i] == vK) eq |= 1u << i;
-    const int need = kleft;  // taps equal to vK that are kept, in ascending q
-    int eq_total;
-    int eq_base = block_exclusive_scan(__popc(eq), S->scan, eq_total);
+      if ((pass >> i) & 1u) {
+        if (mb[i] > vK) gt |= 1u << i;
+        else if (mb[i] == vK) eq |= 1u << i;
+      }
+    // one scan of the packed counts (taps above vK in the high half, ties in the low half):
+    // a kept tap's position = taps above vK before it + min(ties before it, need)
+    int both_total;
+    const int both = block_exclusive_scan((__popc(gt) << 16) | __popc(eq), S->scan, both_total);
+    (void)both_total;
+    int gt_before = both >> 16, eq_before = both & 0xffff;
     keep = 0;
+    int pos0 = gt_before + min(eq_before, need);
 #pragma unroll
     for (int i = 0; i < EQ; ++i) {
-      if ((pass >> i) & 1u) {
-        if (mb[i] > vK) keep |= 1u << i;
-        else if (mb[i] == vK) {
-          if (eq_base < need) keep |= 1u << i;
-          ++eq_base;
-        }
+      if ((gt >> i) & 1u) {
+        keep |= 1u << i;
+      } else if ((eq >> i) & 1u) {
+        if (eq_before < need) keep |= 1u << i;
+        ++eq_before;
       }
     }
-    base = block_exclusive_scan(__popc(keep), S->scan, total);
+    base = pos0;
+    total = K;
   }
   int pos = base;
 #pragma unroll

@@ -12,8 +12,9 @@
 
 namespace zotfs {
 
-// Warp partials of `v` summed in FP64 by warp 0; the total is valid in warp 0 (thread 0
-// uses it).  One barrier; the caller publishes results with another.
+// Warp partials of `v` summed in FP64 by thread 0 (pairwise, eight partials at a time, in a
+// fixed order); the total is valid in thread 0 only.  One barrier; the caller publishes
+// results with another.
 template <typename R>
 __device__ __forceinline__ double block_sum_to_thread0(R v, SharedHdr* S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -21,9 +22,13 @@ __device__ __forceinline__ double block_sum_to_thread0(R v, SharedHdr* S) {
   if (lane == 0) S->red[warp] = (double)v;
   __syncthreads();
   double d = 0.0;
-  if (warp == 0) {
-    d = lane < nwarps ? S->red[lane] : 0.0;
-    d = warp_sum_f64(d);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < nwarps; b += 8) {
+      double r[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) r[i] = b + i < nwarps ? S->red[b + i] : 0.0;
+      d += ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
+    }
   }
   return d;
 }
