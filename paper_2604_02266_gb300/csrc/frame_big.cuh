@@ -325,14 +325,14 @@ __global__ void __launch_bounds__(kBigThreads, 1)
           for (int i = 0; i < E; ++i) {
             const size_t o = (size_t)t * MN + own(c, i);
             const int q = (int)(o - (size_t)t * MN);
-            float l[6];
-            const int hard = qam_llr<R>(Xv[o], bps, (R)io.pam_d, inv_lam, l);
+            float2 l01, l23, l45;
+            const int hard = qam_llr_regs<R>(Xv[o], bps, (R)io.pam_d, inv_lam, l01, l23, l45);
             lab[o] = (uint8_t)hard;
             if (io.llr) {
               float2* ol = reinterpret_cast<float2*>(io.llr + ((size_t)t * MN + q) * bps);
-              ol[0] = make_float2(l[0], l[1]);
-              if (bps > 2) ol[1] = make_float2(l[2], l[3]);
-              if (bps > 4) ol[2] = make_float2(l[4], l[5]);
+              ol[0] = l01;
+              if (bps > 2) ol[1] = l23;
+              if (bps > 4) ol[2] = l45;
             }
           }
       __syncthreads();

@@ -470,7 +470,7 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
     }
     link[8] = 0u;
     int lens[8];  // run length starting at path 32 c + lane (0: not a run start)
-    int count[kMaxRun + 1] = {0, 0, 0, 0, 0};
+    int n1 = 0, n2 = 0, n3 = 0, n4 = 0;
     int last_start = 0;  // start of the sequence that is open at the end of the previous word
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -483,32 +483,35 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
       const int len = (p < P && ((p - seq) & (kMaxRun - 1)) == 0) ? 1 + follow : 0;
       lens[c] = len;
       if (heads) last_start = 32 * c + 31 - __clz(heads);
-#pragma unroll
-      for (int L = 1; L <= kMaxRun; ++L) count[L] += __popc(__ballot_sync(0xffffffffu, len == L));
+      n1 += __popc(__ballot_sync(0xffffffffu, len == 1));
+      n2 += __popc(__ballot_sync(0xffffffffu, len == 2));
+      n3 += __popc(__ballot_sync(0xffffffffu, len == 3));
+      n4 += __popc(__ballot_sync(0xffffffffu, len == 4));
     }
-    int slot[kMaxRun + 1];
-    slot[4] = 0;
-    slot[3] = count[4];
-    slot[2] = slot[3] + count[3];
-    slot[1] = slot[2] + count[2];
+    int s4 = 0, s3 = n4, s2 = n4 + n3, s1 = n4 + n3 + n2;  // first slot of each length
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int p = 32 * c + lane;
-#pragma unroll
-      for (int L = 1; L <= kMaxRun; ++L) {
-        const unsigned m = __ballot_sync(0xffffffffu, lens[c] == L);
-        if (lens[c] == L) {
-          RunRec rr;
-          rr.start = (short)p;
-          rr.len = (short)L;
-          rr.dk = (short)pl[p].dk;
-          rr.dl0 = (short)pl[p].dl;
-          runs[slot[L] + __popc(m & lt)] = rr;
-        }
-        slot[L] += __popc(m);
+      const int len = lens[c];
+      const unsigned m1 = __ballot_sync(0xffffffffu, len == 1), m2 = __ballot_sync(0xffffffffu, len == 2);
+      const unsigned m3 = __ballot_sync(0xffffffffu, len == 3), m4 = __ballot_sync(0xffffffffu, len == 4);
+      if (len) {
+        const int slot = len == 4 ? s4 + __popc(m4 & lt)
+                       : len == 3 ? s3 + __popc(m3 & lt)
+                       : len == 2 ? s2 + __popc(m2 & lt) : s1 + __popc(m1 & lt);
+        RunRec rr;
+        rr.start = (short)p;
+        rr.len = (short)len;
+        rr.dk = (short)pl[p].dk;
+        rr.dl0 = (short)pl[p].dl;
+        runs[slot] = rr;
       }
+      s1 += __popc(m1);
+      s2 += __popc(m2);
+      s3 += __popc(m3);
+      s4 += __popc(m4);
     }
-    if (lane == 0) *nruns_out = count[4] | (count[3] << 7) | (count[2] << 14) | (count[1] << 22);
+    if (lane == 0) *nruns_out = n4 | (n3 << 7) | (n2 << 14) | (n1 << 22);
   }
   __syncthreads();
   const int packed = *nruns_out;
@@ -743,6 +746,31 @@ __device__ __forceinline__ int qam_llr(typename Cx<R>::C x, int bps, R d, R inv_
     l[j] = (float)lr[j];
     if (j < bps) hard |= (lr[j] < (R)0 ? 1 : 0) << (bps - 1 - j);
   }
+  return hard;
+}
+
+// The same LLRs and hard label as qam_llr, returned in registers: o01 = (l0, l1),
+// o23 = (l2, l3), o45 = (l4, l5).
+template <typename R>
+__device__ __forceinline__ int qam_llr_regs(typename Cx<R>::C x, int bps, R d, R inv_lam, float2& o01, float2& o23,
+                                            float2& o45) {
+  const int hb = bps >> 1;
+  R i0, i1, i2, q0, q1, q2;
+  pam_llr<R>(x.x, hb, d, inv_lam, i0, i1, i2);
+  pam_llr<R>(x.y, hb, d, inv_lam, q0, q1, q2);
+  const R z = (R)0;
+  const R l0 = i0;
+  const R l1 = hb == 1 ? q0 : i1;
+  const R l2 = hb == 1 ? z : (hb == 2 ? q0 : i2);
+  const R l3 = hb == 1 ? z : (hb == 2 ? q1 : q0);
+  const R l4 = hb == 3 ? q1 : z;
+  const R l5 = hb == 3 ? q2 : z;
+  o01 = make_float2((float)l0, (float)l1);
+  o23 = make_float2((float)l2, (float)l3);
+  o45 = make_float2((float)l4, (float)l5);
+  int hard = ((l0 < z) << (bps - 1)) | ((l1 < z) << (bps - 2));
+  if (bps > 2) hard |= ((l2 < z) << (bps - 3)) | ((l3 < z) << (bps - 4));
+  if (bps > 4) hard |= ((l4 < z) << 1) | (l5 < z);
   return hard;
 }
 

@@ -425,14 +425,14 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const int q = (j0 + i) * M + k;
-            float l[6];
-            const int hard = qam_llr<R>(x[t][i], bps, (R)io.pam_d, inv_lam, l);
+            float2 l01, l23, l45;
+            const int hard = qam_llr_regs<R>(x[t][i], bps, (R)io.pam_d, inv_lam, l01, l23, l45);
             lab[t * MN + q] = (uint8_t)(__brev((unsigned)hard) >> (32 - bps));  // label bits LSB first
             if (io.llr) {
               float2* o = reinterpret_cast<float2*>(io.llr + ((size_t)t * MN + q) * bps);
-              o[0] = make_float2(l[0], l[1]);
-              if (bps > 2) o[1] = make_float2(l[2], l[3]);
-              if (bps > 4) o[2] = make_float2(l[4], l[5]);
+              o[0] = l01;
+              if (bps > 2) o[1] = l23;
+              if (bps > 4) o[2] = l45;
             }
           }
       __syncthreads();
