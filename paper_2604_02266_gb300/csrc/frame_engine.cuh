@@ -749,6 +749,53 @@ __device__ __forceinline__ int qam_llr(typename Cx<R>::C x, int bps, R d, R inv_
   return hard;
 }
 
+// pam_llr with the constellation size a compile-time constant (levels and Gray labels fold
+// into constants); bitwise the same results as pam_llr.
+template <typename R, int HB>
+__device__ __forceinline__ void pam_llr_c(R x, R d, R inv_lam, R& o0, R& o1, R& o2) {
+  constexpr int m = 1 << HB;
+  const R inf = (R)INFINITY;
+  R mn0[3] = {inf, inf, inf}, mn1[3] = {inf, inf, inf};
+#pragma unroll
+  for (int i = 0; i < m; ++i) {
+    const R a = (R)(2 * i - (m - 1)) * d;
+    const R di = (x - a) * (x - a);
+    const int g = i ^ (i >> 1);
+#pragma unroll
+    for (int b = 0; b < HB; ++b) {
+      if ((g >> (HB - 1 - b)) & 1) mn1[b] = fmin(mn1[b], di);
+      else mn0[b] = fmin(mn0[b], di);
+    }
+  }
+  o0 = (mn1[0] - mn0[0]) * inv_lam;
+  o1 = HB > 1 ? (mn1[1] - mn0[1]) * inv_lam : (R)0;
+  o2 = HB > 2 ? (mn1[2] - mn0[2]) * inv_lam : (R)0;
+}
+
+// qam_llr_regs for a compile-time constellation (2 HB bits per symbol).
+template <typename R, int HB>
+__device__ __forceinline__ int qam_llr_c(typename Cx<R>::C x, R d, R inv_lam, float2& o01, float2& o23,
+                                         float2& o45) {
+  constexpr int bps = 2 * HB;
+  R i0, i1, i2, q0, q1, q2;
+  pam_llr_c<R, HB>(x.x, d, inv_lam, i0, i1, i2);
+  pam_llr_c<R, HB>(x.y, d, inv_lam, q0, q1, q2);
+  const R z = (R)0;
+  const R l0 = i0;
+  const R l1 = HB == 1 ? q0 : i1;
+  const R l2 = HB == 1 ? z : (HB == 2 ? q0 : i2);
+  const R l3 = HB == 1 ? z : (HB == 2 ? q1 : q0);
+  const R l4 = HB == 3 ? q1 : z;
+  const R l5 = HB == 3 ? q2 : z;
+  o01 = make_float2((float)l0, (float)l1);
+  o23 = make_float2((float)l2, (float)l3);
+  o45 = make_float2((float)l4, (float)l5);
+  int hard = ((l0 < z) << (bps - 1)) | ((l1 < z) << (bps - 2));
+  if (bps > 2) hard |= ((l2 < z) << (bps - 3)) | ((l3 < z) << (bps - 4));
+  if (bps > 4) hard |= ((l4 < z) << 1) | (l5 < z);
+  return hard;
+}
+
 // The same LLRs and hard label as qam_llr, returned in registers: o01 = (l0, l1),
 // o23 = (l2, l3), o45 = (l4, l5).
 template <typename R>

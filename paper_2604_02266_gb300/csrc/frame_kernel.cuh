@@ -8,6 +8,8 @@
 // alternately carries p's and t = H p's quasi-periodic extension.
 #pragma once
 
+#include <type_traits>
+
 #include "frame_engine.cuh"
 
 namespace zotfs {
@@ -417,24 +419,36 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
     if ((A.mode & kDemap) && (io.llr || io.bits)) {
       const R inv_lam = (R)1 / (R)io.lam;
       const int bps = io.bps;
+      // x_hat is staged in shared memory and demapped by a plain loop, so only one
+      // constellation's unrolled code is live at a time
       uint8_t* lab = reinterpret_cast<uint8_t*>(ext);  // labels, bit j of the symbol at bit j
+      C* xs = reinterpret_cast<C*>(ext) + (A.ntx * MN + sizeof(C) - 1) / sizeof(C);
       __syncthreads();  // ext no longer read by anyone
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (t < A.ntx)
 #pragma unroll
-          for (int i = 0; i < E; ++i) {
-            const int q = (j0 + i) * M + k;
-            float2 l01, l23, l45;
-            const int hard = qam_llr_regs<R>(x[t][i], bps, (R)io.pam_d, inv_lam, l01, l23, l45);
-            lab[t * MN + q] = (uint8_t)(__brev((unsigned)hard) >> (32 - bps));  // label bits LSB first
-            if (io.llr) {
-              float2* o = reinterpret_cast<float2*>(io.llr + ((size_t)t * MN + q) * bps);
-              o[0] = l01;
-              if (bps > 2) o[1] = l23;
-              if (bps > 4) o[2] = l45;
-            }
+          for (int i = 0; i < E; ++i) xs[(size_t)t * MN + (j0 + i) * M + k] = x[t][i];
+      __syncthreads();
+      const R pd = (R)io.pam_d;
+      auto demap_all = [&](auto hb) {
+        constexpr int HB = decltype(hb)::value;
+#pragma unroll 1
+        for (int e = tid; e < A.ntx * MN; e += blockDim.x) {
+          float2 l01, l23, l45;
+          const int hard = qam_llr_c<R, HB>(xs[e], pd, inv_lam, l01, l23, l45);
+          lab[e] = (uint8_t)(__brev((unsigned)hard) >> (32 - 2 * HB));  // label bits LSB first
+          if (io.llr) {
+            float2* o = reinterpret_cast<float2*>(io.llr + (size_t)e * (2 * HB));
+            o[0] = l01;
+            if (HB > 1) o[1] = l23;
+            if (HB > 2) o[2] = l45;
           }
+        }
+      };
+      if (bps == 2) demap_all(std::integral_constant<int, 1>{});
+      else if (bps == 4) demap_all(std::integral_constant<int, 2>{});
+      else demap_all(std::integral_constant<int, 3>{});
       __syncthreads();
       if (io.bits) {
         // 8 consecutive symbols fill exactly bps bytes (bits LSB first, symbol by symbol)
