@@ -423,10 +423,14 @@ __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t 
 // not change over the CG iterations.
 template <typename R>
 __device__ __forceinline__ void coef_tables(const PathRecT<R>* pl, int P, const FrameArgs& A, typename Cx<R>::C* cf,
-                                            typename Cx<R>::C* ca) {
+                                            typename Cx<R>::C* ca, int first = -1, int stride = 0) {
   const int M = A.M, N = A.N;
+  if (first < 0) {
+    first = threadIdx.x;
+    stride = blockDim.x;
+  }
 #pragma unroll 2
-  for (int e = threadIdx.x; e < P * M; e += blockDim.x) {
+  for (int e = first; e < P * M; e += stride) {
     const int p = e >> A.logM, k = e & (M - 1);
     const PathRecT<R> rec = pl[p];
     const typename Cx<R>::C t = tab<R>(A, (rec.dl + (N >> 1)) * M + k);
@@ -443,6 +447,14 @@ __device__ __forceinline__ void coef_tables(const PathRecT<R>* pl, int P, const 
 template <typename R>
 __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, PathRecT<R>* tmp, int* keys,
                                           int* nruns_out) {
+  return build_runs<R>(pl, P, runs, tmp, keys, nruns_out, [](int, int) {});
+}
+
+// build_runs that also runs side(first_thread, n_threads) on the sorted list: on the warps
+// other than warp 0 while warp 0 cuts the runs (after it, on warp 0, for one-warp blocks).
+template <typename R, typename Side>
+__device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, PathRecT<R>* tmp, int* keys,
+                                          int* nruns_out, Side side) {
   const int P4 = (P + 3) & ~3;
   for (int p = threadIdx.x; p < P4; p += blockDim.x) keys[p] = p < P ? pl[p].dk * 256 + pl[p].dl : 0x7fffffff;
   __syncthreads();
@@ -512,6 +524,9 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
       s4 += __popc(m4);
     }
     if (lane == 0) *nruns_out = n4 | (n3 << 7) | (n2 << 14) | (n1 << 22);
+    if (blockDim.x == 32) side(0, 32);
+  } else {
+    side((int)threadIdx.x - 32, (int)blockDim.x - 32);
   }
   __syncthreads();
   const int packed = *nruns_out;

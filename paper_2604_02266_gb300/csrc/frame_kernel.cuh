@@ -124,15 +124,16 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
   }
   // sorted path lists -> runs (and coefficient tables); all threads
   auto finalize_lists = [&]() {
-    for (int li = 0; li < nlists; ++li)
-      build_runs<R>(paths + (size_t)li * A.p_max, cnt[li], runs + (size_t)li * A.p_max, sort_tmp, sort_keys,
-                    nruns + li);
-    if constexpr (COEF) {
-      for (int li = 0; li < nlists; ++li) {
+    for (int li = 0; li < nlists; ++li) {
+      PathRec* pl = paths + (size_t)li * A.p_max;
+      const int P = cnt[li];
+      if constexpr (COEF) {  // the coefficient tables are built while warp 0 cuts the runs
         const size_t o = (size_t)li * A.p_max * A.M;
-        coef_tables<R>(paths + (size_t)li * A.p_max, cnt[li], A, coefF + o, coefA + o);
+        build_runs<R>(pl, P, runs + (size_t)li * A.p_max, sort_tmp, sort_keys, nruns + li,
+                      [&](int first, int stride) { coef_tables<R>(pl, P, A, coefF + o, coefA + o, first, stride); });
+      } else {
+        build_runs<R>(pl, P, runs + (size_t)li * A.p_max, sort_tmp, sort_keys, nruns + li);
       }
-      __syncthreads();
     }
   };
   C* ext = reinterpret_cast<C*>(smem + off);
