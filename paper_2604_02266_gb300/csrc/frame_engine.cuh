@@ -450,8 +450,9 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
   return build_runs<R>(pl, P, runs, tmp, keys, nruns_out, [](int, int) {});
 }
 
-// build_runs that also runs side(first_thread, n_threads) on the sorted list: on the warps
-// other than warp 0 while warp 0 cuts the runs (after it, on warp 0, for one-warp blocks).
+// build_runs that also runs side(i, n) on the sorted list, i = this thread's index among the
+// n threads doing it: the warps other than warp 0, while warp 0 cuts the runs (for one-warp
+// blocks, warp 0 after the cutting).
 template <typename R, typename Side>
 __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, PathRecT<R>* tmp, int* keys,
                                           int* nruns_out, Side side) {
@@ -524,11 +525,14 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
       s4 += __popc(m4);
     }
     if (lane == 0) *nruns_out = n4 | (n3 << 7) | (n2 << 14) | (n1 << 22);
-    if (blockDim.x == 32) side(0, 32);
   } else {
     side((int)threadIdx.x - 32, (int)blockDim.x - 32);
   }
   __syncthreads();
+  if (blockDim.x == 32) {  // one warp: the side work follows the cutting
+    side((int)threadIdx.x, 32);
+    __syncthreads();
+  }
   const int packed = *nruns_out;
   return (packed & 127) + ((packed >> 7) & 127) + ((packed >> 14) & 255) + ((packed >> 22) & 511);
 }
