@@ -1,0 +1,110 @@
+"""GPU edge cases of the fused receiver: no tap above the threshold, zero CG iterations, a
+frame with non-finite samples among clean ones, the smallest grid, and independence of the
+per-frame results from the order in which the persistent CTAs take the frames."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import qam
+from tests.gpu_util import TOL_LLR, TOL_X, dev, to_dev
+from tests.test_gpu_rx import _check_frames, _run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+def Plan(*a, **k):
+    from paper_2604_02266_gb300 import Plan as P
+    return P(*a, **k)
+
+
+def _rx(plan, b, iters, theta=None, y_data=None):
+    th = to_dev(b["theta"] if theta is None else theta)
+    yd = to_dev(b["y_data_td"]) if y_data is None else y_data
+    return plan.rx(to_dev(b["y_pilot_td"]), yd, to_dev(b["noise_var"]), th, iters, len(b["noise_var"]),
+                   want_paths=True, want_x=True, want_llr=True)
+
+
+def test_rx_no_tap_above_threshold():
+    """theta above every read-off magnitude: empty path lists, x_hat = 0, LLRs 0, bits 0 (an
+    LLR of exactly 0 decides bit 0), status OK."""
+    M, N, Q, F = 64, 32, 16, 4
+    b = synth.fractional_batch(F, seed=71, M=M, N=N, Q=Q)
+    out = _rx(Plan(M, N, 1, 1, Q), b, 10, theta=np.full(F, 1e6, np.float32))
+    torch.cuda.synchronize()
+    assert (out["paths"].count.cpu().numpy() == 0).all()
+    assert (out["status"].cpu().numpy() == 0).all()
+    assert not out["x_hat"].abs().any()
+    assert not out["llr"].abs().any()
+    assert not out["bits"].any()
+
+
+def test_rx_zero_iterations():
+    """Algorithm 1 with no iteration returns x = 0 whatever the paths; the lists still match the
+    oracle's read-off."""
+    M, N, Q, F = 32, 32, 4, 4
+    b = synth.fractional_batch(F, seed=72, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    out = _rx(plan, b, 0)
+    torch.cuda.synchronize()
+    assert not out["x_hat"].abs().any()
+    assert not out["bits"].any()
+    wx, wl, mm = _check_frames(b, out, range(F), M, N, 1, 1, Q, 0, plan.p_max)
+    assert wx == 0.0 and mm == 0
+
+
+def test_rx_nonfinite_frame_is_flagged_and_isolated():
+    """A NaN sample in one data frame sets that frame's status to ZOTFS_ENONFINITE; every other
+    frame's outputs are bitwise those of the same batch without the NaN."""
+    from paper_2604_02266_gb300 import ENONFINITE
+    M, N, Q, F = 64, 32, 16, 8
+    b = synth.fractional_batch(F, seed=73, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    clean = _rx(plan, b, 10)
+    yd = to_dev(b["y_data_td"]).clone()
+    yd[3, 0, 100] = complex(float("nan"), 0.0)
+    dirty = _rx(plan, b, 10, y_data=yd)
+    torch.cuda.synchronize()
+    st = dirty["status"].cpu().numpy()
+    assert st[3] == ENONFINITE
+    others = [f for f in range(F) if f != 3]
+    assert (st[others] == clean["status"].cpu().numpy()[others]).all()
+    for key in ("x_hat", "llr", "bits"):
+        assert torch.equal(dirty[key][others], clean[key][others]), key
+
+
+@pytest.mark.parametrize("M,N,Q", [(16, 8, 4), (16, 16, 64), (256, 8, 16)])
+def test_rx_small_and_ragged_grids(M, N, Q):
+    b = synth.fractional_batch(3, seed=74 + M + N, M=M, N=N, Q=Q, delay_max=2, doppler_max=1)
+    plan = Plan(M, N, 1, 1, Q)
+    out = _run(plan, b, 10, 3)
+    torch.cuda.synchronize()
+    wx, wl, mm = _check_frames(b, out, range(3), M, N, 1, 1, Q, 10, plan.p_max)
+    assert wx < TOL_X and wl < TOL_LLR and mm == 0, (wx, wl, mm)
+
+
+def test_rx_results_do_not_depend_on_frame_order():
+    """A launch with more frames than resident CTAs takes them heaviest first; per-frame
+    results are bitwise those of the same frames run in small launches in index order."""
+    M, N, Q, F = 64, 32, 16, 400
+    b = synth.fractional_batch(F, seed=75, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    whole = _rx(plan, b, 10)
+    parts = []
+    for s in range(0, F, 50):
+        sub = {k: (v[s:s + 50] if isinstance(v, np.ndarray) and v.ndim > 0 and v.shape[0] == F else v)
+               for k, v in b.items()}
+        parts.append(_rx(plan, sub, 10))
+    torch.cuda.synchronize()
+    for key in ("x_hat", "llr", "bits", "status"):
+        assert torch.equal(whole[key], torch.cat([p[key] for p in parts])), key
+    assert torch.equal(whole["paths"].count, torch.cat([p["paths"].count for p in parts]))
