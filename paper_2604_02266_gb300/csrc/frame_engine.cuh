@@ -292,9 +292,11 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
     const C hv = cmul(v[i], tw<R>(A, widx));
     mcol[l * rstep] = v[i];
     hcol[l * rstep] = hv;
-    if (l < E + 3) {
-      mcol[(l + N) * rstep] = v[i];
-      hcol[(l + N) * rstep] = hv;
+    // periodic halo rows N .. N + E + 2 hold row (r mod N): one copy when N >= E + 3, two
+    // for the short grids (N = 8 with E = 8, N = 16 with E = 16)
+    for (int r = l + N; r < N + E + 3; r += N) {
+      mcol[r * rstep] = v[i];
+      hcol[r * rstep] = hv;
     }
   }
 }

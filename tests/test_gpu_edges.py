@@ -7,7 +7,6 @@ import pytest
 import torch
 
 import synth
-from oracle import qam
 from tests.gpu_util import TOL_LLR, TOL_X, dev, to_dev
 from tests.test_gpu_rx import _check_frames, _run
 
@@ -35,17 +34,20 @@ def _rx(plan, b, iters, theta=None, y_data=None):
 
 
 def test_rx_no_tap_above_threshold():
-    """theta above every read-off magnitude: empty path lists, x_hat = 0, LLRs 0, bits 0 (an
-    LLR of exactly 0 decides bit 0), status OK."""
+    """theta above every read-off magnitude: empty path lists, x_hat = 0, status OK, and the
+    LLRs and bits of x = 0 as the oracle computes them (the Gray bits that separate inner
+    from outer levels are not ties at 0)."""
     M, N, Q, F = 64, 32, 16, 4
-    b = synth.fractional_batch(F, seed=71, M=M, N=N, Q=Q)
-    out = _rx(Plan(M, N, 1, 1, Q), b, 10, theta=np.full(F, 1e6, np.float32))
+    b = dict(synth.fractional_batch(F, seed=71, M=M, N=N, Q=Q))
+    b["theta"] = np.full(F, 1e6, np.float32)
+    plan = Plan(M, N, 1, 1, Q)
+    out = _rx(plan, b, 10)
     torch.cuda.synchronize()
     assert (out["paths"].count.cpu().numpy() == 0).all()
     assert (out["status"].cpu().numpy() == 0).all()
     assert not out["x_hat"].abs().any()
-    assert not out["llr"].abs().any()
-    assert not out["bits"].any()
+    wx, wl, mm = _check_frames(b, out, range(F), M, N, 1, 1, Q, 10, plan.p_max)
+    assert wx == 0.0 and wl < TOL_LLR and mm == 0, (wx, wl, mm)
 
 
 def test_rx_zero_iterations():
