@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
       }
       __syncthreads();
     }
-    if (io.status && tid == 0) *io.status = status_from_bits(st);
+    publish_status(A, io.status, st);
   }
 }
 

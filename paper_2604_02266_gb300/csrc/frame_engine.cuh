@@ -106,7 +106,25 @@ struct FrameArgs {
   // the CTAs take the frames (a permutation of [0, n_frames))
   const zotfs_frame_desc* descs;
   const int* frame_ids;
+  // status lives in host-mapped memory that the host polls: each frame's outputs are made
+  // visible system-wide before its status is stored (serving: per-frame completion)
+  int status_fence;
 };
+
+// Store a frame's final status (thread 0).  With A.status_fence every thread of the block has
+// finished the frame's outputs (barrier) and they are fenced at system scope first, so a host
+// that sees the status may read the outputs.
+__device__ __forceinline__ void publish_status(const FrameArgs& A, int32_t* status, int st_bits) {
+  if (A.status_fence) __syncthreads();
+  if (status && threadIdx.x == 0) {
+    if (A.status_fence) {
+      __threadfence_system();
+      *reinterpret_cast<volatile int32_t*>(status) = status_from_bits(st_bits);
+    } else {
+      *status = status_from_bits(st_bits);
+    }
+  }
+}
 
 // Global-memory path lists of one frame: list li (= r * n_tx + t) has count[li] entries at
 // [li * p_max, li * p_max + count[li]) of dk, dl and h.
@@ -812,8 +830,8 @@ __device__ __forceinline__ int qam_llr_c(typename Cx<R>::C x, R d, R inv_lam, fl
   o23 = make_float2((float)l2, (float)l3);
   o45 = make_float2((float)l4, (float)l5);
   int hard = ((l0 < z) << (bps - 1)) | ((l1 < z) << (bps - 2));
-  if (bps > 2) hard |= ((l2 < z) << (bps - 3)) | ((l3 < z) << (bps - 4));
-  if (bps > 4) hard |= ((l4 < z) << 1) | (l5 < z);
+  if constexpr (bps > 2) hard |= ((l2 < z) << (bps - 3)) | ((l3 < z) << (bps - 4));
+  if constexpr (bps > 4) hard |= ((l4 < z) << 1) | (l5 < z);
   return hard;
 }
 

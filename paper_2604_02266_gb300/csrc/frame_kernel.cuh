@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
       }
       __syncthreads();
     }
-    if (io.status && tid == 0) *io.status = status_from_bits(st);
+    publish_status(A, io.status, st);
   }
 }
 

@@ -59,8 +59,10 @@ struct Wave {
   int* h_ids = nullptr;  // pinned
   int* d_ids = nullptr;
   int* d_counters = nullptr;
-  int32_t* d_status = nullptr;
-  int32_t* h_status = nullptr;  // pinned
+  int32_t* h_status = nullptr;  // pinned, mapped: each frame's status, -1 until the kernel stores it
+  int32_t* d_status = nullptr;  // the device's view of h_status
+  std::vector<char> reported;   // completion already published
+  int n_reported = 0;
   char* d_big = nullptr;        // large-frame scratch: big_slots slots of big_slot_bytes
   cudaStream_t main = nullptr;
   cudaStream_t work[kWorkers] = {};
@@ -214,6 +216,9 @@ cudaError_t launch_wave(zotfs_server_s* s, Wave& w) {
     d.path_dl = reinterpret_cast<int16_t*>(base + a.pdl);
     d.path_h = reinterpret_cast<float*>(base + a.ph);
   }
+  for (int i = 0; i < n; ++i) reinterpret_cast<volatile int32_t*>(w.h_status)[i] = -1;
+  w.reported.assign(n, 0);
+  w.n_reported = 0;
   cudaError_t e = cudaMemcpyAsync(w.d_desc, w.h_desc, sizeof(zotfs_frame_desc) * n, cudaMemcpyHostToDevice, w.main);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w.d_ids, w.h_ids, sizeof(int) * n, cudaMemcpyHostToDevice, w.main);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.d_counters, 0, sizeof(int) * buckets.size(), w.main);
@@ -259,6 +264,7 @@ cudaError_t launch_wave(zotfs_server_s* s, Wave& w) {
     A.n_frames = nf;
     A.work_counter = w.d_counters + b;
     A.status = w.d_status;
+    A.status_fence = 1;
     A.descs = w.d_desc;
     A.frame_ids = w.d_ids + off;
     FrameCfg fc;
@@ -286,31 +292,30 @@ cudaError_t launch_wave(zotfs_server_s* s, Wave& w) {
       if (e == cudaSuccess) e = cudaStreamWaitEvent(w.main, w.wdone[wi], 0);
       if (e != cudaSuccess) return e;
     }
-  e = cudaMemcpyAsync(w.h_status, w.d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, w.main);
-  if (e == cudaSuccess) e = cudaEventRecord(w.done, w.main);
-  return e;
+  return cudaEventRecord(w.done, w.main);
 }
 
 void scheduler(zotfs_server_s* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    // reap finished waves
+    // publish frames as their statuses appear in mapped memory; free waves whose work is done
     bool any_busy = false;
     for (Wave& w : s->waves) {
       if (!w.busy) continue;
       const cudaError_t q = cudaEventQuery(w.done);
-      if (q == cudaErrorNotReady) {
-        any_busy = true;
-        continue;
-      }
+      const bool finished = q != cudaErrorNotReady;
       const int64_t t = now_ns();
       for (size_t i = 0; i < w.frames.size(); ++i) {
+        if (w.reported[i]) continue;
+        const int32_t v = reinterpret_cast<volatile const int32_t*>(w.h_status)[i];
+        if (v < 0 && !finished) continue;
+        std::atomic_thread_fence(std::memory_order_acquire);
         const Admitted& a = w.frames[i];
         zotfs_completion c;
         std::memset(&c, 0, sizeof(c));
         c.tag = a.p.r.tag;
-        c.status = q == cudaSuccess ? w.h_status[i] : ZOTFS_ECUDA;
+        c.status = (q == cudaSuccess || !finished) && v >= 0 ? v : ZOTFS_ECUDA;
         c.n_lists = a.p.r.n_rx * a.p.r.n_tx;
         c.arrival_ns = a.p.arrival_ns;
         c.admit_ns = a.admit_ns;
@@ -326,6 +331,12 @@ void scheduler(zotfs_server_s* s) {
         s->live_req[c.tag] = a.p.r;
         s->done.push_back(c);
         ++s->st.completed;
+        w.reported[i] = 1;
+        ++w.n_reported;
+      }
+      if (!finished) {
+        any_busy = true;
+        continue;
       }
       if (q != cudaSuccess) s->thread_error = cudaGetErrorString(q);
       w.frames.clear();
@@ -393,7 +404,6 @@ void destroy_waves(zotfs_server_s* s) {
     if (w.h_ids) cudaFreeHost(w.h_ids);
     if (w.d_ids) cudaFree(w.d_ids);
     if (w.d_counters) cudaFree(w.d_counters);
-    if (w.d_status) cudaFree(w.d_status);
     if (w.h_status) cudaFreeHost(w.h_status);
     if (w.d_big) cudaFree(w.d_big);
     for (int i = 0; i < kWorkers; ++i) {
@@ -472,8 +482,8 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
     if (e == cudaSuccess) e = cudaHostAlloc(&w.h_ids, sizeof(int) * n, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&w.d_ids, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMalloc(&w.d_counters, sizeof(int) * kMaxBuckets);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_status, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_status, sizeof(int32_t) * n, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_status, sizeof(int32_t) * n, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&w.d_status), w.h_status, 0);
     if (e == cudaSuccess && s->big_slots)
       e = cudaMalloc(&w.d_big, s->big_slot_bytes * (size_t)s->big_slots);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.main, cudaStreamNonBlocking);
