@@ -486,8 +486,9 @@ def impl_serve(args):
         b = synth.fractional_batch(args.pool, seed=SEED + 7919 * ci, M=m, N=n, Q=q, n_rx=a, n_tx=a, n_paths=n_paths)
         pool[(m, n, a, q)] = (torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev),
                               b["noise_var"].astype(float), b["theta"].astype(float))
+    light = args.light_work if args.serve_mix == "c5" else 0
     srv = Server(p_max=64, max_wave_frames=args.wave_frames, waves_in_flight=args.waves, keep_llr=False,
-                 arena_bytes=4 << 30, max_M=256, max_N=64, max_ant=4)
+                 arena_bytes=4 << 30, max_M=256, max_N=64, max_ant=4, light_work=light)
 
     def make(n, g, tag0):
         reqs, meta = [], []
@@ -563,7 +564,7 @@ def impl_serve(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "mix": args.serve_mix, "duration_s": args.duration,
                        "pool_frames_per_class": args.pool, "max_wave_frames": args.wave_frames,
-                       "waves_in_flight": args.waves},
+                       "waves_in_flight": args.waves, "light_work": light},
             "runs": runs, "server_stats": stats}
     print(json.dumps(line))
     return 0
@@ -737,6 +738,8 @@ def main():
                     help="serve: c5 = mixed shapes/antennas/QAM, c2 = 64x32 SISO 16-QAM frames only")
     ap.add_argument("--wave-frames", type=int, default=256, help="serve: frames admitted per wave")
     ap.add_argument("--waves", type=int, default=4, help="serve: waves in flight")
+    ap.add_argument("--light-work", type=int, default=8192,
+                    help="serve (c5 mix): frames with M*N*n_rx*n_tx up to this run in their own waves")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 20 if args.impl == "reference" else 2000

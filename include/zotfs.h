@@ -346,6 +346,10 @@ typedef struct zotfs_server_opts {
   int32_t keep_llr;         /* also keep float32 LLRs per frame */
   int64_t arena_bytes;      /* device bytes for admitted frames' outputs */
   int32_t max_M, max_N, max_ant;  /* largest frame accepted (sizes the large-frame scratch) */
+  int32_t light_work;       /* > 0: frames with M*N*n_rx*n_tx <= light_work queue and run in
+                               their own waves (the first half of the wave slots), so frames
+                               that take long never hold a wave slot that short ones wait for;
+                               0: one queue */
 } zotfs_server_opts;
 
 typedef struct zotfs_request {

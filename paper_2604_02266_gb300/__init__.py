@@ -349,9 +349,9 @@ class Server:
     (pilot and data TD frames, complex64) that must stay alive until their completion."""
 
     def __init__(self, p_max=64, max_wave_frames=256, waves_in_flight=4, keep_llr=False, arena_bytes=1 << 30,
-                 max_M=256, max_N=64, max_ant=4):
+                 max_M=256, max_N=64, max_ant=4, light_work=0):
         o = Z.zotfs_server_opts(p_max, max_wave_frames, waves_in_flight, int(bool(keep_llr)), arena_bytes, max_M,
-                                max_N, max_ant)
+                                max_N, max_ant, light_work)
         h = C.c_void_p()
         Z.check(Z.zotfs_server_create(C.byref(o), C.byref(h)))
         self._h = h

@@ -77,7 +77,7 @@ class zotfs_tuning_result(C.Structure):
 class zotfs_server_opts(C.Structure):
     _fields_ = [("p_max", C.c_int32), ("max_wave_frames", C.c_int32), ("waves_in_flight", C.c_int32),
                 ("keep_llr", C.c_int32), ("arena_bytes", C.c_int64), ("max_M", C.c_int32), ("max_N", C.c_int32),
-                ("max_ant", C.c_int32)]
+                ("max_ant", C.c_int32), ("light_work", C.c_int32)]
 
 
 class zotfs_request(C.Structure):

@@ -53,6 +53,7 @@ struct Admitted {
 
 struct Wave {
   bool busy = false;
+  int cls = -1;  // the queue it takes frames from: 0 light, 1 heavy, -1 either (one queue)
   std::vector<Admitted> frames;
   zotfs_frame_desc* h_desc = nullptr;  // pinned
   zotfs_frame_desc* d_desc = nullptr;
@@ -83,7 +84,8 @@ struct zotfs_server_s {
   std::vector<Wave> waves;
   size_t big_slot_bytes = 0;
   int big_slots = 0;
-  std::deque<Pending> pending;
+  std::deque<Pending> pending[2];  // light, heavy (one queue: everything is heavy)
+  bool split = false;              // light frames have their own queue and wave slots
   std::deque<zotfs_completion> done;
   std::mutex mu;
   std::condition_variable cv;
@@ -96,6 +98,13 @@ struct zotfs_server_s {
 namespace {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int frame_class(const zotfs_server_s* s, const zotfs_request& r) {
+  const long long work = (long long)r.M * r.N * r.n_rx * r.n_tx;
+  return (s->split && work <= s->o.light_work) ? 0 : 1;
+}
+
+size_t pending_total(const zotfs_server_s* s) { return s->pending[0].size() + s->pending[1].size(); }
 
 bool arena_alloc(zotfs_server_s* s, size_t bytes, size_t& off) {
   for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
@@ -342,20 +351,18 @@ void scheduler(zotfs_server_s* s) {
       w.frames.clear();
       w.busy = false;
     }
-    if (s->stop && s->pending.empty() && !any_busy) break;
-    // admit pending frames into a free wave
-    Wave* free_w = nullptr;
-    for (Wave& w : s->waves)
-      if (!w.busy) {
-        free_w = &w;
-        break;
-      }
+    if (s->stop && pending_total(s) == 0 && !any_busy) break;
+    // admit pending frames into the free waves, each from its own queue
     bool launched = false;
-    if (free_w && !s->pending.empty()) {
+    for (Wave& wv : s->waves) {
+      if (wv.busy) continue;
+      Wave* free_w = &wv;
+      std::deque<Pending>& queue = s->pending[free_w->cls == 0 ? 0 : 1];
+      if (queue.empty()) continue;
       const int64_t t = now_ns();
-      while (!s->pending.empty() && (int)free_w->frames.size() < s->o.max_wave_frames) {
+      while (!queue.empty() && (int)free_w->frames.size() < s->o.max_wave_frames) {
         Admitted a;
-        a.p = s->pending.front();
+        a.p = queue.front();
         a.bytes = frame_bytes(s, a.p.r, &a);
         if (a.bytes > s->arena_bytes) {  // can never fit: fail the frame instead of blocking the queue
           zotfs_completion c;
@@ -367,13 +374,13 @@ void scheduler(zotfs_server_s* s) {
           s->done.push_back(c);
           ++s->st.rejected_too_large;
           ++s->st.completed;
-          s->pending.pop_front();
+          queue.pop_front();
           continue;
         }
         if (!arena_alloc(s, a.bytes, a.off)) break;  // wait for releases
         a.admit_ns = t;
         free_w->frames.push_back(a);
-        s->pending.pop_front();
+        queue.pop_front();
         ++s->st.admitted;
       }
       if (!free_w->frames.empty()) {
@@ -432,7 +439,7 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
   if (o.p_max < 1 || o.p_max > 256 || o.max_wave_frames < 1 || o.max_wave_frames > 4096 ||
       o.waves_in_flight < 1 || o.waves_in_flight > 16 || o.arena_bytes < 4096 || !is_pow2(o.max_M) ||
       o.max_M < 16 || o.max_M > 256 || !is_pow2(o.max_N) || o.max_N < 8 || o.max_N > 64 || o.max_ant < 1 ||
-      o.max_ant > 4) {
+      o.max_ant > 4 || o.light_work < 0) {
     set_error("zotfs_server_create: options out of range");
     return ZOTFS_EINVAL;
   }
@@ -474,6 +481,9 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
     else s->free_list[0] = s->arena_bytes;
   }
   s->waves.resize(o.waves_in_flight);
+  s->split = o.light_work > 0 && o.waves_in_flight >= 2;
+  if (s->split)  // the first half of the slots serve light frames
+    for (int i = 0; i < o.waves_in_flight; ++i) s->waves[i].cls = i < o.waves_in_flight / 2 ? 0 : 1;
   for (Wave& w : s->waves) {
     if (st) break;
     const int n = o.max_wave_frames;
@@ -529,7 +539,7 @@ zotfs_status zotfs_server_submit(zotfs_server s, const zotfs_request* reqs, int 
       set_error("zotfs_server_submit: server is shutting down");
       return ZOTFS_EINVAL;
     }
-    for (int i = 0; i < n; ++i) s->pending.push_back(Pending{reqs[i], t});
+    for (int i = 0; i < n; ++i) s->pending[frame_class(s, reqs[i])].push_back(Pending{reqs[i], t});
     s->st.submitted += n;
   }
   s->cv.notify_one();
@@ -554,7 +564,8 @@ zotfs_status zotfs_server_replay(zotfs_server s, const zotfs_request* reqs, cons
     if (j > i) {
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        for (int q = i; q < j; ++q) s->pending.push_back(Pending{reqs[q], t0 + (int64_t)(arrival_s[q] * 1e9)});
+        for (int q = i; q < j; ++q)
+          s->pending[frame_class(s, reqs[q])].push_back(Pending{reqs[q], t0 + (int64_t)(arrival_s[q] * 1e9)});
         s->st.submitted += j - i;
       }
       s->cv.notify_one();
@@ -643,7 +654,7 @@ zotfs_status zotfs_server_get_stats(zotfs_server s, zotfs_server_stats* out) {
   }
   std::lock_guard<std::mutex> lk(s->mu);
   *out = s->st;
-  out->pending = (int64_t)s->pending.size();
+  out->pending = (int64_t)pending_total(s);
   out->arena_in_use = (int64_t)s->in_use;
   out->arena_high_water = (int64_t)s->high_water;
   if (!s->thread_error.empty()) {
@@ -658,7 +669,8 @@ zotfs_status zotfs_server_destroy(zotfs_server s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
-    s->pending.clear();
+    s->pending[0].clear();
+    s->pending[1].clear();
   }
   s->cv.notify_one();
   if (s->th.joinable()) s->th.join();

@@ -144,3 +144,33 @@ def test_replay_poisson_arrivals():
         assert (np.diff(arr) >= 0).all()  # arrival stamps follow the schedule
     finally:
         srv.close()
+
+
+def test_light_frames_have_their_own_queue():
+    """With light_work set, small frames queue and run in their own wave slots: every frame
+    completes with the same results as alone, and the heavy frames never delay the light
+    ones' admission behind them."""
+    from paper_2604_02266_gb300 import Plan, Server
+    frames = _frames(24, seed=15, shapes=[(32, 16), (128, 64)], ants=[(1, 1), (4, 4)])
+    srv = Server(p_max=64, max_wave_frames=4, waves_in_flight=4, keep_llr=True, arena_bytes=256 << 20, max_M=128,
+                 max_N=64, max_ant=4, light_work=2048)
+    try:
+        srv.submit([_req(Server, i, fr) for i, fr in enumerate(frames)])
+        got = _drain(srv, len(frames))
+        for i, fr in enumerate(frames):
+            assert got[i][0] in (0, 6), (i, got[i][0])
+            M, N, nrx, ntx, Q = fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"]
+            served = srv.read(i, ntx, M * N, int(np.log2(Q)), nrx * ntx, llr=True)
+            b = fr["b"]
+            alone = Plan(M, N, nrx, ntx, Q).rx(fr["yp"][None], fr["yd"][None], to_dev(b["noise_var"]),
+                                               to_dev(b["theta"]), fr["iters"], 1, want_llr=True)
+            assert np.array_equal(served["bits"], alone["bits"].cpu().numpy().reshape(-1)), i
+            assert np.array_equal(served["llr"], alone["llr"].cpu().numpy().reshape(-1)), i
+            srv.release(i)
+        light = [i for i, fr in enumerate(frames) if fr["M"] * fr["N"] * fr["nrx"] * fr["ntx"] <= 2048]
+        heavy = [i for i in range(len(frames)) if i not in light]
+        assert light and heavy
+        # all were submitted together: the light frames' admissions do not wait for heavy ones
+        assert max(got[i][2] for i in light) <= max(got[i][3] for i in heavy)
+    finally:
+        srv.close()
