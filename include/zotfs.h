@@ -134,6 +134,11 @@ typedef struct zotfs_tuning {
   int32_t threads_per_frame;
   int32_t fft_radix;
   int32_t ctas_per_sm;  /* resident CTAs per SM the persistent grid is sized for; 0 = max */
+  int32_t cluster;      /* 2 or 4: each frame runs on a thread-block cluster of that many CTAs
+                           (one per SM), which exchange the CG vectors through distributed
+                           shared memory -- lower per-frame latency, for SISO plans with a
+                           separate pilot whose frame fits one CTA; the plan falls back to one
+                           CTA per frame where it does not apply.  0 or 1: one CTA per frame */
 } zotfs_tuning;
 zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* tuning);
 zotfs_status zotfs_plan_get_tuning(zotfs_plan plan, zotfs_tuning* tuning);

@@ -131,14 +131,15 @@ class Plan:
             setattr(o, k, v)
         Z.check(Z.zotfs_plan_set_options(self._h, C.byref(o)))
 
-    def set_tuning(self, threads_per_frame=0, fft_radix=0, ctas_per_sm=0):
-        t = Z.zotfs_tuning(threads_per_frame, fft_radix, ctas_per_sm)
+    def set_tuning(self, threads_per_frame=0, fft_radix=0, ctas_per_sm=0, cluster=0):
+        t = Z.zotfs_tuning(threads_per_frame, fft_radix, ctas_per_sm, cluster)
         Z.check(Z.zotfs_plan_set_tuning(self._h, C.byref(t)))
 
     def tuning(self):
         t = Z.zotfs_tuning()
         Z.check(Z.zotfs_plan_get_tuning(self._h, C.byref(t)))
-        return {"threads_per_frame": t.threads_per_frame, "fft_radix": t.fft_radix, "ctas_per_sm": t.ctas_per_sm}
+        return {"threads_per_frame": t.threads_per_frame, "fft_radix": t.fft_radix, "ctas_per_sm": t.ctas_per_sm,
+                "cluster": t.cluster}
 
     @property
     def p_max(self):

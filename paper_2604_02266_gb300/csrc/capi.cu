@@ -202,7 +202,32 @@ static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 2
 
 // Launch the shared-memory frame kernel when the shape fits one CTA, else the large-frame
 // kernel on the plan's scratch slots.
+// The cluster receiver, where the plan asks for it and the call qualifies: FP32 SISO, the
+// data frame in the time domain, a separate pilot (or loaded lists), no single apply / DZT.
+static bool cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, const FrameArgs& A, ClusterCfg& cc) {
+  if (plan->tune.cluster < 2 || real_bytes_of(plan) != 4 || A.y_is_dd || (A.mode & (kApply | kDzt | kLoadX)))
+    return false;
+  if (!(A.mode & kCG)) return false;
+  if ((A.mode & kEstimate) && A.pilot_mode != ZOTFS_PILOT_SEPARATE) return false;
+  return choose_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.cluster, cc);
+}
+
 static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream) {
+  ClusterCfg cc;
+  if (cluster_applies(plan, nrx, ntx, A, cc)) {
+    int clusters = 0;
+    cudaError_t e = cluster_max_active(cc, clusters);
+    if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
+    if (clusters < 1) {
+      set_error("cluster receiver does not fit on the device");
+      return ZOTFS_EUNSUPPORTED;
+    }
+    if (clusters > A.n_frames) clusters = A.n_frames;
+    e = cluster_launch(cc, A, radix_of(plan), clusters, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cluster kernel launch");
+    ++g_launches;
+    return ZOTFS_OK;
+  }
   FrameCfg cfg;
   if (choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, cfg,
                        real_bytes_of(plan)))
@@ -387,6 +412,7 @@ zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* t) {
   if (t->fft_radix != 0 && t->fft_radix != 2 && t->fft_radix != 4) return inval("fft_radix must be 0, 2 or 4");
   if (t->threads_per_frame < 0 || t->threads_per_frame > 1024) return inval("threads_per_frame");
   if (t->ctas_per_sm < 0) return inval("ctas_per_sm");
+  if (t->cluster < 0 || t->cluster == 3 || t->cluster > 4) return inval("cluster must be 0, 1, 2 or 4");
   zotfs_tuning n = *t;
   if (n.fft_radix == 0) n.fft_radix = kDefaultRadix;
   if (n.threads_per_frame > 0) {

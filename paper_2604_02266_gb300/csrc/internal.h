@@ -90,6 +90,15 @@ cudaError_t big_launch(const BigCfg& cfg, const FrameArgs& A, int radix, int gri
                        cudaStream_t stream);
 cudaError_t big_occupancy(const BigCfg& cfg, int& blocks);
 
+// Cluster receiver (cluster_variant.cu): one SISO frame on C CTAs of a thread-block cluster.
+struct ClusterCfg {
+  int C, T;
+  size_t smem;
+};
+bool choose_cluster_cfg(int M, int N, int nrx, int ntx, int p_max, int C, ClusterCfg& cfg);
+cudaError_t cluster_launch(const ClusterCfg& cfg, const FrameArgs& A, int radix, int clusters, cudaStream_t stream);
+cudaError_t cluster_max_active(const ClusterCfg& cfg, int& clusters);
+
 // FrameArgs for a descriptor-driven launch over frames of one geometry (batch.cu); per-frame
 // values (noise, threshold, QAM order, pilot amplitude, iterations, buffers) come from the
 // descriptors.
