@@ -134,11 +134,14 @@ typedef struct zotfs_tuning {
   int32_t threads_per_frame;
   int32_t fft_radix;
   int32_t ctas_per_sm;  /* resident CTAs per SM the persistent grid is sized for; 0 = max */
-  int32_t cluster;      /* 2 or 4: each frame runs on a thread-block cluster of that many CTAs
-                           (one per SM), which exchange the CG vectors through distributed
-                           shared memory -- lower per-frame latency, for SISO plans with a
-                           separate pilot whose frame fits one CTA; the plan falls back to one
-                           CTA per frame where it does not apply.  0 or 1: one CTA per frame */
+  int32_t cluster;      /* the cluster receiver: each frame on a thread-block cluster of
+                           CTAs (one per SM) that exchange the CG vectors through distributed
+                           shared memory, for SISO plans (separate pilot or given lists) whose
+                           extension replica fits one CTA's shared memory.  2 or 4: that many
+                           CTAs wherever it applies.  0: 2 CTAs for frames too large for the
+                           one-CTA shared-memory kernel (instead of the large-frame kernel,
+                           whose vectors live in L2), when the call has at most one frame per
+                           two SMs -- latency first while the GPU has idle SMs.  1: never */
 } zotfs_tuning;
 zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* tuning);
 zotfs_status zotfs_plan_get_tuning(zotfs_plan plan, zotfs_tuning* tuning);

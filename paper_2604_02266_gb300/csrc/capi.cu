@@ -205,11 +205,20 @@ static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 2
 // The cluster receiver, where the plan asks for it and the call qualifies: FP32 SISO, the
 // data frame in the time domain, a separate pilot (or loaded lists), no single apply / DZT.
 static bool cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, const FrameArgs& A, ClusterCfg& cc) {
-  if (plan->tune.cluster < 2 || real_bytes_of(plan) != 4 || A.y_is_dd || (A.mode & (kApply | kDzt | kLoadX)))
+  if (plan->tune.cluster == 1 || real_bytes_of(plan) != 4 || A.y_is_dd || (A.mode & (kApply | kDzt | kLoadX)))
     return false;
   if (!(A.mode & kCG)) return false;
   if ((A.mode & kEstimate) && A.pilot_mode != ZOTFS_PILOT_SEPARATE) return false;
-  return choose_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.cluster, cc);
+  if (plan->tune.cluster >= 2)
+    return choose_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.cluster, cc);
+  // automatic: only where the one-CTA shared-memory kernel does not fit, and while the call
+  // leaves SMs idle
+  FrameCfg fc;
+  if (choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, fc,
+                       real_bytes_of(plan)))
+    return false;
+  if ((long long)A.n_frames * 2 > plan->sm_count) return false;
+  return choose_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, 2, cc);
 }
 
 static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream) {
