@@ -124,3 +124,12 @@ def check_path_list(M, N, lib_list, heff, theta, p_max, region=None, rtol=1e-4):
         assert not listed[mustnot & region].any(), "a tap below the top-P cut is listed"
         n_amb += int((amb_k & passing).sum())
     return n_amb
+
+
+def one_cta_plan(M, N, nrx, ntx, Q, **opts):
+    """A plan that runs every frame on one CTA (no cluster receiver): the kernels that uneven
+    batches and the serving loop use, so their results can be compared bit for bit."""
+    from paper_2604_02266_gb300 import Plan
+    plan = Plan(M, N, nrx, ntx, Q, **opts)
+    plan.set_tuning(cluster=1)
+    return plan

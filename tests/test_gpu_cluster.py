@@ -78,3 +78,18 @@ def test_cluster_equalize_given_lists():
         y_dd = zak.vec(zak.dzt(y[f, 0].astype(complex), M, N))
         ref = eq.cga([[lists[f]]], y_dd, float(lam[f]), 12)
         assert rel_l2(x[f].reshape(-1), ref) < TOL_X, f
+
+
+def test_automatic_cluster_for_large_frames_at_low_load():
+    """With the default tuning, a SISO frame too large for the one-CTA shared-memory kernel
+    (128x64) runs on a 2-CTA cluster when the call leaves SMs idle: bit for bit the same as
+    asking for cluster = 2, and within tolerance of the large-frame kernel (cluster = 1)."""
+    M, N, Q, F = 128, 64, 16, 2
+    b = synth.fractional_batch(F, seed=90, M=M, N=N, Q=Q)
+    auto = _rx(_plan(M, N, Q, 0), b, 10)
+    two = _rx(_plan(M, N, Q, 2), b, 10)
+    big = _rx(_plan(M, N, Q, 1), b, 10)
+    torch.cuda.synchronize()
+    for key in ("x_hat", "llr", "bits", "status"):
+        assert torch.equal(auto[key], two[key]), key
+    assert rel_l2(auto["x_hat"].cpu().numpy(), big["x_hat"].cpu().numpy()) < 2 * TOL_X

@@ -8,7 +8,7 @@ import torch
 
 import synth
 from oracle import zak, equalizer as eq
-from tests.gpu_util import TOL_LIN, TOL_LLR, TOL_X, dev, fill_paths, random_pathlist, rel_l2, to_dev
+from tests.gpu_util import TOL_LIN, TOL_LLR, TOL_X, dev, fill_paths, one_cta_plan, random_pathlist, rel_l2, to_dev
 from tests.test_gpu_rx import _check_frames, _run
 from tests.test_gpu_stages import _cg_case
 
@@ -104,6 +104,6 @@ def test_rx_batch_with_large_buckets():
     assert set(status.cpu().numpy().tolist()) <= {0, 6}
     for i, (b, o) in enumerate(keep):
         M, N, nrx, ntx, Q = shapes[i % len(shapes)]
-        alone = _run(Plan(M, N, nrx, ntx, Q), b, 10, 1)
+        alone = _run(one_cta_plan(M, N, nrx, ntx, Q), b, 10, 1)
         assert torch.equal(alone["x_hat"][0], o["x"]), i
         assert torch.equal(alone["bits"][0], o["bits"]), i

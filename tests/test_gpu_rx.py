@@ -12,7 +12,7 @@ import torch
 
 import synth
 from oracle import zak, ddchannel as dc, equalizer as eq, qam
-from tests.gpu_util import (TOL_LLR, TOL_X, check_path_list, dev, pathlist_from_lib, rel_l2, to_dev)
+from tests.gpu_util import (TOL_LLR, TOL_X, check_path_list, dev, one_cta_plan, pathlist_from_lib, rel_l2, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -235,7 +235,7 @@ def test_rx_batch_uneven_alone_equals_in_mix():
     assert set(status.cpu().numpy().tolist()) <= {0, 6}
     for i, (b, o, iters) in enumerate(keep):
         M, N, nrx, ntx, Q = shapes[i % len(shapes)]
-        plan = Plan(M, N, nrx, ntx, Q)
+        plan = one_cta_plan(M, N, nrx, ntx, Q)
         alone = _run(plan, b, iters, 1)
         assert torch.equal(alone["x_hat"][0], o["x"]), i
         assert torch.equal(alone["bits"][0], o["bits"]), i

@@ -11,7 +11,7 @@ import pytest
 import torch
 
 import synth
-from tests.gpu_util import TOL_LLR, TOL_X, dev, to_dev
+from tests.gpu_util import TOL_LLR, TOL_X, dev, one_cta_plan, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -81,7 +81,7 @@ def test_served_mix_equals_alone():
             M, N, nrx, ntx, Q = fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"]
             bps = int(np.log2(Q))
             served = srv.read(i, ntx, M * N, bps, nrx * ntx, llr=True)
-            plan = Plan(M, N, nrx, ntx, Q)
+            plan = one_cta_plan(M, N, nrx, ntx, Q)
             b = fr["b"]
             alone = plan.rx(fr["yp"][None], fr["yd"][None], to_dev(b["noise_var"]), to_dev(b["theta"]), fr["iters"], 1,
                             want_paths=True, want_llr=True)
@@ -162,7 +162,7 @@ def test_light_frames_have_their_own_queue():
             M, N, nrx, ntx, Q = fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"]
             served = srv.read(i, ntx, M * N, int(np.log2(Q)), nrx * ntx, llr=True)
             b = fr["b"]
-            alone = Plan(M, N, nrx, ntx, Q).rx(fr["yp"][None], fr["yd"][None], to_dev(b["noise_var"]),
+            alone = one_cta_plan(M, N, nrx, ntx, Q).rx(fr["yp"][None], fr["yd"][None], to_dev(b["noise_var"]),
                                                to_dev(b["theta"]), fr["iters"], 1, want_llr=True)
             assert np.array_equal(served["bits"], alone["bits"].cpu().numpy().reshape(-1)), i
             assert np.array_equal(served["llr"], alone["llr"].cpu().numpy().reshape(-1)), i
