@@ -747,6 +747,61 @@ def impl_mimo(args):
     return 0
 
 
+# ------------------------------------------------------------- one-frame latency workload
+
+LATENCY_SHAPES = ((64, 32), (128, 32), (64, 64), (128, 64), (256, 32))
+
+
+def impl_latency(args):
+    """Per-frame latency of the receiver called one frame at a time (the paper's real-time
+    setting: each packet is processed as it arrives): p50 / p99 over a stream of frames, for
+    one CTA per frame (or the large-frame kernel) and for the 2-CTA cluster receiver."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Plan
+    rows = []
+    for (m, n) in LATENCY_SHAPES:
+        b = synth.fractional_batch(args.latency_frames, seed=SEED + m + n, M=m, N=n, Q=Q)
+        yp, yd = torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev)
+        nv, th = torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev)
+        res = {"M": m, "N": n}
+        for name, cl in (("one_cta", 1), ("cluster2", 2)):
+            plan = Plan(m, n, 1, 1, Q)
+            plan.set_tuning(cluster=cl)
+            outs = plan._rx_outputs(1, dev, False, False, False)
+            for f in range(3):
+                plan.rx(yp[f:f + 1], yd[f:f + 1], nv[f:f + 1], th[f:f + 1], ITERS, 1, out=outs)
+            torch.cuda.synchronize()
+            ts = []
+            for f in range(args.latency_frames):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                plan.rx(yp[f:f + 1], yd[f:f + 1], nv[f:f + 1], th[f:f + 1], ITERS, 1, out=outs)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ts = np.array(ts)
+            res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                         "within_0_5ms": float((ts <= DEADLINE_MS).mean())}
+        rows.append(res)
+    head = rows[0]["one_cta"]
+    line = {"metric": "one-frame Zak-OTFS receiver latency (p50/p99), SISO 16-QAM", "value": head["p50_ms"],
+            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "one frame per call: pilot + data frame in HBM, 6-path fractional channel, "
+                                   "SNR 0..30 dB, 10 CG iterations, device time per call", "frames": args.latency_frames},
+            "shapes": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -761,10 +816,12 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=24, help="oracle sample per host core for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=4, help="oracle frames per host core per step (--impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency"],
                     help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
-                         "mixed: the uneven FP16/BF16 batch under CUDA graphs; mimo: 4x4 128x64 64-QAM frames")
+                         "mixed: the uneven FP16/BF16 batch under CUDA graphs; mimo: 4x4 128x64 64-QAM frames; "
+                         "latency: one frame per call")
     ap.add_argument("--mimo-steps", type=int, default=5, help="mimo: timed steps")
+    ap.add_argument("--latency-frames", type=int, default=200, help="latency: frames per shape")
     ap.add_argument("--mixed-steps", type=int, default=20, help="mixed: timed steps per storage type")
     ap.add_argument("--tune-frames", type=int, default=64, help="mixed: frames per shape group the autotuner times")
     ap.add_argument("--tuning-file", default="", help="mixed: write the autotuner's JSON here ({dtype} expands)")
@@ -791,6 +848,8 @@ def main():
         return impl_mixed(args)
     if args.workload == "mimo":
         return impl_mimo(args)
+    if args.workload == "latency":
+        return impl_latency(args)
     return impl_zotfs(args)
 
 
