@@ -705,7 +705,10 @@ def impl_mixed(args):
 
 def impl_mimo(args):
     """256 frames of a 4x4 stack at 128x64, 64-QAM (16 path lists per frame, 32768 stacked
-    unknowns per CG): the large-frame kernel, whose vectors live in L2-resident scratch."""
+    unknowns per CG): the large-frame kernels, whose vectors live in global scratch slots.  The
+    headline runs the default tuning (the clustered kernel, 2 CTAs per frame at this load); the
+    one-CTA kernel and the 4-CTA cluster are timed beside it, each also one frame per call
+    (where the default takes 4 CTAs per frame)."""
     import torch
     ws, rank, local = _dist()
     if rank != 0:
@@ -718,23 +721,42 @@ def impl_mimo(args):
     from paper_2604_02266_gb300 import Plan, launch_count
     Mm, Nm, Qm, A, F = 128, 64, 64, 4, 256
     b = synth.fractional_batch(F, seed=SEED + 3, M=Mm, N=Nm, Q=Qm, n_rx=A, n_tx=A)
-    plan = Plan(Mm, Nm, A, A, Qm)
     yp, yd = torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev)
     nv, th = torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev)
-    outs = plan._rx_outputs(F, dev, True, False, False)
-    for _ in range(args.warmup):
-        plan.rx(yp, yd, nv, th, ITERS, F, out=outs)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = args.mimo_steps
-    e0.record()
-    for _ in range(steps):
-        plan.rx(yp, yd, nv, th, ITERS, F, out=outs)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    P = outs[0].count.cpu().numpy()
-    st = outs[4].cpu().numpy()
+    variants = {}
+    head = None
+    for name, cl, ctas in (("default", 0, 0), ("one_cta", 1, 0), ("cluster2", 2, 0), ("cluster4", 4, 0)):
+        plan = Plan(Mm, Nm, A, A, Qm)
+        plan.set_tuning(cluster=cl, ctas_per_sm=ctas)
+        outs = plan._rx_outputs(F, dev, True, False, False)
+        for _ in range(args.warmup):
+            plan.rx(yp, yd, nv, th, ITERS, F, out=outs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.rx(yp, yd, nv, th, ITERS, F, out=outs)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        launches = launch_count() * steps  # the library counts the launches of its last call
+        one = plan._rx_outputs(1, dev, False, False, False)
+        ts = []
+        for f in range(12):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            plan.rx(yp[f:f + 1], yd[f:f + 1], nv[f:f + 1], th[f:f + 1], ITERS, 1, out=one)
+            s1.record()
+            s1.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        variants[name] = {"ms_per_step": ms, "frames_s": F / ms * 1e3, "one_frame_p50_ms": float(np.median(ts[2:]))}
+        if head is None:
+            P = outs[0].count.cpu().numpy()
+            st = outs[4].cpu().numpy()
+            head = (ms, launches, P, st)
+        del plan, outs, one
+    ms, launches, P, st = head
     line = {"metric": "equalized Zak-OTFS frames/s, 4x4 MIMO 128x64 64-QAM", "value": F / ms * 1e3, "unit": "frames/s",
             "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -742,7 +764,8 @@ def impl_mimo(args):
                                    "channels per frame, separate pilot frame per tx antenna, SNR 0..30 dB, 10 CG "
                                    "iterations over 32768 stacked unknowns, complex FP32 with FP64 CG scalars"},
             "mbit_s": F * A * Mm * Nm * 6 / ms / 1e3, "paths_per_list": {"mean": float(P.mean()), "max": int(P.max())},
-            "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()), "gpu_launches": launch_count()}
+            "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()), "gpu_launches": launches,
+            "variants": variants}
     print(json.dumps(line))
     return 0
 

@@ -34,7 +34,8 @@ def _units():
     units = [("capi.cu", [], "capi.o"), ("plain.cu", [], "plain.o"), ("frame_table.cu", [], "frame_table.o"),
              ("batch.cu", [], "batch.o"), ("big_variant.cu", [], "big_variant.o"),
              ("server.cu", [], "server.o"), ("tune.cu", [], "tune.o"),
-             ("cluster_variant.cu", [], "cluster_variant.o")]
+             ("cluster_variant.cu", [], "cluster_variant.o"),
+             ("big_cluster_variant.cu", [], "big_cluster_variant.o")]
     for i in range(N_VARIANTS):
         units.append(("frame_variant.cu", [f"-DZOTFS_VARIANT={i}"], f"frame_v{i}.o"))
     return units

@@ -1,4 +1,5 @@
 // C ABI of the zotfs library: plans, argument validation and dispatch to the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -203,12 +204,13 @@ static int radix_of(const zotfs_plan_s* plan) { return plan->tune.fft_radix == 2
 // Launch the shared-memory frame kernel when the shape fits one CTA, else the large-frame
 // kernel on the plan's scratch slots.
 // The cluster receiver, where the plan asks for it and the call qualifies: FP32 SISO, the
-// data frame in the time domain, a separate pilot (or loaded lists), no single apply / DZT.
+// data frame in the time domain, a separate pilot frame, no single apply / DZT.
 static bool cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, const FrameArgs& A, ClusterCfg& cc) {
   if (plan->tune.cluster == 1 || real_bytes_of(plan) != 4 || A.y_is_dd || (A.mode & (kApply | kDzt | kLoadX)))
     return false;
-  if (!(A.mode & kCG)) return false;
-  if ((A.mode & kEstimate) && A.pilot_mode != ZOTFS_PILOT_SEPARATE) return false;
+  // an embedded pilot is removed from the data grid before the CG, which the cluster
+  // receiver does not do
+  if (!(A.mode & kCG) || A.pilot_mode != ZOTFS_PILOT_SEPARATE) return false;
   if (plan->tune.cluster >= 2)
     return choose_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.cluster, cc);
   // automatic: only where the one-CTA shared-memory kernel does not fit, and while the call
@@ -219,6 +221,27 @@ static bool cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, const Fr
     return false;
   if ((long long)A.n_frames * 2 > plan->sm_count) return false;
   return choose_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, 2, cc);
+}
+
+// The clustered large-frame kernel, for calls the one-CTA shared-memory kernel cannot take:
+// FP32, equalisation with separate pilot frames (lists estimated or loaded; DD or time-domain
+// data).  cluster = 2 or 4 asks for it; cluster = 0 takes it with 4 CTAs per frame while the
+// call leaves SMs idle (latency) and with 2 otherwise (measured on 4x4 128x64 frames: about
+// as fast per SM as one CTA per frame, with half the frame latency and a shorter tail).
+static bool big_cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, const FrameArgs& A,
+                                BigClusterCfg& bc) {
+  if (plan->tune.cluster == 1 || real_bytes_of(plan) != 4 || !plan->d_big) return false;
+  if (!(A.mode & kCG) || (A.mode & (kApply | kDzt | kLoadX))) return false;
+  if (A.pilot_mode != ZOTFS_PILOT_SEPARATE) return false;  // as for the cluster receiver
+  FrameCfg fc;
+  if (choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, fc,
+                       real_bytes_of(plan)))
+    return false;
+  if (plan->tune.cluster >= 2)
+    return choose_big_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.cluster, bc);
+  const int first = (long long)A.n_frames * 4 <= plan->sm_count ? 4 : 2;
+  return choose_big_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, first, bc) ||
+         choose_big_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, 6 - first, bc);
 }
 
 static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream) {
@@ -241,6 +264,28 @@ static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& 
   if (choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, cfg,
                        real_bytes_of(plan)))
     return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+  BigClusterCfg bcc;
+  if (big_cluster_applies(plan, nrx, ntx, A, bcc)) {
+    int clusters = 0;
+    cudaError_t e = big_cluster_max_active(bcc, clusters);
+    if (e != cudaSuccess) return cuda_fail(e, "cluster occupancy query");
+    clusters = big_cluster_count(bcc, clusters, plan->sm_count, plan->tune.ctas_per_sm);
+    const long long room = (long long)(plan->big_bytes / bcc.slot_bytes);
+    if (clusters > room) clusters = (int)room;
+    if (clusters > A.n_frames) clusters = A.n_frames;
+    if (clusters < 1) {
+      set_error("clustered large-frame receiver does not fit on the device");
+      return ZOTFS_EUNSUPPORTED;
+    }
+    int* counter = plan->d_counters + (plan->counter_next++ & 63);
+    A.work_counter = counter;
+    e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work counter)");
+    e = big_cluster_launch(bcc, A, radix_of(plan), clusters, plan->d_big, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clustered large-frame kernel launch");
+    ++g_launches;
+    return ZOTFS_OK;
+  }
   BigCfg big;
   if (real_bytes_of(plan) != 4 || !plan->d_big || !choose_big_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, big)) {
     set_error("no kernel for this shape / antenna count / precision");
@@ -345,8 +390,18 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
       if (e == cudaSuccess) {
         p->big_slots = p->sm_count * (occ > 0 ? occ : 1);
         p->big_slot_bytes = bc.slot_bytes;
-        e = cudaMalloc(&p->d_big, bc.slot_bytes * (size_t)p->big_slots);
+        p->big_bytes = bc.slot_bytes * (size_t)p->big_slots;
       }
+      // room for every resident cluster of the clustered kernel too
+      for (int CL : {2, 4}) {
+        BigClusterCfg cc;
+        int clusters = 0;
+        if (e == cudaSuccess && choose_big_cluster_cfg(M, N, n_rx, n_tx, 64, CL, cc)) {
+          e = big_cluster_max_active(cc, clusters);
+          p->big_bytes = std::max(p->big_bytes, cc.slot_bytes * (size_t)clusters);
+        }
+      }
+      if (e == cudaSuccess) e = cudaMalloc(&p->d_big, p->big_bytes);
     }
   }
   if (e == cudaSuccess) e = cudaMemcpy(p->d_W, W.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);

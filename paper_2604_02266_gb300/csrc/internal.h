@@ -31,6 +31,7 @@ struct zotfs_plan_s {
   char* d_big;
   size_t big_slot_bytes;
   int big_slots;
+  size_t big_bytes;  // size of d_big (also the clustered large-frame kernel's slots)
 };
 
 namespace zotfs {
@@ -89,6 +90,20 @@ bool choose_big_cfg(int M, int N, int nrx, int ntx, int p_max, BigCfg& cfg);
 cudaError_t big_launch(const BigCfg& cfg, const FrameArgs& A, int radix, int grid, char* scratch,
                        cudaStream_t stream);
 cudaError_t big_occupancy(const BigCfg& cfg, int& blocks);
+
+// Clustered large-frame kernel (big_cluster_variant.cu): one frame on CL CTAs of a cluster,
+// its vectors in one global scratch slot per cluster.
+struct BigClusterCfg {
+  int CL, T, EQ;
+  size_t smem, slot_bytes;
+};
+bool choose_big_cluster_cfg(int M, int N, int nrx, int ntx, int p_max, int CL, BigClusterCfg& cfg);
+cudaError_t big_cluster_launch(const BigClusterCfg& cfg, const FrameArgs& A, int radix, int clusters, char* scratch,
+                               cudaStream_t stream);
+cudaError_t big_cluster_max_active(const BigClusterCfg& cfg, int& clusters);
+// Clusters of one launch: the resident maximum, capped by `ctas_per_sm` CTAs per SM when it is
+// positive.
+int big_cluster_count(const BigClusterCfg& cfg, int max_active, int sm_count, int ctas_per_sm);
 
 // Cluster receiver (cluster_variant.cu): one SISO frame on C CTAs of a thread-block cluster.
 struct ClusterCfg {

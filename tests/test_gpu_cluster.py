@@ -93,3 +93,22 @@ def test_automatic_cluster_for_large_frames_at_low_load():
     for key in ("x_hat", "llr", "bits", "status"):
         assert torch.equal(auto[key], two[key]), key
     assert rel_l2(auto["x_hat"].cpu().numpy(), big["x_hat"].cpu().numpy()) < 2 * TOL_X
+
+
+def test_cluster_request_leaves_embedded_pilot_frames_to_one_cta():
+    """The cluster receivers take separate pilot frames only (an embedded pilot is removed from
+    the data grid before the CG, which they do not do): zotfs_equalize on an embedded-pilot
+    plan that asks for a cluster runs the one-CTA kernel, bit for bit."""
+    from paper_2604_02266_gb300 import PILOT_EMBEDDED, Plan
+    M, N, Q, F = 64, 32, 16, 4
+    b = synth.fractional_batch(F, seed=91, M=M, N=N, Q=Q)
+    yd, nv = to_dev(b["y_data_td"]), to_dev(b["noise_var"])
+    xs = []
+    for cl in (1, 2):
+        plan = Plan(M, N, 1, 1, Q, pilot_mode=PILOT_EMBEDDED, a_pilot=b["a_pilot"], guard=2)
+        plan.set_tuning(cluster=cl)
+        if cl == 1:
+            paths = plan.rx(yd, yd, nv, to_dev(b["theta"]), 10, F, want_paths=True)["paths"]
+        xs.append(plan.equalize(yd, paths, nv, 10, F))
+    torch.cuda.synchronize()
+    assert torch.equal(xs[0], xs[1])

@@ -107,3 +107,64 @@ def test_rx_batch_with_large_buckets():
         alone = _run(one_cta_plan(M, N, nrx, ntx, Q), b, 10, 1)
         assert torch.equal(alone["x_hat"][0], o["x"]), i
         assert torch.equal(alone["bits"][0], o["bits"]), i
+
+
+def _cluster_plan(M, N, nrx, ntx, Q, CL):
+    plan = Plan(M, N, nrx, ntx, Q)
+    plan.set_tuning(cluster=CL)
+    return plan
+
+
+@pytest.mark.parametrize("nrx,ntx,M,N,CL", [(4, 4, 128, 64, 4), (4, 4, 128, 64, 2), (2, 2, 128, 64, 4),
+                                            (4, 4, 64, 32, 2), (4, 4, 64, 32, 4), (1, 1, 256, 64, 4),
+                                            (2, 2, 256, 64, 2)])
+def test_big_cluster_rx_vs_oracle(nrx, ntx, M, N, CL):
+    """The clustered large-frame kernel (CL CTAs per frame, one scratch slot per cluster):
+    estimated lists, CG and demap against the FP64 oracle."""
+    F, Q = 2, 16
+    b = synth.fractional_batch(F, seed=9100 + 7 * CL + M + nrx, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx, snr_db=(12, 28))
+    plan = _cluster_plan(M, N, nrx, ntx, Q, CL)
+    out = _run(plan, b, 10, F)
+    torch.cuda.synchronize()
+    assert set(out["status"].cpu().numpy().tolist()) <= {0, 6}
+    wx, wl, mm = _check_frames(b, out, range(F), M, N, nrx, ntx, Q, 10, plan.p_max)
+    assert wx < TOL_X and wl < TOL_LLR and mm == 0, (wx, wl, mm)
+
+
+def test_big_cluster_matches_big_kernel_over_many_frames():
+    """More frames than resident clusters (one CTA per SM: 76 two-CTA clusters take 90 frames
+    from the work counter): the same path lists bit for bit as the one-CTA large-frame kernel,
+    x within FP32 reordering; the default tuning at this load is the same 2-CTA kernel, bit
+    for bit."""
+    M, N, nrx, ntx, Q, F = 64, 32, 4, 4, 16, 90
+    b = synth.fractional_batch(F, seed=9200, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx)
+    one = _run(_cluster_plan(M, N, nrx, ntx, Q, 1), b, 10, F)
+    few = Plan(M, N, nrx, ntx, Q)
+    few.set_tuning(cluster=2, ctas_per_sm=1)
+    two = _run(few, b, 10, F)
+    auto = _run(Plan(M, N, nrx, ntx, Q), b, 10, F)
+    torch.cuda.synchronize()
+    for key in ("count", "dk", "dl", "h"):
+        assert torch.equal(getattr(one["paths"], key), getattr(two["paths"], key)), key
+    assert torch.equal(one["status"], two["status"])
+    for f in range(F):
+        assert rel_l2(two["x_hat"][f].cpu().numpy(), one["x_hat"][f].cpu().numpy()) < 2 * TOL_X, f
+    for key in ("x_hat", "llr", "bits", "status"):
+        assert torch.equal(auto[key], two[key]), key
+
+
+@pytest.mark.parametrize("y_is_dd", [False, True])
+def test_big_cluster_equalize_given_lists(y_is_dd):
+    """zotfs_equalize on the clustered large-frame kernel, time-domain or DD data frames."""
+    M, N, nrx, ntx, F, iters = 128, 64, 2, 2, 2, 10
+    b, grids = _cg_case(M, N, F, 20, seed=9300 + int(y_is_dd), nrx=nrx, ntx=ntx)
+    plan = _cluster_plan(M, N, nrx, ntx, 16, 4)
+    flat = [pl for gr in grids for row in gr for pl in row]
+    paths = fill_paths(plan.new_paths(F), flat, plan.p_max)
+    y_dd = np.stack([np.stack([zak.vec(zak.dzt(b["y_data_td"][f, r].astype(complex), M, N)) for r in range(nrx)])
+                     for f in range(F)])
+    y = y_dd.astype(np.complex64) if y_is_dd else b["y_data_td"]
+    x = plan.equalize(to_dev(y), paths, to_dev(b["noise_var"]), iters, F, y_is_dd=y_is_dd).cpu().numpy()
+    for f in range(F):
+        ref = eq.cga(grids[f], y_dd[f].reshape(-1), float(b["noise_var"][f]), iters)
+        assert rel_l2(x[f].reshape(-1), ref) < TOL_X, f
