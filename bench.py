@@ -684,7 +684,7 @@ def impl_mixed(args):
             "frames_s": len(frames) / ms_graph * 1e3, "mbit_s": bits_per_step / ms_graph / 1e3,
             "ms_per_step_graph": ms_graph, "ms_per_step_tuned_eager": ms_eager, "ms_per_step_default_eager": ms_default,
             "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()),
-            "tuning": [{k: t[k] for k in ("M", "N", "n_rx", "n_tx", "threads_per_frame", "fft_radix", "ctas_per_sm",
+            "tuning": [{k: t[k] for k in ("M", "N", "n_rx", "n_tx", "threads_per_frame", "fft_radix", "ctas_per_sm", "cluster",
                                           "sm_ms_per_frame", "ms_best", "ms_default")} for t in tuning]}
         del tuned, frames, keep
     head = out["storage"]["fp16"]

@@ -134,14 +134,19 @@ typedef struct zotfs_tuning {
   int32_t threads_per_frame;
   int32_t fft_radix;
   int32_t ctas_per_sm;  /* resident CTAs per SM the persistent grid is sized for; 0 = max */
-  int32_t cluster;      /* the cluster receiver: each frame on a thread-block cluster of
-                           CTAs (one per SM) that exchange the CG vectors through distributed
-                           shared memory, for SISO plans (separate pilot or given lists) whose
-                           extension replica fits one CTA's shared memory.  2 or 4: that many
-                           CTAs wherever it applies.  0: 2 CTAs for frames too large for the
-                           one-CTA shared-memory kernel (instead of the large-frame kernel,
-                           whose vectors live in L2), when the call has at most one frame per
-                           two SMs -- latency first while the GPU has idle SMs.  1: never */
+  int32_t cluster;      /* CTAs of a thread-block cluster per frame, for plans with separate
+                           pilot frames (an embedded-pilot plan runs one CTA per frame):
+                           SISO frames whose extension replica fits one CTA's shared memory
+                           run on the cluster receiver (replicas in shared memory, the CG
+                           vectors exchanged through distributed shared memory); equalisation
+                           of frames too large for the one-CTA shared-memory kernel otherwise
+                           runs on the clustered large-frame kernel (vectors in one global
+                           scratch slot per cluster).  2 or 4: that many CTAs wherever one of
+                           them applies.  0: only frames too large for the one-CTA kernel --
+                           the cluster receiver (2 CTAs) when the call has at most one frame
+                           per two SMs, else the clustered large-frame kernel, 4 CTAs when the
+                           call has at most one frame per four SMs and 2 otherwise (MIMO
+                           frames only: loaded SISO calls keep one CTA per frame).  1: never */
 } zotfs_tuning;
 zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* tuning);
 zotfs_status zotfs_plan_get_tuning(zotfs_plan plan, zotfs_tuning* tuning);
@@ -273,6 +278,11 @@ typedef struct zotfs_batch_opts {
   int32_t n_tuning;           /* entries in `tuning` (host array, read during create only) */
   const zotfs_tuning_entry* tuning;
   int32_t max_sms;            /* SMs the batch's grids are sized for; 0: all of the device's */
+  int32_t cluster;            /* frames too large for one CTA's shared memory (separate pilot
+                                 frames): 0 per-bucket choice (tuning entry, else 2-CTA
+                                 clusters for MIMO buckets, one CTA per SISO frame), 1 one CTA
+                                 per frame, 2 or 4 CTAs of a cluster per frame; other values
+                                 are ZOTFS_EINVAL */
 } zotfs_batch_opts;
 
 /* Build a batch from host descriptors: validates every frame, groups frames into buckets

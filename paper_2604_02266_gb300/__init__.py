@@ -240,7 +240,7 @@ class Batch:
                     setattr(d, key, val)
         return arr, keep
 
-    def __init__(self, frames, threads_per_frame=0, ctas_per_sm=0, fft_radix=0, tuning=None, max_sms=0):
+    def __init__(self, frames, threads_per_frame=0, ctas_per_sm=0, fft_radix=0, tuning=None, max_sms=0, cluster=0):
         n = len(frames)
         arr, self._keep = self.descriptors(frames)
         entries = tuning or []
@@ -248,8 +248,8 @@ class Batch:
         for i, (shape, tun) in enumerate(entries):
             tarr[i].M, tarr[i].N, tarr[i].n_rx, tarr[i].n_tx = shape
             tarr[i].tuning = Z.zotfs_tuning(tun.get("threads_per_frame", 0), tun.get("fft_radix", 0),
-                                            tun.get("ctas_per_sm", 0))
-        opts = Z.zotfs_batch_opts(threads_per_frame, ctas_per_sm, fft_radix, len(entries), tarr, max_sms)
+                                            tun.get("ctas_per_sm", 0), tun.get("cluster", 0))
+        opts = Z.zotfs_batch_opts(threads_per_frame, ctas_per_sm, fft_radix, len(entries), tarr, max_sms, cluster)
         h = C.c_void_p()
         Z.check(Z.zotfs_batch_create(arr, n, C.byref(opts), C.byref(h)))
         self._h = h
@@ -317,7 +317,8 @@ def autotune(frames, warmup=0, reps=0, max_frames=0, stream=None):
         b = r.best
         out.append({"M": b.M, "N": b.N, "n_rx": b.n_rx, "n_tx": b.n_tx,
                     "threads_per_frame": b.tuning.threads_per_frame, "fft_radix": b.tuning.fft_radix,
-                    "ctas_per_sm": b.tuning.ctas_per_sm, "sm_ms_per_frame": r.sm_ms_per_frame, "ms_best": r.ms_best,
+                    "ctas_per_sm": b.tuning.ctas_per_sm, "cluster": b.tuning.cluster,
+                    "sm_ms_per_frame": r.sm_ms_per_frame, "ms_best": r.ms_best,
                     "ms_default": r.ms_default,
                     "n_candidates": r.n_candidates, "n_frames": r.n_frames})
     del keep
@@ -341,7 +342,7 @@ def load_tuning(path):
     out = []
     for e in doc["entries"]:
         shape = (int(e["M"]), int(e["N"]), int(e["n_rx"]), int(e["n_tx"]))
-        out.append((shape, {k: int(e.get(k, 0)) for k in ("threads_per_frame", "fft_radix", "ctas_per_sm")}))
+        out.append((shape, {k: int(e.get(k, 0)) for k in ("threads_per_frame", "fft_radix", "ctas_per_sm", "cluster")}))
     return out
 
 

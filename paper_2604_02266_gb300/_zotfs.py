@@ -63,7 +63,8 @@ class zotfs_tuning_entry(C.Structure):
 
 class zotfs_batch_opts(C.Structure):
     _fields_ = [("threads_per_frame", C.c_int32), ("ctas_per_sm", C.c_int32), ("fft_radix", C.c_int32),
-                ("n_tuning", C.c_int32), ("tuning", C.POINTER(zotfs_tuning_entry)), ("max_sms", C.c_int32)]
+                ("n_tuning", C.c_int32), ("tuning", C.POINTER(zotfs_tuning_entry)), ("max_sms", C.c_int32),
+                ("cluster", C.c_int32)]
 
 
 class zotfs_autotune_opts(C.Structure):

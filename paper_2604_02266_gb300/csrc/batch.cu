@@ -32,7 +32,9 @@ struct Bucket {
   float2* d_Tab = nullptr;
   bool big = false;      // vectors too large for shared memory: the large-frame kernel
   zotfs::BigCfg bigcfg{};
-  char* d_big = nullptr;  // its scratch slots (one per CTA of the bucket's grid)
+  bool bigc = false;      // ... on clusters of bccfg.CL CTAs per frame (grid counts clusters)
+  zotfs::BigClusterCfg bccfg{};
+  char* d_big = nullptr;  // its scratch slots (one per CTA, or per cluster, of the grid)
 };
 
 }  // namespace
@@ -149,6 +151,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
   if (o.fft_radix != 0 && o.fft_radix != 2 && o.fft_radix != 4) return binval("fft_radix must be 0, 2 or 4");
   if (o.n_tuning < 0 || (o.n_tuning > 0 && !o.tuning)) return binval("tuning table");
   if (o.max_sms < 0) return binval("max_sms < 0");
+  if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4) return binval("cluster must be 0, 1, 2 or 4");
 
   std::vector<zotfs_frame_desc> D(descs, descs + n_frames);
   for (int i = 0; i < n_frames; ++i) {
@@ -212,13 +215,14 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
   std::vector<int> occ(b->buckets.size(), 0);
   for (size_t bi = 0; bi < b->buckets.size() && st == ZOTFS_OK; ++bi) {
     Bucket& B = b->buckets[bi];
-    int tpf = o.threads_per_frame, radix = o.fft_radix, cps = o.ctas_per_sm;
+    int tpf = o.threads_per_frame, radix = o.fft_radix, cps = o.ctas_per_sm, cl = o.cluster;
     for (int j = 0; j < o.n_tuning; ++j) {
       const zotfs_tuning_entry& te = o.tuning[j];
       if (te.M == B.M && te.N == B.N && te.n_rx == B.nrx && te.n_tx == B.ntx) {
         if (!o.threads_per_frame) tpf = te.tuning.threads_per_frame;
         if (!o.fft_radix) radix = te.tuning.fft_radix;
         if (!o.ctas_per_sm) cps = te.tuning.ctas_per_sm;
+        if (!o.cluster) cl = te.tuning.cluster;
       }
     }
     B.radix = radix == 2 ? 2 : (radix == 4 ? 4 : kDefaultRadix);
@@ -232,8 +236,20 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
         break;
       }
       B.big = true;
+      // MIMO frames on 2-CTA clusters unless the caller asks otherwise (a SISO frame's pilot
+      // and data transforms do not spread over the cluster's CTAs, which costs throughput);
+      // separate pilot frames only: the clustered kernel does not remove an embedded pilot
+      if ((cl >= 2 || (cl == 0 && B.nrx * B.ntx > 1)) && B.pilot_mode == ZOTFS_PILOT_SEPARATE)
+        B.bigc = choose_big_cluster_cfg(B.M, B.N, B.nrx, B.ntx, B.p_max, cl >= 2 ? cl : 2, B.bccfg);
     }
-    e = B.big ? big_occupancy(B.bigcfg, occ[bi]) : frame_variant_occupancy(B.cfg.variant, B.cfg.T, B.cfg.smem, occ[bi]);
+    if (B.bigc) {
+      int clusters = 0;
+      e = big_cluster_max_active(B.bccfg, clusters);
+      occ[bi] = std::max(1, clusters * B.bccfg.CL / std::max(1, b->sm_count));  // CTAs per SM
+      if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
+    } else {
+      e = B.big ? big_occupancy(B.bigcfg, occ[bi]) : frame_variant_occupancy(B.cfg.variant, B.cfg.T, B.cfg.smem, occ[bi]);
+    }
     if (e != cudaSuccess) {
       st = cuda_fail(e, "occupancy query");
       break;
@@ -254,6 +270,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     int sms = (int)std::ceil(share * avail);
     sms = std::max(1, std::min(sms, avail));
     B.grid = std::max(1, std::min((int)B.ids.size(), sms * occ[bi]));
+    if (B.bigc) B.grid = std::max(1, std::min((int)B.ids.size(), sms * occ[bi] / B.bccfg.CL));  // clusters
   }
   // each bucket's CTAs take its frames heaviest first (lowest threshold first: more taps pass
   // it; then more iterations), so the last frames to start are the lightest
@@ -292,7 +309,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     B.d_W = it->second.first;
     B.d_Tab = it->second.second;
     if (B.big) {
-      e = cudaMalloc(&B.d_big, B.bigcfg.slot_bytes * (size_t)B.grid);
+      e = cudaMalloc(&B.d_big, (B.bigc ? B.bccfg.slot_bytes : B.bigcfg.slot_bytes) * (size_t)B.grid);
       if (e != cudaSuccess) {
         st = e == cudaErrorMemoryAllocation ? ZOTFS_ENOMEM : cuda_fail(e, "large-frame scratch");
         if (st == ZOTFS_ENOMEM) set_error("large-frame scratch allocation failed");
@@ -352,8 +369,9 @@ zotfs_status zotfs_rx_batch(zotfs_batch b, int32_t* status, zotfs_stream stream)
     A.status = status;
     A.descs = b->d_descs;
     A.frame_ids = b->d_ids + B.ids_off;
-    e = B.big ? big_launch(B.bigcfg, A, B.radix, B.grid, B.d_big, s)
-              : frame_variant_launch(B.cfg.variant, A, B.radix, B.grid, B.cfg.T, B.cfg.smem, s);
+    e = B.bigc  ? big_cluster_launch(B.bccfg, A, B.radix, B.grid, B.d_big, s)
+        : B.big ? big_launch(B.bigcfg, A, B.radix, B.grid, B.d_big, s)
+                : frame_variant_launch(B.cfg.variant, A, B.radix, B.grid, B.cfg.T, B.cfg.smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "bucket kernel launch");
     ++g_launches;
     e = cudaEventRecord(b->events[1 + bi], s);

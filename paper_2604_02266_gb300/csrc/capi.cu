@@ -226,8 +226,9 @@ static bool cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, const Fr
 // The clustered large-frame kernel, for calls the one-CTA shared-memory kernel cannot take:
 // FP32, equalisation with separate pilot frames (lists estimated or loaded; DD or time-domain
 // data).  cluster = 2 or 4 asks for it; cluster = 0 takes it with 4 CTAs per frame while the
-// call leaves SMs idle (latency) and with 2 otherwise (measured on 4x4 128x64 frames: about
-// as fast per SM as one CTA per frame, with half the frame latency and a shorter tail).
+// call has at most one frame per four SMs (latency), and with 2 otherwise for MIMO frames
+// (measured on 4x4 128x64 frames: about as fast per SM as one CTA per frame, with half the
+// frame latency and a shorter tail).
 static bool big_cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, const FrameArgs& A,
                                 BigClusterCfg& bc) {
   if (plan->tune.cluster == 1 || real_bytes_of(plan) != 4 || !plan->d_big) return false;
@@ -239,7 +240,11 @@ static bool big_cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, cons
     return false;
   if (plan->tune.cluster >= 2)
     return choose_big_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.cluster, bc);
-  const int first = (long long)A.n_frames * 4 <= plan->sm_count ? 4 : 2;
+  const bool low_load = (long long)A.n_frames * 4 <= plan->sm_count;
+  // a SISO frame's pilot and data transforms do not spread over the cluster's CTAs, which
+  // costs throughput (128x64 in a loaded batch: 6.45 ms against 5.53 ms on one CTA per frame)
+  if (!low_load && nrx * ntx == 1) return false;
+  const int first = low_load ? 4 : 2;
   return choose_big_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, first, bc) ||
          choose_big_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, 6 - first, bc);
 }

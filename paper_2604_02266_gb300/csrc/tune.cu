@@ -27,7 +27,7 @@ zotfs_status tinval(const std::string& m) {
 constexpr int kTuneFramesPerSm = 4;
 
 struct Candidate {
-  int threads, radix, ctas;
+  int threads, radix, ctas, cluster;
 };
 
 // Launch shapes worth timing for one (M, N, n_rx, n_tx, p_max) group.
@@ -42,12 +42,17 @@ std::vector<Candidate> candidates(int M, int N, int nrx, int ntx, int p_max) {
     if (frame_variant_occupancy(cfg.variant, cfg.T, cfg.smem, occ) != cudaSuccess || occ < 1) continue;
     any = true;
     for (int radix : {2, 4})
-      for (int c = 1; c <= occ; ++c) out.push_back({T, radix, c});
+      for (int c = 1; c <= occ; ++c) out.push_back({T, radix, c, 0});
   }
-  if (!any) {  // the large-frame kernel: fixed threads and occupancy, radix only
+  if (!any) {  // the large-frame kernels: fixed threads and occupancy; radix, CTAs per frame
     BigCfg big;
     if (choose_big_cfg(M, N, nrx, ntx, p_max, big))
-      for (int radix : {2, 4}) out.push_back({0, radix, 0});
+      for (int radix : {2, 4}) out.push_back({0, radix, 0, 1});
+    for (int cl : {2, 4}) {
+      BigClusterCfg bc;
+      if (choose_big_cluster_cfg(M, N, nrx, ntx, p_max, cl, bc))
+        for (int radix : {2, 4}) out.push_back({0, radix, 0, cl});
+    }
   }
   return out;
 }
@@ -61,6 +66,7 @@ float time_shape(const std::vector<zotfs_frame_desc>& D, const Candidate& c, int
   o.fft_radix = c.radix;
   o.ctas_per_sm = c.ctas;
   o.max_sms = max_sms;
+  o.cluster = c.cluster;
   zotfs_batch b = nullptr;
   if (zotfs_batch_create(D.data(), (int)D.size(), &o, &b) != ZOTFS_OK) return -1.f;
   float ms = -1.f;
@@ -210,7 +216,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     R.best.n_rx = d0.n_rx;
     R.best.n_tx = d0.n_tx;
     R.n_frames = target;
-    R.ms_default = time_shape(T, Candidate{0, 0, 0}, 0, warmup, reps, d_status, stream, e0, e1);
+    R.ms_default = time_shape(T, Candidate{0, 0, 0, 0}, 0, warmup, reps, d_status, stream, e0, e1);
     if (R.ms_default < 0.f) {
       st = ZOTFS_EINVAL;
       set_error(std::string("autotune: default launch shape failed: ") + zotfs_last_error());
@@ -225,6 +231,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
         R.best.tuning.threads_per_frame = c.threads;
         R.best.tuning.fft_radix = c.radix;
         R.best.tuning.ctas_per_sm = c.ctas;
+        R.best.tuning.cluster = c.cluster;
       }
     }
     R.sm_ms_per_frame = R.ms_best * (float)sm_count / (float)target;

@@ -56,7 +56,7 @@ def test_struct_layouts_match_header_sizes(libpath):
     assert ctypes.sizeof(Z.zotfs_paths) == 5 * 8 + 8
     assert ctypes.sizeof(Z.zotfs_tuning) == 16
     assert ctypes.sizeof(Z.zotfs_frame_desc) == 15 * 4 + 4 + 9 * 8  # 15 scalars, pad, 9 pointers
-    assert ctypes.sizeof(Z.zotfs_batch_opts) == 4 * 4 + 8 + 8  # int max_sms + tail padding
+    assert ctypes.sizeof(Z.zotfs_batch_opts) == 4 * 4 + 8 + 4 + 4  # ..., max_sms, cluster
     assert ctypes.sizeof(Z.zotfs_autotune_opts) == 12
     assert ctypes.sizeof(Z.zotfs_tuning_entry) == 4 * 4 + 16
     assert ctypes.sizeof(Z.zotfs_tuning_result) == 4 * 4 + 16 + 5 * 4

@@ -81,32 +81,47 @@ def test_rx_4x4_128x64_64qam():
 
 
 def test_rx_batch_with_large_buckets():
-    """An uneven batch mixing shared-memory and large-frame buckets: each frame equals its
-    result alone."""
+    """An uneven batch mixing shared-memory and large-frame buckets.  With cluster = 1 each frame
+    equals its result alone through a one-CTA plan, bit for bit; by default the large buckets
+    run on 2-CTA clusters, and each frame equals its result in a batch of its own, bit for
+    bit, and the one-CTA result within FP32 reordering."""
     from paper_2604_02266_gb300 import Batch
     shapes = [(128, 64, 1, 1, 16), (64, 32, 1, 1, 16), (128, 64, 2, 2, 16), (64, 64, 2, 2, 4), (32, 16, 2, 2, 64)]
     frames, keep = [], []
     for i in range(15):
         M, N, nrx, ntx, Q = shapes[i % len(shapes)]
         b = synth.fractional_batch(1, seed=8100 + i, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx, snr_db=(5 + 2 * i,))
-        bps = int(np.log2(Q))
-        o = {"x": torch.zeros(ntx, M * N, dtype=torch.complex64, device=dev()),
-             "bits": torch.zeros(ntx, M * N * bps // 8, dtype=torch.uint8, device=dev())}
         frames.append(dict(M=M, N=N, n_rx=nrx, n_tx=ntx, qam=Q, iters=10, pilot_mode=0, guard=2, p_max=64,
                            in_dtype=0, noise_var=float(b["noise_var"][0]), theta=float(b["theta"][0]),
                            a_pilot=float(b["a_pilot"]), y_pilot=to_dev(b["y_pilot_td"][0]),
-                           y_data=to_dev(b["y_data_td"][0]), x_hat=o["x"], bits=o["bits"]))
-        keep.append((b, o))
-    batch = Batch(frames)
-    status = torch.full((len(frames),), -1, dtype=torch.int32, device=dev())
-    batch.run(status)
-    torch.cuda.synchronize()
-    assert set(status.cpu().numpy().tolist()) <= {0, 6}
-    for i, (b, o) in enumerate(keep):
+                           y_data=to_dev(b["y_data_td"][0])))
+        keep.append(b)
+
+    def outputs(fr):
+        M, N, ntx, Q = fr["M"], fr["N"], fr["n_tx"], fr["qam"]
+        return {"x_hat": torch.zeros(ntx, M * N, dtype=torch.complex64, device=dev()),
+                "bits": torch.zeros(ntx, M * N * int(np.log2(Q)) // 8, dtype=torch.uint8, device=dev())}
+
+    def run(frs, cluster):
+        outs = [outputs(fr) for fr in frs]
+        batch = Batch([dict(fr, **o) for fr, o in zip(frs, outs)], cluster=cluster)
+        status = torch.full((len(frs),), -1, dtype=torch.int32, device=dev())
+        batch.run(status)
+        torch.cuda.synchronize()
+        assert set(status.cpu().numpy().tolist()) <= {0, 6}
+        return outs
+
+    one = run(frames, 1)
+    mix = run(frames, 0)
+    for i, b in enumerate(keep):
         M, N, nrx, ntx, Q = shapes[i % len(shapes)]
         alone = _run(one_cta_plan(M, N, nrx, ntx, Q), b, 10, 1)
-        assert torch.equal(alone["x_hat"][0], o["x"]), i
-        assert torch.equal(alone["bits"][0], o["bits"]), i
+        assert torch.equal(alone["x_hat"][0], one[i]["x_hat"]), i
+        assert torch.equal(alone["bits"][0], one[i]["bits"]), i
+        own = run([frames[i]], 0)[0]
+        assert torch.equal(own["x_hat"], mix[i]["x_hat"]), i
+        assert torch.equal(own["bits"], mix[i]["bits"]), i
+        assert rel_l2(mix[i]["x_hat"].cpu().numpy(), one[i]["x_hat"].cpu().numpy()) < 2 * TOL_X, i
 
 
 def _cluster_plan(M, N, nrx, ntx, Q, CL):
