@@ -7,7 +7,9 @@ Passages followed:
 * Eq. sparse_mvm / Eq. D_definition: u[q] = sum_p D_{p,q} v[c_p(q)];
 * Eq. sparse_herm_mvm: u[r] = sum_p conj(D_{p,q_p(r)}) v[q_p(r)];
 * Algorithm 1 (Sec. IV-C, compute-aware CGA): CG on (H^H H + lambda I) x = H^H y with the
-  two MVMs per iteration, scalar lambda, fixed iteration count, no early exit;
+  two MVMs per iteration, scalar lambda, fixed iteration count, no early exit; optionally the
+  residual-norm stopping test that Sec. IV-C describes for the original CGA (stop once the
+  squared residual norm falls below a threshold), read as relative: ||c||^2 <= eps^2 ||b||^2;
 * Eq. lmmse (Sec. III-B "Equalization"): x = (H^H H + R_n)^-1 H^H y with R_n = lambda I,
   solved by Cholesky as the paper suggests.
 
@@ -87,7 +89,7 @@ def as_operator(paths):
     return StackedOperator([[paths]])
 
 
-def cga(paths, y, lam, iters, history=False):
+def cga(paths, y, lam, iters, history=False, eps=0.0):
     """Compute-aware CGA, Algorithm 1, in FP64.
 
     b = H^H y, x = 0, c = b, p = b, c_n = ||c||^2; then for each of ``iters`` iterations:
@@ -97,6 +99,11 @@ def cga(paths, y, lam, iters, history=False):
     Readings where Algorithm 1 is silent: p^H a_p is taken as its real part (the system
     matrix is Hermitian positive definite); alpha = 0 when p^H a_p = 0 and beta = 0 when
     c_n = 0, so a converged noiseless run stays finite.
+
+    eps > 0 adds the residual-norm stopping test of the original CGA (Sec. IV-C, "Profiling-
+    based fixed termination"), relative to ||b||^2: no further iteration once
+    c_n <= eps^2 ||b||^2, tested before the first iteration and after each update of c.
+    ``iters`` stays the cap.  eps = 0 is Algorithm 1 as printed (no early exit).
     """
     op = as_operator(paths)
     b = op.adjoint(y)
@@ -104,8 +111,11 @@ def cga(paths, y, lam, iters, history=False):
     c = b.copy()
     p = b.copy()
     cn = float(np.vdot(c, c).real)
+    stop_at = eps * eps * cn if eps > 0.0 else -1.0
     hist = [cn]
     for _ in range(iters):
+        if cn <= stop_at:
+            break
         a = op.adjoint(op.forward(p)) + lam * p
         pa = float(np.vdot(p, a).real)
         alpha = cn / pa if pa != 0.0 else 0.0

@@ -36,7 +36,7 @@ def subtract_pilot(y_dd_vec, paths, a_pilot):
 
 
 def receive(y_pilot_td, y_data_td, M, N, n_rx, n_tx, Q, noise_var, theta, iters,
-            a_pilot, K0=None, L0=None, p_max=None, embedded_guard=None):
+            a_pilot, K0=None, L0=None, p_max=None, embedded_guard=None, cg_eps=0.0):
     """Full receiver for one frame.
 
     y_pilot_td: separate-pilot mode: (n_tx, n_rx, MN) complex; embedded mode: ignored.
@@ -60,7 +60,7 @@ def receive(y_pilot_td, y_data_td, M, N, n_rx, n_tx, Q, noise_var, theta, iters,
         paths = [[pl]]
         y_dd = subtract_pilot(y_dd[0], pl, a_pilot)[None, :]
     y_vec = y_dd.reshape(-1)
-    x_hat = equalizer.cga(paths, y_vec, noise_var, iters)
+    x_hat = equalizer.cga(paths, y_vec, noise_var, iters, eps=cg_eps)
     llr = qam.maxlog_llr(x_hat, noise_var, Q)
     return {
         "paths": paths,

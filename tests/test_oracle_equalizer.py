@@ -144,3 +144,36 @@ def test_noiseless_separate_pilot_recovery(Q, seed):
     out = receiver.receive(b["y_pilot_td"][0], b["y_data_td"][0], 16, 16, 1, 1, Q,
                            float(b["noise_var"][0]), float(b["theta"][0]), 256, b["a_pilot"])
     assert (out["bits"].reshape(-1) == b["bits"][0, 0]).all()
+
+
+def test_cg_stopping_test_against_the_dense_residual():
+    """The optional residual-norm stopping test (Sec. IV-C's description of the original CGA,
+    read relative to ||b||^2).  With the threshold placed between two consecutive squared
+    residual norms of the fixed-iteration run, the stopped run (a) returns the iterate of the
+    first iteration whose true residual b - A x, computed with the dense Eq. Hdd matrix, is
+    below eps ||b||, and (b) did not stop one iteration earlier: the previous iterate's true
+    residual is above it.  eps = 0 is Algorithm 1 as printed, eps >= 1 stops before the
+    first iteration (x = 0)."""
+    g = np.random.default_rng(21)
+    M, N = 16, 16
+    pl = _paths(g, M, N, 5, span=(3, 3))
+    Hd = dc.dense_H(dc.heff_from_paths(pl), M // 2, N // 2)
+    lam = 0.02
+    A = Hd.conj().T @ Hd + lam * np.eye(M * N)
+    y = g.standard_normal(M * N) + 1j * g.standard_normal(M * N)
+    b = Hd.conj().T @ y
+    nb2 = float(np.vdot(b, b).real)
+    _, hist = eq.cga(pl, y, lam, 12, history=True)
+    k = 5  # stop after iteration k: hist[k] > eps^2 ||b||^2 >= hist[k + 1]
+    eps = np.sqrt(np.sqrt(hist[k] * hist[k + 1]) / nb2)
+    x = eq.cga(pl, y, lam, 12, eps=eps)
+
+    def res2(v):
+        r = b - A @ v
+        return float(np.vdot(r, r).real)
+
+    assert res2(x) <= eps * eps * nb2
+    assert res2(eq.cga(pl, y, lam, k)) > eps * eps * nb2
+    assert np.abs(x - eq.cga(pl, y, lam, k + 1)).max() == 0.0
+    assert np.abs(eq.cga(pl, y, lam, 12, eps=0.0) - eq.cga(pl, y, lam, 12)).max() == 0.0
+    assert not np.any(eq.cga(pl, y, lam, 12, eps=1.0))
