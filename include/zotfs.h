@@ -97,6 +97,12 @@ typedef struct zotfs_options {
   int32_t in_dtype;    /* zotfs_dtype of TD input frames; default ZOTFS_C64 */
   int32_t tap_dtype;   /* zotfs_dtype of path taps in zotfs_paths; default ZOTFS_C64 */
   int32_t compute;     /* zotfs_compute; default ZOTFS_COMPUTE_FP32 */
+  float   cg_eps;      /* residual-norm stopping test of the CG (the original CGA's test that
+                          Sec. IV-C describes, relative form): a frame stops iterating once
+                          ||c||^2 <= cg_eps^2 ||b||^2, evaluated in FP64 inside the frame's
+                          kernel (no host round trip); the iteration count stays the cap.
+                          Default 0: no test, the fixed iteration count of Algorithm 1.  Must
+                          be finite and >= 0.  zotfs_equalize_static ignores it. */
 } zotfs_options;
 
 typedef struct zotfs_plan_s* zotfs_plan;
@@ -252,6 +258,7 @@ typedef struct zotfs_frame_desc {
   int32_t pilot_mode, guard, p_max, in_dtype;
   int32_t K0, L0;           /* -1: M/2, N/2 */
   float   noise_var, theta, a_pilot;  /* a_pilot <= 0: the plan default for the mode */
+  float   cg_eps;           /* CG stopping test as zotfs_options.cg_eps; 0: fixed iterations */
   const void* y_pilot;      /* dev TD pilots (separate mode) */
   const void* y_data;       /* dev TD data frames */
   float*   x_hat;           /* dev or NULL */
@@ -373,6 +380,7 @@ typedef struct zotfs_server_opts {
 typedef struct zotfs_request {
   int32_t M, N, n_rx, n_tx, qam, iters;
   float noise_var, theta, a_pilot;  /* a_pilot <= 0: sqrt(MN) */
+  float cg_eps;                     /* CG stopping test as zotfs_options.cg_eps; 0: off */
   const void* y_pilot;              /* dev C64 pilots [t][r][MN], resident until completion */
   const void* y_data;               /* dev C64 data [r][MN] */
   uint64_t tag;                     /* caller's id, unique among frames not yet released */

@@ -374,9 +374,9 @@ class Server:
             pass
 
     @staticmethod
-    def request(tag, y_pilot, y_data, M, N, n_rx, n_tx, qam, iters, noise_var, theta, a_pilot=0.0):
+    def request(tag, y_pilot, y_data, M, N, n_rx, n_tx, qam, iters, noise_var, theta, a_pilot=0.0, cg_eps=0.0):
         _need_cuda(y_pilot, y_data)
-        return Z.zotfs_request(M, N, n_rx, n_tx, qam, iters, noise_var, theta, a_pilot, y_pilot.data_ptr(),
+        return Z.zotfs_request(M, N, n_rx, n_tx, qam, iters, noise_var, theta, a_pilot, cg_eps, y_pilot.data_ptr(),
                                y_data.data_ptr(), tag)
 
     def submit(self, reqs):

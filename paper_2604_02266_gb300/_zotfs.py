@@ -33,7 +33,7 @@ PILOT_SEPARATE, PILOT_EMBEDDED = 0, 1
 class zotfs_options(C.Structure):
     _fields_ = [("pilot_mode", C.c_int32), ("K0", C.c_int32), ("L0", C.c_int32), ("a_pilot", C.c_float),
                 ("guard", C.c_int32), ("p_max", C.c_int32), ("in_dtype", C.c_int32), ("tap_dtype", C.c_int32),
-                ("compute", C.c_int32)]
+                ("compute", C.c_int32), ("cg_eps", C.c_float)]
 
 
 class zotfs_paths(C.Structure):
@@ -50,7 +50,7 @@ class zotfs_frame_desc(C.Structure):
     _fields_ = [("M", C.c_int32), ("N", C.c_int32), ("n_rx", C.c_int32), ("n_tx", C.c_int32),
                 ("qam", C.c_int32), ("iters", C.c_int32), ("pilot_mode", C.c_int32), ("guard", C.c_int32),
                 ("p_max", C.c_int32), ("in_dtype", C.c_int32), ("K0", C.c_int32), ("L0", C.c_int32),
-                ("noise_var", C.c_float), ("theta", C.c_float), ("a_pilot", C.c_float),
+                ("noise_var", C.c_float), ("theta", C.c_float), ("a_pilot", C.c_float), ("cg_eps", C.c_float),
                 ("y_pilot", C.c_void_p), ("y_data", C.c_void_p), ("x_hat", C.c_void_p), ("llr", C.c_void_p),
                 ("bits", C.c_void_p), ("path_count", C.c_void_p), ("path_dk", C.c_void_p),
                 ("path_dl", C.c_void_p), ("path_h", C.c_void_p)]
@@ -85,7 +85,7 @@ class zotfs_server_opts(C.Structure):
 class zotfs_request(C.Structure):
     _fields_ = [("M", C.c_int32), ("N", C.c_int32), ("n_rx", C.c_int32), ("n_tx", C.c_int32), ("qam", C.c_int32),
                 ("iters", C.c_int32), ("noise_var", C.c_float), ("theta", C.c_float), ("a_pilot", C.c_float),
-                ("y_pilot", C.c_void_p), ("y_data", C.c_void_p), ("tag", C.c_uint64)]
+                ("cg_eps", C.c_float), ("y_pilot", C.c_void_p), ("y_data", C.c_void_p), ("tag", C.c_uint64)]
 
 
 class zotfs_completion(C.Structure):

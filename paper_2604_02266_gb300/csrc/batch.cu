@@ -130,6 +130,7 @@ static zotfs_status validate_desc(const zotfs_frame_desc& d, int i) {
     return bad("TD frames must be 16-byte aligned");
   if (!std::isfinite(d.noise_var) || d.noise_var < 0.f) return bad("noise_var must be finite and >= 0");
   if (!std::isfinite(d.theta)) return bad("theta must be finite");
+  if (!std::isfinite(d.cg_eps) || d.cg_eps < 0.f) return bad("cg_eps must be finite and >= 0");
   if (d.path_count && (!d.path_dk || !d.path_dl || !d.path_h)) return bad("path outputs: all or none");
   return ZOTFS_OK;
 }

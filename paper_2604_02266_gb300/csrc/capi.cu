@@ -53,6 +53,7 @@ void fill_plan_args(const zotfs_plan_s* plan, FrameArgs& A) {
   A.inv_sqrtN = 1.0 / std::sqrt((double)plan->N);
   A.sqrtN = std::sqrt((double)plan->N);
   A.pam_d = std::sqrt(3.0 / (2.0 * (plan->qam - 1)));
+  A.eps2 = (double)plan->opt.cg_eps * (double)plan->opt.cg_eps;
   const bool fp64 = plan->opt.compute == ZOTFS_COMPUTE_FP64;
   A.W = fp64 ? (const void*)plan->d_W64 : (const void*)plan->d_W;
   A.Tab = fp64 ? (const void*)plan->d_Tab64 : (const void*)plan->d_Tab;
@@ -311,6 +312,13 @@ static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& 
 
 using namespace zotfs;
 
+// The ABI's struct sizes (mirrored by the Python binding's ctypes structures).
+static_assert(sizeof(zotfs_options) == 40, "zotfs_options layout");
+static_assert(sizeof(zotfs_tuning) == 16, "zotfs_tuning layout");
+static_assert(sizeof(zotfs_frame_desc) == 16 * 4 + 9 * 8, "zotfs_frame_desc layout");
+static_assert(sizeof(zotfs_batch_opts) == 32, "zotfs_batch_opts layout");
+static_assert(sizeof(zotfs_request) == 10 * 4 + 3 * 8, "zotfs_request layout");
+
 extern "C" {
 
 const char* zotfs_last_error(void) { return g_err.c_str(); }
@@ -461,6 +469,7 @@ zotfs_status zotfs_plan_set_options(zotfs_plan plan, const zotfs_options* o) {
   for (int d : {n.in_dtype, n.tap_dtype})
     if (d != ZOTFS_C64 && d != ZOTFS_C32_F16 && d != ZOTFS_C32_BF16 && d != ZOTFS_C128) return inval("unknown dtype");
   if (n.compute != ZOTFS_COMPUTE_FP32 && n.compute != ZOTFS_COMPUTE_FP64) return inval("compute must be FP32 or FP64");
+  if (!std::isfinite(n.cg_eps) || n.cg_eps < 0.f) return inval("cg_eps must be finite and >= 0");
   if (n.compute == ZOTFS_COMPUTE_FP64) {
     FrameCfg cfg;
     if (!choose_frame_cfg(plan->M, plan->N, plan->nrx, plan->ntx, n.p_max, 0, cfg, 8))

@@ -221,10 +221,14 @@ __global__ void __launch_bounds__(kBigThreads, 1)
           write_ext<R, E, true>(extP + t * blk, A, k, jw + c * E, v);
         }
       double cn = block_sum_to_thread0(part, S);
-      if (tid == 0) S->isc[1] = isfinite(cn) ? 0 : 1;
+      const double stop_at = io.eps2 > 0.0 ? io.eps2 * cn : -1.0;  // eps^2 ||b||^2 (thread 0)
+      if (tid == 0) {
+        S->isc[1] = isfinite(cn) ? 0 : 1;
+        S->isc[4] = cn <= stop_at ? 1 : 0;
+      }
       __syncthreads();
 
-      for (int it = 0; it < io.iters; ++it) {
+      for (int it = 0; it < io.iters && !S->isc[4]; ++it) {
         // t = H p  (extP -> extT)
         for (int r = 0; r < A.nrx; ++r)
           for (int c = 0; c < NCH; ++c) {
@@ -272,6 +276,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
         if (tid == 0) {
           S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;
           if (!isfinite(cn_new)) S->isc[1] = 1;
+          if (cn_new <= stop_at) S->isc[4] = 1;
           cn = cn_new;
         }
         __syncthreads();

@@ -199,10 +199,15 @@ __global__ void __launch_bounds__(TMAX, 1)
     int set = 0;
     double cn = cluster_sum<CL>(cluster, cs, set, block_sum_to_thread0(part, S));  // extP complete
     set ^= 1;
-    if (tid == 0) S->isc[1] = isfinite(cn) ? 0 : 1;
+    // every CTA's thread 0 holds the same rank-ordered sums, so all take the same decision
+    const double stop_at = io.eps2 > 0.0 ? io.eps2 * cn : -1.0;
+    if (tid == 0) {
+      S->isc[1] = isfinite(cn) ? 0 : 1;
+      S->isc[4] = cn <= stop_at ? 1 : 0;
+    }
     __syncthreads();
 
-    for (int it = 0; it < io.iters; ++it) {
+    for (int it = 0; it < io.iters && !S->isc[4]; ++it) {
       // t = H p  (extP -> extT)
       for (int r = 0; r < A.nrx; ++r)
         for (int c = 0; c < NCH; ++c) {
@@ -252,6 +257,7 @@ __global__ void __launch_bounds__(TMAX, 1)
       if (tid == 0) {
         S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;
         if (!isfinite(cn_new)) S->isc[1] = 1;
+        if (cn_new <= stop_at) S->isc[4] = 1;
         cn = cn_new;
       }
       __syncthreads();

@@ -169,11 +169,16 @@ __global__ void __launch_bounds__(TMAX, 1) cluster_kernel(const __grid_constant_
     int set = 0;
     double cn = cluster_sum<C>(cluster, cs, set, block_sum_to_thread0(part, S));  // all gathers of y_ext done
     set ^= 1;
-    if (tid == 0) S->isc[1] = isfinite(cn) ? 0 : 1;
+    // every CTA's thread 0 holds the same rank-ordered sums, so all take the same decision
+    const double stop_at = io.eps2 > 0.0 ? io.eps2 * cn : -1.0;
+    if (tid == 0) {
+      S->isc[1] = isfinite(cn) ? 0 : 1;
+      S->isc[4] = cn <= stop_at ? 1 : 0;
+    }
     broadcast_ext<C>(cluster, ext, A, k, j0, p);
     cluster.sync();
 
-    for (int it = 0; it < io.iters; ++it) {
+    for (int it = 0; it < io.iters && !S->isc[4]; ++it) {
       gather_fwd<R, E>(ext, blk, paths, runs, nruns, A, 0, k, j0, v);  // t = H p
       cluster.sync();                                                   // p_ext no longer read
       broadcast_ext<C>(cluster, ext, A, k, j0, v);
@@ -205,6 +210,7 @@ __global__ void __launch_bounds__(TMAX, 1) cluster_kernel(const __grid_constant_
       if (tid == 0) {
         S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;  // beta, FP64
         if (!isfinite(cn_new)) S->isc[1] = 1;
+        if (cn_new <= stop_at) S->isc[4] = 1;
         cn = cn_new;
       }
       __syncthreads();

@@ -86,6 +86,7 @@ struct FrameArgs {
   const float* noise_var;
   const float* theta;
   int iters;
+  double eps2;  // CG stopping test: stop once ||c||^2 <= eps2 ||b||^2; 0 = off
   const void* v_in;
   int adjoint;
   const void* x_in;
@@ -145,6 +146,7 @@ struct FrameIO {
   const char* x_in;     // x_hat input [t][MN] (demap-only mode)
   float lam, theta;
   int iters;
+  double eps2;          // CG stopping test of this frame (0 = fixed iterations)
   int bps;              // bits per QAM symbol of this frame
   double pam_d;         // PAM half-spacing of this frame's QAM (unit mean energy)
   double a_pilot;       // pilot amplitude divided out of the read-off
@@ -160,7 +162,7 @@ struct SharedHdr {       // fixed part of the dynamic shared memory
   uint64_t mbar;
   double dsc[4];
   double fsc[4];
-  int isc[4];
+  int isc[6];            // [4]: the CG stopping test has fired
   int scan[40];
   double red[32];
   int hist[128];         // radix-select histogram of the read-off (kept zero between uses)

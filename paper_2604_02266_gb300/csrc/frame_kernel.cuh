@@ -50,6 +50,7 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
     io.lam = d.noise_var;
     io.theta = d.theta;
     io.iters = d.iters;
+    io.eps2 = (double)d.cg_eps * (double)d.cg_eps;
     io.bps = 31 - __clz(d.qam);
     io.pam_d = sqrt(3.0 / (2.0 * (d.qam - 1)));
     io.a_pilot = d.a_pilot;
@@ -77,6 +78,7 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
   io.lam = A.noise_var ? A.noise_var[f] : 0.f;
   io.theta = A.theta ? A.theta[f] : 0.f;
   io.iters = A.iters;
+  io.eps2 = A.eps2;
   io.bps = A.bps;
   io.pam_d = A.pam_d;
   io.a_pilot = A.a_pilot;
@@ -329,14 +331,19 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           }
         }
       double cn = block_sum_to_thread0(part, S);  // valid in thread 0
-      if (tid == 0) S->isc[1] = isfinite(cn) ? 0 : 1;
-      __syncthreads();  // all gathers of y_ext done; flag published
+      const double stop_at = io.eps2 > 0.0 ? io.eps2 * cn : -1.0;  // eps^2 ||b||^2 (thread 0)
+      if (tid == 0) {
+        S->isc[1] = isfinite(cn) ? 0 : 1;
+        S->isc[4] = cn <= stop_at ? 1 : 0;
+      }
+      __syncthreads();  // all gathers of y_ext done; flags published
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (t < A.ntx) write_ext<R, E>(ext + t * blk, A, k, j0, p[t]);
       __syncthreads();
 
-      for (int it = 0; it < io.iters; ++it) {
+      // the stopping test's flag is read after the barrier that follows the p update
+      for (int it = 0; it < io.iters && !S->isc[4]; ++it) {
         // t = H p
 #pragma unroll
         for (int r = 0; r < NB; ++r)
@@ -380,6 +387,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
         if (tid == 0) {
           S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;  // beta, FP64
           if (!isfinite(cn_new)) S->isc[1] = 1;
+          if (cn_new <= stop_at) S->isc[4] = 1;
           cn = cn_new;
         }
         __syncthreads();

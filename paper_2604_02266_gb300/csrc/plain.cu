@@ -143,11 +143,14 @@ __global__ void plain_apply_kernel(PlainGeo G, const PathRec* paths, const int* 
   u[(size_t)b * MN + q] = acc;
 }
 
-enum { kCn = 0, kAlpha = 1, kBeta = 2 };
+enum { kCn = 0, kAlpha = 1, kBeta = 2, kStopAt = 3, kStopped = 4 };
 enum { kEpiCn0 = 0, kEpiAlpha = 1, kEpiBeta = 2 };
 
 // Single CTA: sum of Re(conj(a) b); FP32 per thread, FP64 across warps; scalar epilogue.
-__global__ void plain_dot_kernel(const float2* a, const float2* b, int n, double* scal, int epi, int* flags) {
+// eps2 > 0: the CG stopping test (||c||^2 <= eps2 ||b||^2); once it fires, alpha = beta = 0
+// leave x and c as they are for the remaining launches of the iteration loop.
+__global__ void plain_dot_kernel(const float2* a, const float2* b, int n, double* scal, int epi, int* flags,
+                                 double eps2) {
   float s = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s = fmaf(a[i].x, b[i].x, fmaf(a[i].y, b[i].y, s));
   s = warp_sum(s);
@@ -161,11 +164,16 @@ __global__ void plain_dot_kernel(const float2* a, const float2* b, int n, double
     if (lane == 0) {
       if (epi == kEpiCn0) {
         scal[kCn] = d;
+        scal[kStopAt] = eps2 > 0.0 ? eps2 * d : -1.0;
+        scal[kStopped] = d <= scal[kStopAt] ? 1.0 : 0.0;
       } else if (epi == kEpiAlpha) {
-        scal[kAlpha] = d != 0.0 ? scal[kCn] / d : 0.0;
+        scal[kAlpha] = scal[kStopped] != 0.0 ? 0.0 : (d != 0.0 ? scal[kCn] / d : 0.0);
+      } else if (scal[kStopped] != 0.0) {
+        scal[kBeta] = 0.0;
       } else {
         scal[kBeta] = scal[kCn] != 0.0 ? d / scal[kCn] : 0.0;
         scal[kCn] = d;
+        if (d <= scal[kStopAt]) scal[kStopped] = 1.0;
       }
       if (!isfinite(d)) flags[1] = 1;
     }
@@ -338,7 +346,7 @@ zotfs_status run_plain(zotfs_plan_s* plan, const void* y_pilot_td, const void* y
     const float* lamp = noise_var + f;
     plain_apply_kernel<<<nblk(nx), kBlock, 0, stream>>>(G, pl, counts, ydd, cv, 1, 0.f, nullptr);  // b -> c
     plain_init_kernel<<<nblk(nx), kBlock, 0, stream>>>(cv, xv, cv, pv, nx);
-    plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiCn0, flags);
+    plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiCn0, flags, A.eps2);
     g_launches += 3;
     for (int it = 0; it < iters; ++it) {
       plain_apply_kernel<<<nblk(nrx * MN), kBlock, 0, stream>>>(G, pl, counts, pv, tv, 0, 0.f, nullptr);
@@ -347,9 +355,9 @@ zotfs_status run_plain(zotfs_plan_s* plan, const void* y_pilot_td, const void* y
       g_launches += 2;
       plain_addlam_kernel<<<nblk(nx), kBlock, 0, stream>>>(av, pv, lamp, nx);
       ++g_launches;
-      plain_dot_kernel<<<1, 1024, 0, stream>>>(pv, av, nx, scal, kEpiAlpha, flags);
+      plain_dot_kernel<<<1, 1024, 0, stream>>>(pv, av, nx, scal, kEpiAlpha, flags, A.eps2);
       plain_xc_kernel<<<nblk(nx), kBlock, 0, stream>>>(xv, cv, pv, av, scal, nx);
-      plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiBeta, flags);
+      plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiBeta, flags, A.eps2);
       plain_p_kernel<<<nblk(nx), kBlock, 0, stream>>>(pv, cv, scal, nx);
       g_launches += 4;
     }
@@ -546,15 +554,15 @@ extern "C" zotfs_status zotfs_equalize_static(int M, int N, int n_rx, int n_tx, 
     const float* lamp = noise_var + f;
     plain_apply_kernel<<<nblk(nx), kBlock, 0, stream>>>(G, pl, counts, yf, cv, 1, 0.f, nullptr);  // b -> c
     plain_init_kernel<<<nblk(nx), kBlock, 0, stream>>>(cv, xv, cv, pv, nx);
-    plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiCn0, flags);
+    plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiCn0, flags, 0.0);  // fixed iterations
     g_launches += 4;
     for (int it = 0; it < iters; ++it) {
       plain_apply_kernel<<<nblk(n_rx * MN), kBlock, 0, stream>>>(G, pl, counts, pv, tv, 0, 0.f, nullptr);
       plain_apply_kernel<<<nblk(nx), kBlock, 0, stream>>>(G, pl, counts, tv, av, 1, 0.f, nullptr);
       plain_addlam_kernel<<<nblk(nx), kBlock, 0, stream>>>(av, pv, lamp, nx);
-      plain_dot_kernel<<<1, 1024, 0, stream>>>(pv, av, nx, scal, kEpiAlpha, flags);
+      plain_dot_kernel<<<1, 1024, 0, stream>>>(pv, av, nx, scal, kEpiAlpha, flags, 0.0);
       plain_xc_kernel<<<nblk(nx), kBlock, 0, stream>>>(xv, cv, pv, av, scal, nx);
-      plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiBeta, flags);
+      plain_dot_kernel<<<1, 1024, 0, stream>>>(cv, cv, nx, scal, kEpiBeta, flags, 0.0);
       plain_p_kernel<<<nblk(nx), kBlock, 0, stream>>>(pv, cv, scal, nx);
       g_launches += 7;
     }

@@ -180,6 +180,7 @@ zotfs_status validate_request(const zotfs_server_s* s, const zotfs_request& r) {
   if ((reinterpret_cast<uintptr_t>(r.y_pilot) | reinterpret_cast<uintptr_t>(r.y_data)) & 15u)
     return bad("frames must be 16-byte aligned");
   if (!std::isfinite(r.noise_var) || r.noise_var < 0.f || !std::isfinite(r.theta)) return bad("noise_var / theta");
+  if (!std::isfinite(r.cg_eps) || r.cg_eps < 0.f) return bad("cg_eps must be finite and >= 0");
   return ZOTFS_OK;
 }
 
@@ -213,6 +214,7 @@ cudaError_t launch_wave(zotfs_server_s* s, Wave& w) {
     d.K0 = r.M / 2;
     d.L0 = r.N / 2;
     d.noise_var = r.noise_var;
+    d.cg_eps = r.cg_eps;
     d.theta = r.theta;
     d.a_pilot = r.a_pilot > 0.f ? r.a_pilot : (float)std::sqrt((double)r.M * r.N);
     d.y_pilot = r.y_pilot;

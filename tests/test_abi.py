@@ -52,10 +52,11 @@ def test_struct_layouts_match_header_sizes(libpath):
     """The ctypes mirrors have the sizes the C compiler gives the header's structs."""
     from paper_2604_02266_gb300 import _zotfs as Z
     # all fields are 4-byte ints/floats or 8-byte pointers in declaration order
-    assert ctypes.sizeof(Z.zotfs_options) == 36
+    assert ctypes.sizeof(Z.zotfs_options) == 40
     assert ctypes.sizeof(Z.zotfs_paths) == 5 * 8 + 8
     assert ctypes.sizeof(Z.zotfs_tuning) == 16
-    assert ctypes.sizeof(Z.zotfs_frame_desc) == 15 * 4 + 4 + 9 * 8  # 15 scalars, pad, 9 pointers
+    assert ctypes.sizeof(Z.zotfs_frame_desc) == 16 * 4 + 9 * 8  # 16 scalars, 9 pointers
+    assert ctypes.sizeof(Z.zotfs_request) == 10 * 4 + 3 * 8  # 10 scalars, 2 pointers, the tag
     assert ctypes.sizeof(Z.zotfs_batch_opts) == 4 * 4 + 8 + 4 + 4  # ..., max_sms, cluster
     assert ctypes.sizeof(Z.zotfs_autotune_opts) == 12
     assert ctypes.sizeof(Z.zotfs_tuning_entry) == 4 * 4 + 16

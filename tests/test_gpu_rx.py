@@ -30,7 +30,7 @@ def Plan(*a, **k):
     return P(*a, **k)
 
 
-def _check_frames(b, out, frames, M, N, nrx, ntx, Q, iters, p_max, region=None, embedded=False):
+def _check_frames(b, out, frames, M, N, nrx, ntx, Q, iters, p_max, region=None, embedded=False, cg_eps=0.0):
     """Validate path lists, then compare x_hat / LLRs / bits with the oracle run on the
     library's lists.  Returns (worst x rel-L2, worst LLR rel-L2, bit mismatches)."""
     lists = out["paths"].to_host()
@@ -57,7 +57,7 @@ def _check_frames(b, out, frames, M, N, nrx, ntx, Q, iters, p_max, region=None, 
         if embedded:
             from oracle import receiver
             y_dd = receiver.subtract_pilot(y_dd, grid[0][0], b["a_pilot"])
-        ref = eq.cga(grid, y_dd, lam, iters)
+        ref = eq.cga(grid, y_dd, lam, iters, eps=cg_eps)
         worst_x = max(worst_x, rel_l2(x[f].reshape(-1), ref))
         llr_ref = qam.maxlog_llr(ref, lam, Q)
         if L is not None:
