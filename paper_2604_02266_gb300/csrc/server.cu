@@ -38,6 +38,7 @@ int64_t now_ns() {
 
 constexpr int kWorkers = 8;       // worker streams per wave
 constexpr int kMaxBuckets = 128;  // shape buckets per wave
+constexpr int kServerCluster = 2;  // CTAs per MIMO frame too large for one CTA's shared memory
 
 struct Pending {
   zotfs_request r;
@@ -285,12 +286,21 @@ cudaError_t launch_wave(zotfs_server_s* s, Wave& w) {
       const int grid = std::max(1, std::min(nf, s->sm_count * std::max(occ, 1)));
       e = frame_variant_launch(fc.variant, A, kDefaultRadix, grid, fc.T, fc.smem, st);
     } else {
-      BigCfg bc;
-      if (!choose_big_cfg(M, N, nrx, ntx, s->o.p_max, bc)) return cudaErrorInvalidValue;
-      bc.slot_bytes = s->big_slot_bytes;
+      // MIMO frames on 2-CTA clusters (half the frame latency of one CTA per frame at the
+      // same cost per SM), one scratch slot per cluster; SISO frames on one CTA each
       const int share = big_share[big_idx++];
-      const int grid = std::min(nf, share);
-      e = big_launch(bc, A, kDefaultRadix, grid, w.d_big + (size_t)big_next * s->big_slot_bytes, st);
+      char* slots = w.d_big + (size_t)big_next * s->big_slot_bytes;
+      BigClusterCfg bcc;
+      if (nrx * ntx > 1 && choose_big_cluster_cfg(M, N, nrx, ntx, s->o.p_max, kServerCluster, bcc)) {
+        bcc.slot_bytes = s->big_slot_bytes;
+        const int clusters = std::max(1, std::min(nf, share / kServerCluster));
+        e = big_cluster_launch(bcc, A, kDefaultRadix, clusters, slots, st);
+      } else {
+        BigCfg bc;
+        if (!choose_big_cfg(M, N, nrx, ntx, s->o.p_max, bc)) return cudaErrorInvalidValue;
+        bc.slot_bytes = s->big_slot_bytes;
+        e = big_launch(bc, A, kDefaultRadix, std::min(nf, share), slots, st);
+      }
       big_next += share;
     }
     if (e != cudaSuccess) return e;
@@ -472,6 +482,9 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
               break;
             }
             s->big_slot_bytes = std::max(s->big_slot_bytes, bc.slot_bytes);
+            BigClusterCfg bcc;
+            if (nr * nt > 1 && choose_big_cluster_cfg(M, N, nr, nt, o.p_max, kServerCluster, bcc))
+              s->big_slot_bytes = std::max(s->big_slot_bytes, bcc.slot_bytes);
           }
     }
   if (e != cudaSuccess && !st) st = cuda_fail(e, "server setup");

@@ -126,6 +126,15 @@ def check_path_list(M, N, lib_list, heff, theta, p_max, region=None, rtol=1e-4):
     return n_amb
 
 
+def served_plan(M, N, nrx, ntx, Q, **opts):
+    """A plan that runs a frame on the kernel the serving loop picks for it: MIMO frames too
+    large for one CTA's shared memory on 2-CTA clusters, every other frame on one CTA."""
+    from paper_2604_02266_gb300 import Plan
+    plan = Plan(M, N, nrx, ntx, Q, **opts)
+    plan.set_tuning(cluster=2 if nrx * ntx > 1 else 1)
+    return plan
+
+
 def one_cta_plan(M, N, nrx, ntx, Q, **opts):
     """A plan that runs every frame on one CTA (no cluster receiver): the kernels that uneven
     batches and the serving loop use, so their results can be compared bit for bit."""

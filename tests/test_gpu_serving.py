@@ -11,7 +11,7 @@ import pytest
 import torch
 
 import synth
-from tests.gpu_util import TOL_LLR, TOL_X, dev, one_cta_plan, to_dev
+from tests.gpu_util import TOL_LLR, TOL_X, dev, served_plan, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -81,7 +81,7 @@ def test_served_mix_equals_alone():
             M, N, nrx, ntx, Q = fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"]
             bps = int(np.log2(Q))
             served = srv.read(i, ntx, M * N, bps, nrx * ntx, llr=True)
-            plan = one_cta_plan(M, N, nrx, ntx, Q)
+            plan = served_plan(M, N, nrx, ntx, Q)
             b = fr["b"]
             alone = plan.rx(fr["yp"][None], fr["yd"][None], to_dev(b["noise_var"]), to_dev(b["theta"]), fr["iters"], 1,
                             want_paths=True, want_llr=True)
@@ -162,7 +162,7 @@ def test_light_frames_have_their_own_queue():
             M, N, nrx, ntx, Q = fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"]
             served = srv.read(i, ntx, M * N, int(np.log2(Q)), nrx * ntx, llr=True)
             b = fr["b"]
-            alone = one_cta_plan(M, N, nrx, ntx, Q).rx(fr["yp"][None], fr["yd"][None], to_dev(b["noise_var"]),
+            alone = served_plan(M, N, nrx, ntx, Q).rx(fr["yp"][None], fr["yd"][None], to_dev(b["noise_var"]),
                                                to_dev(b["theta"]), fr["iters"], 1, want_llr=True)
             assert np.array_equal(served["bits"], alone["bits"].cpu().numpy().reshape(-1)), i
             assert np.array_equal(served["llr"], alone["llr"].cpu().numpy().reshape(-1)), i
@@ -172,5 +172,36 @@ def test_light_frames_have_their_own_queue():
         assert light and heavy
         # all were submitted together: the light frames' admissions do not wait for heavy ones
         assert max(got[i][2] for i in light) <= max(got[i][3] for i in heavy)
+    finally:
+        srv.close()
+
+
+def test_served_frames_with_stopping_test_equal_alone():
+    """zotfs_request.cg_eps reaches the frame's kernel: served frames that ask for the CG
+    stopping test equal the same frames run alone with that plan option, bit for bit."""
+    from paper_2604_02266_gb300 import Server
+    frames = _frames(8, seed=17, shapes=[(64, 32), (64, 64)], ants=[(1, 1), (4, 4)])
+    eps = 0.05
+    srv = Server(p_max=64, max_wave_frames=8, waves_in_flight=2, keep_llr=True, arena_bytes=256 << 20, max_M=128,
+                 max_N=64, max_ant=4)
+    try:
+        reqs = []
+        for i, fr in enumerate(frames):
+            b = fr["b"]
+            reqs.append(Server.request(i, fr["yp"], fr["yd"], fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"],
+                                       fr["iters"], float(b["noise_var"][0]), float(b["theta"][0]), cg_eps=eps))
+        srv.submit(reqs)
+        got = _drain(srv, len(frames))
+        for i, fr in enumerate(frames):
+            assert got[i][0] in (0, 6), (i, got[i][0])
+            M, N, nrx, ntx, Q = fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"]
+            served = srv.read(i, ntx, M * N, int(np.log2(Q)), nrx * ntx, llr=True)
+            b = fr["b"]
+            alone = served_plan(M, N, nrx, ntx, Q, cg_eps=eps).rx(fr["yp"][None], fr["yd"][None],
+                                                                   to_dev(b["noise_var"]), to_dev(b["theta"]),
+                                                                   fr["iters"], 1, want_llr=True)
+            assert np.array_equal(served["llr"], alone["llr"].cpu().numpy().reshape(-1)), i
+            assert np.array_equal(served["bits"], alone["bits"].cpu().numpy().reshape(-1)), i
+            srv.release(i)
     finally:
         srv.close()
