@@ -9,11 +9,9 @@
 // Shared-memory vector layout ("ext").  The vector an operator gathers from is stored as
 // its quasi-periodic extension (footnote of Eq. y_channel_DD):
 //     X_ext[A, r] = X[<A>_M, <r>_N] exp(j2pi floor(A/M) <r>_N / N)
-// for columns A in [-M/2, 3M/2) and rows r in [0, CS), column-major: element (A, r) at
-// (A + M/2) CS + r.  CS = ext_rows(N, E) covers the N rows and the periodic halo rows a window
-// reads (up to row N + E + 1); in FP32 it is rounded up to 2 mod 4, so that a window is read
-// as 16-byte row pairs from an even row and the 8 consecutive columns a quarter-warp reads
-// fall in distinct banks; in FP64 (one 16-byte element per load) it is odd.
+// for columns A in [-M/2, 3M/2) and rows r in [0, N + E + 3), column-major: element (A, r)
+// at (A + M/2) CS + r with column stride CS = N + E + 3 (odd, so the 32 consecutive columns
+// a warp reads fall in distinct banks).
 // With it, path p's contribution to output (k, l) -- the twisted shift of Sec. IV-B with
 // map Eq. map_chMatDD_col, wrap count n and phase phi -- becomes a plain shifted read:
 //     (H v)[k, l]   = sum_p h_p W[dl (k - dk)]      X_ext[k - dk, l - dl]
@@ -22,8 +20,8 @@
 // phase exp(j2pi n l_{p,q} / N) of the paper's phi is carried by the stored halo columns,
 // the term (l_p - L0) A by the per-(path, column) coefficient, so each gather is one
 // shared load at a constant offset and two packed FMAs.  Rows are periodic (no phase), so
-// the halo rows let a thread read a window of up to E + 3 consecutive source rows (and the
-// row pair around it) without a wrap.  Paths are applied in runs: paths with equal dk and consecutive dl read overlapping
+// E + 3 halo rows let a thread read a window of up to E + 3 consecutive source rows without a
+// wrap.  Paths are applied in runs: paths with equal dk and consecutive dl read overlapping
 // rows, so a run of L <= 4 such paths loads one (L + E - 1)-row window into registers and
 // applies all L paths from it.
 //
@@ -171,15 +169,9 @@ struct SharedHdr {       // fixed part of the dynamic shared memory
 };
 
 // Shared-memory bytes needed by a frame kernel launch (host and device agree on this).
-// Rows of the extension = its column stride CS (see the layout note at the top).
-__host__ __device__ __forceinline__ int ext_rows(int N, int E, int real_bytes = 4) {
-  int cs = N + E + 2;
-  if (real_bytes == 8) return cs | 1;
-  while ((cs & 3) != 2) ++cs;
-  return cs;
-}
-__host__ __device__ __forceinline__ size_t ext_block_elems(int M, int N, int E, int real_bytes = 4) {
-  return (size_t)ext_rows(N, E, real_bytes) * (size_t)(2 * M);
+__host__ __device__ __forceinline__ int ext_rows(int N, int E) { return N + E + 3; }  // = column stride CS
+__host__ __device__ __forceinline__ size_t ext_block_elems(int M, int N, int E) {
+  return (size_t)ext_rows(N, E) * (size_t)(2 * M);
 }
 // Bytes of the per-(path, delay column) coefficient tables: forward and adjoint forms, one
 // complex value per path and column k for every antenna pair.
@@ -197,7 +189,7 @@ __host__ __device__ __forceinline__ size_t frame_smem_bytes(int M, int N, int E,
   paths += ((size_t)((p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);     // sort keys
   if (coef) paths += coef_table_bytes(M, nrx, ntx, p_max, real_bytes);
   int nb = nrx > ntx ? nrx : ntx;
-  size_t ext = (size_t)nb * ext_block_elems(M, N, E, real_bytes) * 2 * real_bytes;
+  size_t ext = (size_t)nb * ext_block_elems(M, N, E) * 2 * real_bytes;
   return hdr + paths + ext;
 }
 
@@ -306,7 +298,7 @@ template <typename R, int E, bool kRowMajor = false>
 __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArgs& A, int k, int j0,
                                           const typename Cx<R>::C (&v)[E]) {
   using C = typename Cx<R>::C;
-  const int M = A.M, N = A.N, CS = ext_rows(N, E, (int)sizeof(R)), Hk = M >> 1, logM = A.logM, MN = M * N;
+  const int M = A.M, N = A.N, CS = N + E + 3, Hk = M >> 1, logM = A.logM, MN = M * N;
   const size_t rstep = kRowMajor ? (size_t)(2 * M) : 1;  // distance between consecutive rows
   // halo column: k < M/2 stores X_ext[k + M] = X[k] W_N[l]; k >= M/2 stores X_ext[k - M] = X[k] W_N[-l]
   const bool low = k < Hk;
@@ -320,9 +312,9 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
     const C hv = cmul(v[i], tw<R>(A, widx));
     mcol[l * rstep] = v[i];
     hcol[l * rstep] = hv;
-    // periodic halo rows N .. CS - 1 hold row (r mod N): one copy when N >= CS - N, two for
-    // the short grids (N = 8 with E = 8, N = 16 with E = 16)
-    for (int r = l + N; r < CS; r += N) {
+    // periodic halo rows N .. N + E + 2 hold row (r mod N): one copy when N >= E + 3, two
+    // for the short grids (N = 8 with E = 8, N = 16 with E = 16)
+    for (int r = l + N; r < N + E + 3; r += N) {
       mcol[r * rstep] = v[i];
       hcol[r * rstep] = hv;
     }
@@ -339,14 +331,19 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
 // of path 0; path p at ct[p M]) -- hf W[dl k] for kFwd, h W[dl k] for the adjoint, whose
 // conjugate the caller's final combine applies -- else they are formed here from the path
 // record and the twiddle table.
-// The L paths of a run applied from a window held in registers: path m reads W[OFF + (kFwd ?
-// L - 1 - m : m) + i] for output row i.
-template <typename R, int E, int L, int OFF, bool kFwd, bool kCoef>
-__device__ __forceinline__ void run_paths(const typename Cx<R>::C* W, const PathRecT<R>* pl,
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
+__device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
                                           const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
-                                          typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
+                                          int j0, typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
   using C = typename Cx<R>::C;
   const int M = A.M, N = A.N;
+  const int CS = kRowMajor ? 1 : N + E + 3;
+  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;
+  const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
+  const C* a = src + (size_t)row0 * RS + (kFwd ? -rr.dk : rr.dk) * CS;
+  C W[L + E - 1];
+#pragma unroll
+  for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
   const C* cr = kCoef ? ct + (size_t)rr.start * M : nullptr;
 #pragma unroll
   for (int m = 0; m < L; ++m) {
@@ -360,49 +357,7 @@ __device__ __forceinline__ void run_paths(const typename Cx<R>::C* W, const Path
     }
     const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
 #pragma unroll
-    for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, W[OFF + (kFwd ? L - 1 - m : m) + i]);
-  }
-}
-
-template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
-__device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
-                                          const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
-                                          int j0, typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
-  using C = typename Cx<R>::C;
-  const int M = A.M, N = A.N;
-  const int CS = kRowMajor ? 1 : ext_rows(N, E, (int)sizeof(R));
-  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;
-  const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
-  const C* a = src + (size_t)row0 * RS + (kFwd ? -rr.dk : rr.dk) * CS;
-  if constexpr (!kRowMajor && sizeof(C) == 8) {
-    // FP32 column-major: read the window as 16-byte row pairs from the even row at or below
-    // row0 (CS is even and every column starts 16-byte aligned); the row parity is the same
-    // for a warp's threads (j0 is a multiple of E), so the branch does not diverge
-    constexpr int kOdd = (L + E + 1) / 2, kEven = (L + E) / 2;  // pairs for an odd / even row0
-    const float4* a2 = reinterpret_cast<const float4*>(a - (row0 & 1));
-    C W[2 * kOdd];
-    if (row0 & 1) {
-#pragma unroll
-      for (int w = 0; w < kOdd; ++w) {
-        const float4 v = a2[w];
-        W[2 * w] = make_float2(v.x, v.y);
-        W[2 * w + 1] = make_float2(v.z, v.w);
-      }
-      run_paths<R, E, L, 1, kFwd, kCoef>(W, pl, ct, rr, A, k, accA, accB);
-    } else {
-#pragma unroll
-      for (int w = 0; w < kEven; ++w) {
-        const float4 v = a2[w];
-        W[2 * w] = make_float2(v.x, v.y);
-        W[2 * w + 1] = make_float2(v.z, v.w);
-      }
-      run_paths<R, E, L, 0, kFwd, kCoef>(W, pl, ct, rr, A, k, accA, accB);
-    }
-  } else {
-    C W[L + E - 1];
-#pragma unroll
-    for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
-    run_paths<R, E, L, 0, kFwd, kCoef>(W, pl, ct, rr, A, k, accA, accB);
+    for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, W[(kFwd ? L - 1 - m : m) + i]);
   }
 }
 
@@ -416,7 +371,7 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
   // register budget: the window holds L + E - 1 complex values beside 2E accumulators
   constexpr int kLMax = E >= 32 ? 1 : (E >= 16 ? 2 : kMaxRun);
   const int Hk = A.M >> 1;
-  const int CS = kRowMajor ? 1 : ext_rows(A.N, E, (int)sizeof(R));
+  const int CS = kRowMajor ? 1 : A.N + E + 3;
   C accA[E], accB[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
   C* ext = reinterpret_cast<C*>(smem + off);
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM;
-  const size_t blk = ext_block_elems(M, N, E, (int)sizeof(R));
+  const size_t blk = ext_block_elems(M, N, E);
   const int tid = threadIdx.x;
   const int k = tid & (M - 1);
   const int j0 = (tid >> logM) * E;
