@@ -251,6 +251,23 @@ static bool big_cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, cons
 }
 
 static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream) {
+  if (plan->d_grid) {  // paper-scale grid: one frame at a time on the whole GPU
+    if (plan->opt.pilot_mode != ZOTFS_PILOT_SEPARATE) {
+      set_error("grids with M > 256 or M*N > 16384 take separate pilot frames only");
+      return ZOTFS_EUNSUPPORTED;
+    }
+    GridCfg gc;
+    cudaError_t e = choose_grid_cfg(plan->M, plan->N, plan->opt.p_max, plan->sm_count, gc);
+    if (e != cudaSuccess) return cuda_fail(e, "grid receiver configuration");
+    if (grid_scratch_size(plan->M, plan->N, plan->opt.p_max, gc.grid) > plan->grid_bytes) {
+      set_error("grid receiver scratch too small");
+      return ZOTFS_EUNSUPPORTED;
+    }
+    e = grid_launch(gc, A, plan->d_grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid receiver launch");
+    ++g_launches;
+    return ZOTFS_OK;
+  }
   ClusterCfg cc;
   if (cluster_applies(plan, nrx, ntx, A, cc)) {
     int clusters = 0;
@@ -328,10 +345,14 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
   g_launches = 0;
   if (!out) return inval("out is NULL");
   *out = nullptr;
-  if (!is_pow2(M) || M < 16 || M > 256) return inval("M must be a power of two in [16, 256]");
+  if (!is_pow2(M) || M < 16 || M > 16384) return inval("M must be a power of two in [16, 16384]");
   if (!is_pow2(N) || N < 8 || N > 64) return inval("N must be a power of two in [8, 64]");
-  if (M * N > 16384) return inval("M*N must be <= 16384");
   if (n_rx < 1 || n_rx > 4 || n_tx < 1 || n_tx > 4) return inval("n_rx, n_tx must be in [1, 4]");
+  const bool paper_scale = M > 256 || M * N > 16384;  // the grid receiver
+  if (paper_scale && (n_rx != 1 || n_tx != 1))
+    return inval("grids with M > 256 or M*N > 16384 are SISO only (n_rx = n_tx = 1)");
+  if (paper_scale && ((size_t)M * N > kGridMaxElems || M < 32))
+    return inval("grids with M > 256 or M*N > 16384 need 32 <= M and M*N <= 524288");
   if (qam != 4 && qam != 16 && qam != 64) return inval("qam must be 4, 16 or 64");
   if (pulse != ZOTFS_PULSE_SINC && pulse != ZOTFS_PULSE_RECT) return inval("unknown pulse");
 
@@ -385,14 +406,19 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
       Tab[(size_t)(dl + N / 2) * M + k] = W[src];
       Tab64[(size_t)(dl + N / 2) * M + k] = W64[src];
     }
-  p->plain_bytes = plain_scratch_bytes(M, N, n_rx, n_tx, 256);
+  p->plain_bytes = paper_scale ? 0 : plain_scratch_bytes(M, N, n_rx, n_tx, 256);
   e = cudaMalloc(&p->d_W, sizeof(float2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab, sizeof(float2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_W64, sizeof(double2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab64, sizeof(double2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(int) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int) * kOrderCap * kOrderSlots);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_plain, p->plain_bytes);
+  if (e == cudaSuccess && p->plain_bytes) e = cudaMalloc(&p->d_plain, p->plain_bytes);
+  if (e == cudaSuccess && paper_scale) {
+    // scratch for the largest grid the receiver launches (two CTAs per SM) and p_max 256
+    p->grid_bytes = grid_scratch_size(M, N, 256, 2 * p->sm_count);
+    e = cudaMalloc(&p->d_grid, p->grid_bytes);
+  }
   {
     FrameCfg fc;
     BigCfg bc;
@@ -444,6 +470,7 @@ zotfs_status zotfs_plan_destroy(zotfs_plan plan) {
   if (plan->d_order) cudaFree(plan->d_order);
   if (plan->d_plain) cudaFree(plan->d_plain);
   if (plan->d_big) cudaFree(plan->d_big);
+  if (plan->d_grid) cudaFree(plan->d_grid);
   delete plan;
   return ZOTFS_OK;
 }
@@ -673,6 +700,10 @@ zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void*
   if ((!emb && !y_pilot_td) || !y_data_td || !noise_var || !theta || !status) return inval("NULL buffer");
   if (plan->opt.compute != ZOTFS_COMPUTE_FP32) {
     set_error("the plain form runs in FP32 only");
+    return ZOTFS_EUNSUPPORTED;
+  }
+  if (plan->d_grid) {
+    set_error("the plain form runs grids with M <= 256 and M*N <= 16384 only");
     return ZOTFS_EUNSUPPORTED;
   }
   if (paths) {

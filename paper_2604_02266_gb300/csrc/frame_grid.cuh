@@ -1,0 +1,618 @@
+// The receiver for paper-scale frames (M up to 16384, M N up to 524288: 4 MB per FP32
+// vector), one frame at a time on the whole GPU.  A cooperative persistent kernel: its CTAs
+// split every stage by delay columns (Zak transform tiles, operator gathers, CG updates,
+// demapping) or by contiguous index ranges (read-off, bit packing) and meet at grid barriers;
+// the frame's grid, the quasi-periodic extensions of p and t (row-major, as in the
+// large-frame kernel) and the CG vectors live in global scratch that stays in L2 (about
+// 45 MB at 16384 x 32).  The read-off is the threshold / stable-compaction / exact top-P_max
+// of the shared-memory kernel, with its scans and radix-select histograms taken over the grid.
+// Algorithm 1's scalars are FP64 sums of per-CTA partials taken in CTA order, so every CTA
+// derives the same alpha, beta and stopping decision.  SISO, separate pilot frames (or
+// loaded lists), FP32.
+#pragma once
+
+#include "frame_kernel.cuh"
+
+namespace zotfs {
+
+constexpr int kGridThreads = 256;
+constexpr int kGridE = 8;         // rows per work item: column k, rows j0 .. j0 + 7
+constexpr int kGridDftCols = 32;  // delay columns per Zak-transform tile
+constexpr uint32_t kGridMaxPolls = 1u << 22;
+
+constexpr int kGridMaxCtas = 1024;
+
+struct GridBarrier {
+  unsigned count;  // CTAs arrived at the current barrier
+  unsigned gen;    // barriers completed
+  int err;         // a wait gave up: every CTA leaves at its next barrier
+  int pad;
+};
+
+// Global scratch of one grid receiver (one frame at a time).
+struct GridScratch {
+  float2* Y;                     // [MN] Zak-transformed grid (pilot, then data), q = l M + k
+  float2* extP;                  // extensions of p and t (row-major, ext_block_elems(M, N, 8))
+  float2* extT;
+  float2 *X, *Cv, *Pv, *Vv;      // [MN] the CG vectors x, c, p and a
+  uint8_t* lab;                  // [MN] hard labels, bit j of the label = bit j of the symbol
+  PathRecT<float>* list;         // [p_max] the frame's path list
+  double* part;                  // [2 grid] per-CTA partial sums, two alternating sets
+  int* icnt;                     // [2 grid] per-CTA counts of the read-off compaction
+  int* hist;                     // [5 x 128] radix-select histograms (zeroed per frame)
+  GridBarrier* bar;
+};
+
+// Rows of the extension and bytes of the scratch for one (M, N, p_max) at a given grid.
+__host__ __device__ __forceinline__ size_t grid_scratch_bytes(int M, int N, int p_max, int grid) {
+  const size_t MN = (size_t)M * N, ext = ext_block_elems(M, N, kGridE);
+  size_t b = 0;
+  auto take = [&](size_t n) { b += (n + 255) & ~size_t(255); };
+  take(MN * 8);       // Y
+  take(ext * 8);      // extP
+  take(ext * 8);      // extT
+  for (int i = 0; i < 4; ++i) take(MN * 8);
+  take(MN);           // lab
+  take((size_t)p_max * sizeof(PathRecT<float>));
+  take((size_t)grid * 16);
+  take((size_t)grid * 8);
+  take(5 * 128 * 4);
+  take(sizeof(GridBarrier));
+  return b;
+}
+
+__host__ __device__ __forceinline__ GridScratch grid_scratch_carve(char* base, int M, int N, int p_max, int grid) {
+  const size_t MN = (size_t)M * N, ext = ext_block_elems(M, N, kGridE);
+  GridScratch G;
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    char* p = base + off;
+    off += (n + 255) & ~size_t(255);
+    return p;
+  };
+  G.Y = reinterpret_cast<float2*>(take(MN * 8));
+  G.extP = reinterpret_cast<float2*>(take(ext * 8));
+  G.extT = reinterpret_cast<float2*>(take(ext * 8));
+  G.X = reinterpret_cast<float2*>(take(MN * 8));
+  G.Cv = reinterpret_cast<float2*>(take(MN * 8));
+  G.Pv = reinterpret_cast<float2*>(take(MN * 8));
+  G.Vv = reinterpret_cast<float2*>(take(MN * 8));
+  G.lab = reinterpret_cast<uint8_t*>(take(MN));
+  G.list = reinterpret_cast<PathRecT<float>*>(take((size_t)p_max * sizeof(PathRecT<float>)));
+  G.part = reinterpret_cast<double*>(take((size_t)grid * 16));
+  G.icnt = reinterpret_cast<int*>(take((size_t)grid * 8));
+  G.hist = reinterpret_cast<int*>(take(5 * 128 * 4));
+  G.bar = reinterpret_cast<GridBarrier*>(take(sizeof(GridBarrier)));
+  return G;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier over all CTAs of the cooperative grid (co-resident by construction of the launch).
+// Every thread counts the barriers passed in `gen`.  Returns false in every thread of the CTA
+// when this wait or an earlier one gave up (bounded polls): the caller abandons the frame.
+// (Arrivals on per-CTA flags gathered by one warp were measured slower than one counter.)
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen) {
+  __syncthreads();
+  const unsigned g = gen;
+  gen = g + 1;
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    if (*reinterpret_cast<volatile int*>(&b->err) != 0) {
+      ok = 0;
+    } else {
+      __threadfence();
+      if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+        atomicExch(&b->count, 0u);
+        __threadfence();
+        atomicExch(&b->gen, g + 1);
+      } else {
+        uint32_t polls = 0;
+        while (ld_acquire_gpu(&b->gen) == g) {
+          if (++polls > kGridMaxPolls) {
+            atomicExch(&b->err, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Y[l M + k] = N^-1/2 sum_n y[k + n M] W_N^{-n l} (Eq. zak) for all columns: tiles of
+// kGridDftCols columns over all N rows staged in shared memory (coalesced along k), then one
+// direct N-point DFT per output.  `tile` holds N kGridDftCols values, `wn` N twiddles.
+__device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, const FrameArgs& A, float2* tile,
+                                         float2* wn) {
+  const int M = A.M, N = A.N, logM = A.logM;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) wn[i] = conjf2(tw<float>(A, (size_t)i << logM));
+  const float s = (float)A.inv_sqrtN;
+  const int ntiles = M / kGridDftCols;
+  __syncthreads();
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int k0 = t * kGridDftCols;
+    for (int e = threadIdx.x; e < N * kGridDftCols; e += blockDim.x) {
+      const int n = e / kGridDftCols, kk = e - n * kGridDftCols;
+      tile[e] = load_complex<float2>(src, (size_t)n * M + k0 + kk, dtype);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * kGridDftCols; e += blockDim.x) {
+      const int l = e / kGridDftCols, kk = e - l * kGridDftCols;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int n = 0; n < N; ++n) {
+        const float2 w = wn[(n * l) & (N - 1)], v = tile[n * kGridDftCols + kk];
+        acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
+        acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
+      }
+      Y[(size_t)l * M + k0 + kk] = cscale(acc, s);
+    }
+    __syncthreads();
+  }
+}
+
+// Sum of the CTAs' partials (each CTA's thread 0 stored part[blockIdx.x] before the barrier),
+// by warp 0 in a fixed order -- lane j adds CTAs j, j + 32, ..., then a butterfly over the
+// lanes -- so every CTA gets the same value; valid in thread 0.  Consecutive reductions
+// alternate between two sets of partials (part and part + gridDim.x): a CTA that has summed
+// one set may store into the other while a slower CTA is still summing the first.
+__device__ __forceinline__ double grid_partials(const double* part) {
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+#pragma unroll 4
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(part + b);
+    s = warp_sum_f64(s);
+  }
+  return s;
+}
+
+// This CTA's exclusive prefix and the grid total of one count per CTA, by warp 0; stored in
+// S->isc[2] (prefix) and S->isc[3] (total).
+__device__ __forceinline__ void grid_prefix(const int* counts, SharedHdr* S) {
+  if (threadIdx.x < 32) {
+    int pre = 0, tot = 0;
+#pragma unroll 4
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+      const int c = __ldcg(counts + b);
+      tot += c;
+      if (b < (int)blockIdx.x) pre += c;
+    }
+    pre = warp_sum_i(pre);
+    tot = warp_sum_i(tot);
+    if (threadIdx.x == 0) {
+      S->isc[2] = pre;
+      S->isc[3] = tot;
+    }
+  }
+  __syncthreads();
+}
+
+template <int EQ>
+__global__ void __launch_bounds__(kGridThreads, 2)
+    grid_kernel(const __grid_constant__ FrameArgs A, GridScratch G) {
+  using R = float;
+  using C = float2;
+  using PathRec = PathRecT<R>;
+  constexpr int E = kGridE;
+  extern __shared__ __align__(128) unsigned char smem[];
+  SharedHdr* S = reinterpret_cast<SharedHdr*>(smem);
+  size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
+  PathRec* paths = reinterpret_cast<PathRec*>(smem + off);
+  int* cnt = reinterpret_cast<int*>(paths + A.p_max);
+  int* nruns = cnt + 1;
+  off += ((size_t)A.p_max * sizeof(PathRec) + sizeof(int) * 2 + 127) & ~size_t(127);
+  RunRec* runs = reinterpret_cast<RunRec*>(smem + off);
+  off += ((size_t)A.p_max * sizeof(RunRec) + 127) & ~size_t(127);
+  PathRec* sort_tmp = reinterpret_cast<PathRec*>(smem + off);
+  off += ((size_t)A.p_max * sizeof(PathRec) + 127) & ~size_t(127);
+  int* sort_keys = reinterpret_cast<int*>(smem + off);
+  off += ((size_t)((A.p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);
+  C* tile = reinterpret_cast<C*>(smem + off);
+  off += (size_t)A.N * kGridDftCols * sizeof(C);
+  C* wn = reinterpret_cast<C*>(smem + off);
+
+  const int M = A.M, N = A.N, MN = M * N, logM = A.logM, tid = threadIdx.x;
+  const int gtid = blockIdx.x * blockDim.x + tid, nthr = gridDim.x * blockDim.x;
+  const int items = MN / E;  // (column k, row group j0 / E), k fastest
+  const size_t blk = ext_block_elems(M, N, E);
+  const bool write_paths = (A.mode & kWritePaths) != 0;
+  unsigned gen = 0;  // barriers passed
+  auto fail = [&](const FrameIO& io) {
+    if (tid == 0 && io.status) *io.status = ZOTFS_ETIMEOUT;
+  };
+
+  for (int f = 0; f < A.n_frames; ++f) {
+    const FrameIO io = frame_io(A, f, (int)sizeof(C));
+    int st = 0;
+    if (blockIdx.x == 0)
+      for (int i = tid; i < 5 * 128; i += blockDim.x) G.hist[i] = 0;
+
+    // ------------------------------------------------ Zak transform only
+    if (A.mode & kDzt) {
+      grid_dzt(io.y_data, A.in_dtype, reinterpret_cast<C*>(io.u_out), A, tile, wn);
+      if (!grid_sync(G.bar, gen)) return fail(io);
+      if (blockIdx.x == 0 && tid == 0 && io.status) *io.status = ZOTFS_OK;
+      continue;
+    }
+
+    // ------------------------------------------------ path list
+    int P = 0;
+    if (A.mode & kEstimate) {
+      grid_dzt(io.y_pilot, A.in_dtype, G.Y, A, tile, wn);
+      if (!grid_sync(G.bar, gen)) return fail(io);
+      // read-off: thread g owns q in [g EQ, g EQ + EQ) (Eq. heff_hadamard over the pilot grid)
+      const R scale = (R)(1.0 / io.a_pilot);
+      const R th2 = (R)io.theta * (R)io.theta;
+      C hv[EQ];
+      uint32_t mb[EQ];
+      uint32_t pass = 0;
+#pragma unroll
+      for (int i = 0; i < EQ; ++i) {
+        const int q = gtid * EQ + i;
+        hv[i] = make_float2(0.f, 0.f);
+        mb[i] = 0;
+        if (q < MN) {
+          const int l = q >> logM;
+          const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+          const C h = cscale(cmul(G.Y[q], tw<R>(A, (size_t)((-A.K0 * dl) & (MN - 1)))), scale);
+          const R m2 = h.x * h.x + h.y * h.y;
+          hv[i] = h;
+          mb[i] = __float_as_uint(m2);
+          if (m2 > th2) pass |= 1u << i;
+        }
+      }
+      int blk_total;
+      const int in_blk = block_exclusive_scan(__popc(pass), S->scan, blk_total);
+      if (tid == 0) G.icnt[blockIdx.x] = blk_total;
+      if (!grid_sync(G.bar, gen)) return fail(io);
+      grid_prefix(G.icnt, S);
+      int total = S->isc[3];
+      int base = S->isc[2] + in_blk;
+      uint32_t keep = pass;
+      int trunc = 0;
+      if (total > A.p_max) {
+        // the K-th largest |h|^2 among the passing taps, exactly: radix select on the bit
+        // patterns, 7 bits per pass, histograms over the whole grid
+        trunc = 1;
+        const int K = A.p_max;
+        uint32_t prefix = 0, fixed = 0;
+        int kleft = K;
+        int hp = 0;
+        for (int hb = 31; hb > 0; hb -= 7, ++hp) {
+          const int w = hb < 7 ? hb : 7, sh = hb - w;
+          int* H = G.hist + hp * 128;
+#pragma unroll
+          for (int i = 0; i < EQ; ++i)
+            if (((pass >> i) & 1u) && ((mb[i] ^ prefix) & fixed) == 0) atomicAdd(&H[(mb[i] >> sh) & 127u], 1);
+          if (!grid_sync(G.bar, gen)) return fail(io);
+          if (tid < 32) {  // the bin holding the kleft-th largest, from the top (lane: 4 bins)
+            const int lane = tid;
+            int c[4], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              c[j] = __ldcg(H + 4 * lane + j);
+              sum += c[j];
+            }
+            int suf = sum;  // inclusive suffix sum over lanes >= lane
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int n = __shfl_down_sync(0xffffffffu, suf, o);
+              if (lane + o < 32) suf += n;
+            }
+            int acc = suf - sum;  // taps in the bins above this lane's four
+#pragma unroll
+            for (int j = 3; j >= 0; --j) {
+              if (acc < kleft && acc + c[j] >= kleft) {
+                S->isc[2] = 4 * lane + j;
+                S->isc[3] = kleft - acc;
+              }
+              acc += c[j];
+            }
+          }
+          __syncthreads();
+          prefix |= (uint32_t)S->isc[2] << sh;
+          kleft = S->isc[3];
+          fixed |= ((1u << w) - 1u) << sh;
+          __syncthreads();
+        }
+        const uint32_t vK = prefix;  // the K-th largest value; `kleft` ties to it are kept
+        const int need = kleft;
+        uint32_t gt = 0, eq = 0;
+#pragma unroll
+        for (int i = 0; i < EQ; ++i)
+          if ((pass >> i) & 1u) {
+            if (mb[i] > vK) gt |= 1u << i;
+            else if (mb[i] == vK) eq |= 1u << i;
+          }
+        int tg, te;
+        const int gt_in = block_exclusive_scan(__popc(gt), S->scan, tg);
+        const int eq_in = block_exclusive_scan(__popc(eq), S->scan, te);
+        if (tid == 0) {
+          G.icnt[blockIdx.x] = tg;
+          G.icnt[gridDim.x + blockIdx.x] = te;
+        }
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        grid_prefix(G.icnt, S);
+        const int gt_pre = S->isc[2];
+        __syncthreads();
+        grid_prefix(G.icnt + gridDim.x, S);
+        int eq_before = S->isc[2] + eq_in;
+        base = gt_pre + gt_in + min(eq_before, need);
+        keep = 0;
+#pragma unroll
+        for (int i = 0; i < EQ; ++i) {
+          if ((gt >> i) & 1u) {
+            keep |= 1u << i;
+          } else if ((eq >> i) & 1u) {
+            if (eq_before < need) keep |= 1u << i;
+            ++eq_before;
+          }
+        }
+        total = K;
+      }
+      if (trunc) st |= kStTrunc;
+      const PathIO* gout = (write_paths && io.paths.count) ? &io.paths : nullptr;
+      int pos = base;
+#pragma unroll
+      for (int i = 0; i < EQ; ++i) {
+        if ((keep >> i) & 1u) {
+          const int q = gtid * EQ + i;
+          const int k = q & (M - 1), l = q >> logM;
+          const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
+          const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+          PathRec rec;
+          rec.h = hv[i];
+          rec.dk = dk;
+          rec.dl = dl;
+          rec.hf = cmul(hv[i], tw<R>(A, (size_t)((-dl * dk) & (MN - 1))));
+          rec.pad0 = rec.pad1 = 0;
+          G.list[pos] = rec;
+          if (gout) {
+            gout->dk[pos] = (int16_t)dk;
+            gout->dl[pos] = (int16_t)dl;
+            store_complex(gout->h, (size_t)pos, gout->tap_dtype, hv[i]);
+          }
+          ++pos;
+        }
+      }
+      if (gout && blockIdx.x == 0 && tid == 0) {
+        gout->count[0] = total;
+        if (gout->status) gout->status[0] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
+      }
+      if (!grid_sync(G.bar, gen)) return fail(io);
+      P = total;
+      for (int p = tid; p < P; p += blockDim.x) {
+        PathRec rec;
+        const float4* s4 = reinterpret_cast<const float4*>(G.list + p);
+        const float4 a = __ldcg(s4), b = __ldcg(s4 + 1);
+        rec.h = make_float2(a.x, a.y);
+        rec.hf = make_float2(a.z, a.w);
+        rec.dk = __float_as_int(b.x);
+        rec.dl = __float_as_int(b.y);
+        rec.pad0 = rec.pad1 = 0;
+        paths[p] = rec;
+      }
+      if (tid == 0) cnt[0] = P;
+      __syncthreads();
+    } else if (A.mode & kLoadPaths) {
+      int bad;
+      P = load_paths<R>(A, io.paths, 0, paths, bad);
+      if (tid == 0) cnt[0] = P;
+      if (bad) st |= kStInval;
+      __syncthreads();
+    }
+    if ((A.mode & (kEstimate | kLoadPaths)) && (A.mode & (kCG | kApply)))
+      build_runs<R>(paths, P, runs, sort_tmp, sort_keys, nruns);
+
+    C v[E];
+    // ------------------------------------------------ one operator apply
+    if (A.mode & kApply) {
+      C* src = A.adjoint ? G.extT : G.extP;
+      for (int it = gtid; it < items; it += nthr) {
+        const int k = it & (M - 1), j0 = (it >> logM) * E;
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = reinterpret_cast<const C*>(io.v_in)[(size_t)(j0 + i) * M + k];
+        write_ext<R, E, true>(src, A, k, j0, v);
+      }
+      if (!grid_sync(G.bar, gen)) return fail(io);
+      for (int it = gtid; it < items; it += nthr) {
+        const int k = it & (M - 1), j0 = (it >> logM) * E;
+        if (A.adjoint) gather_adj<R, E, true>(src, blk, paths, runs, nruns, A, 0, k, j0, v);
+        else gather_fwd<R, E, true>(src, blk, paths, runs, nruns, A, 0, k, j0, v);
+#pragma unroll
+        for (int i = 0; i < E; ++i) reinterpret_cast<C*>(io.u_out)[(size_t)(j0 + i) * M + k] = v[i];
+      }
+      if (!grid_sync(G.bar, gen)) return fail(io);
+      if (blockIdx.x == 0 && tid == 0 && io.status) *io.status = status_from_bits(st);
+      continue;
+    }
+
+    // ------------------------------------------------ equalisation (Algorithm 1)
+    if (A.mode & kCG) {
+      const R lam = (R)io.lam;
+      const C* Yd = reinterpret_cast<const C*>(io.y_data);
+      if (!A.y_is_dd) {
+        grid_dzt(io.y_data, A.in_dtype, G.Y, A, tile, wn);
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        Yd = G.Y;
+      }
+      for (int it = gtid; it < items; it += nthr) {
+        const int k = it & (M - 1), j0 = (it >> logM) * E;
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = Yd[(size_t)(j0 + i) * M + k];
+        write_ext<R, E, true>(G.extT, A, k, j0, v);
+      }
+      if (!grid_sync(G.bar, gen)) return fail(io);
+
+      // b = H^H y;  c = b, p = b, x = 0, c_n = ||c||^2
+      R part = 0;
+      for (int it = gtid; it < items; it += nthr) {
+        const int k = it & (M - 1), j0 = (it >> logM) * E;
+        gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const size_t o = (size_t)(j0 + i) * M + k;
+          G.Cv[o] = v[i];
+          G.Pv[o] = v[i];
+          G.X[o] = make_float2(0.f, 0.f);
+          part = fma(v[i].x, v[i].x, fma(v[i].y, v[i].y, part));
+        }
+        write_ext<R, E, true>(G.extP, A, k, j0, v);
+      }
+      double* const partA = G.part;               // Re(p^H a)
+      double* const partC = G.part + gridDim.x;   // ||c||^2
+      double d = block_sum_to_thread0(part, S);
+      if (tid == 0) partC[blockIdx.x] = d;
+      if (!grid_sync(G.bar, gen)) return fail(io);
+      double cn = grid_partials(partC);  // thread 0; the same in every CTA
+      const double stop_at = io.eps2 > 0.0 ? io.eps2 * cn : -1.0;
+      if (tid == 0) {
+        S->isc[1] = isfinite(cn) ? 0 : 1;
+        S->isc[4] = cn <= stop_at ? 1 : 0;
+      }
+      __syncthreads();
+
+      for (int iter = 0; iter < io.iters && !S->isc[4]; ++iter) {
+        // t = H p  (extP -> extT)
+        for (int it = gtid; it < items; it += nthr) {
+          const int k = it & (M - 1), j0 = (it >> logM) * E;
+          gather_fwd<R, E, true>(G.extP, blk, paths, runs, nruns, A, 0, k, j0, v);
+          write_ext<R, E, true>(G.extT, A, k, j0, v);
+        }
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        // a = H^H t + lambda p;  Re(p^H a)
+        part = 0;
+        for (int it = gtid; it < items; it += nthr) {
+          const int k = it & (M - 1), j0 = (it >> logM) * E;
+          gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            const size_t o = (size_t)(j0 + i) * M + k;
+            const C pv = G.Pv[o];
+            v[i].x = fma(lam, pv.x, v[i].x);
+            v[i].y = fma(lam, pv.y, v[i].y);
+            part = fma(pv.x, v[i].x, fma(pv.y, v[i].y, part));
+            G.Vv[o] = v[i];
+          }
+        }
+        d = block_sum_to_thread0(part, S);
+        if (tid == 0) partA[blockIdx.x] = d;
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        const double pa = grid_partials(partA);
+        if (tid == 0) S->fsc[0] = (pa != 0.0) ? cn / pa : 0.0;  // alpha, FP64
+        __syncthreads();
+        const R alpha = (R)S->fsc[0];
+        // x += alpha p;  c -= alpha a;  c_n' = ||c||^2
+        part = 0;
+        for (int it = gtid; it < items; it += nthr) {
+          const int k = it & (M - 1), j0 = (it >> logM) * E;
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            const size_t o = (size_t)(j0 + i) * M + k;
+            const C pv = G.Pv[o], av = G.Vv[o];
+            C xv = G.X[o], cv = G.Cv[o];
+            xv.x = fma(alpha, pv.x, xv.x);
+            xv.y = fma(alpha, pv.y, xv.y);
+            cv.x = fma(-alpha, av.x, cv.x);
+            cv.y = fma(-alpha, av.y, cv.y);
+            G.X[o] = xv;
+            G.Cv[o] = cv;
+            part = fma(cv.x, cv.x, fma(cv.y, cv.y, part));
+          }
+        }
+        d = block_sum_to_thread0(part, S);
+        if (tid == 0) partC[blockIdx.x] = d;
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        const double cn_new = grid_partials(partC);
+        if (tid == 0) {
+          S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;  // beta, FP64
+          if (!isfinite(cn_new)) S->isc[1] = 1;
+          if (cn_new <= stop_at) S->isc[4] = 1;
+          cn = cn_new;
+        }
+        __syncthreads();
+        const R beta = (R)S->fsc[1];
+        if (iter + 1 < io.iters) {
+          // p = c + beta p, and its extension
+          for (int it = gtid; it < items; it += nthr) {
+            const int k = it & (M - 1), j0 = (it >> logM) * E;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+              const size_t o = (size_t)(j0 + i) * M + k;
+              const C cv = G.Cv[o];
+              C pv = G.Pv[o];
+              pv.x = fma(beta, pv.x, cv.x);
+              pv.y = fma(beta, pv.y, cv.y);
+              G.Pv[o] = pv;
+              v[i] = pv;
+            }
+            write_ext<R, E, true>(G.extP, A, k, j0, v);
+          }
+          if (!grid_sync(G.bar, gen)) return fail(io);
+        }
+      }
+      if (S->isc[1]) st |= kStNonFinite;
+      if ((A.mode & kWriteX) && io.x_hat)
+        for (int it = gtid; it < items; it += nthr) {
+          const int k = it & (M - 1), j0 = (it >> logM) * E;
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            const size_t o = (size_t)(j0 + i) * M + k;
+            reinterpret_cast<C*>(io.x_hat)[o] = G.X[o];
+          }
+        }
+    }
+
+    // ------------------------------------------------ demapping
+    if ((A.mode & kDemap) && (io.llr || io.bits)) {
+      const C* xs = (A.mode & kLoadX) ? reinterpret_cast<const C*>(io.x_in) : G.X;
+      const R inv_lam = (R)1 / (R)io.lam;
+      const int bps = io.bps;
+      for (int q = gtid; q < MN; q += nthr) {
+        float2 l01, l23, l45;
+        const int hard = qam_llr_regs<R>(xs[q], bps, (R)io.pam_d, inv_lam, l01, l23, l45);
+        G.lab[q] = (uint8_t)(__brev((unsigned)hard) >> (32 - bps));
+        if (io.llr) {
+          float2* ol = reinterpret_cast<float2*>(io.llr + (size_t)q * bps);
+          ol[0] = l01;
+          if (bps > 2) ol[1] = l23;
+          if (bps > 4) ol[2] = l45;
+        }
+      }
+      if (io.bits) {
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        for (int g = gtid; g < MN / 8; g += nthr) {
+          const unsigned long long l8 = __ldcg(reinterpret_cast<const unsigned long long*>(G.lab) + g);
+          unsigned long long w = 0;
+#pragma unroll
+          for (int s8 = 0; s8 < 8; ++s8) w |= ((l8 >> (8 * s8)) & 0xffull) << (bps * s8);
+          uint8_t* o = io.bits + (size_t)g * bps;
+          for (int h = 0; h < bps; ++h) o[h] = (uint8_t)(w >> (8 * h));
+        }
+      }
+    }
+    // every CTA done with this frame's scratch before the next frame (or the status) moves on
+    if (!grid_sync(G.bar, gen)) return fail(io);
+    if (blockIdx.x == 0 && tid == 0 && io.status) *io.status = status_from_bits(st);
+  }
+}
+
+__host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max) {
+  size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
+  off += ((size_t)p_max * sizeof(PathRecT<float>) + sizeof(int) * 2 + 127) & ~size_t(127);
+  off += ((size_t)p_max * sizeof(RunRec) + 127) & ~size_t(127);
+  off += ((size_t)p_max * sizeof(PathRecT<float>) + 127) & ~size_t(127);
+  off += ((size_t)((p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);
+  off += (size_t)N * kGridDftCols * sizeof(float2);
+  off += (size_t)N * sizeof(float2);
+  return off;
+}
+
+}  // namespace zotfs

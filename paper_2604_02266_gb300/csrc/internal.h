@@ -32,6 +32,9 @@ struct zotfs_plan_s {
   size_t big_slot_bytes;
   int big_slots;
   size_t big_bytes;  // size of d_big (also the clustered large-frame kernel's slots)
+  // paper-scale grids: the grid receiver's scratch (one frame at a time)
+  char* d_grid;
+  size_t grid_bytes;
 };
 
 namespace zotfs {
@@ -104,6 +107,18 @@ cudaError_t big_cluster_max_active(const BigClusterCfg& cfg, int& clusters);
 // Clusters of one launch: the resident maximum, capped by `ctas_per_sm` CTAs per SM when it is
 // positive.
 int big_cluster_count(const BigClusterCfg& cfg, int max_active, int sm_count, int ctas_per_sm);
+
+// Paper-scale grid receiver (grid_variant.cu): one SISO frame at a time on the whole GPU, a
+// cooperative launch whose CTAs meet at grid barriers; frames with M > 256 or M N > 16384.
+constexpr size_t kGridMaxElems = (size_t)1 << 19;  // M N up to 524288 (16384 x 32)
+struct GridCfg {
+  int T, EQ, grid;
+  size_t smem;
+};
+bool grid_shape(int M, int N, int nrx, int ntx);
+cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, GridCfg& cfg);
+size_t grid_scratch_size(int M, int N, int p_max, int grid);
+cudaError_t grid_launch(const GridCfg& cfg, const FrameArgs& A, char* scratch, cudaStream_t stream);
 
 // Cluster receiver (cluster_variant.cu): one SISO frame on C CTAs of a thread-block cluster.
 struct ClusterCfg {

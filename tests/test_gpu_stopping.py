@@ -62,6 +62,7 @@ ROUTES = {  # name: (M, N, n_rx, n_tx, cluster, plain)
     "cluster_receiver": (64, 32, 1, 1, 2, False),
     "large_frame": (128, 64, 1, 1, 1, False),
     "clustered_large_frame": (64, 32, 4, 4, 2, False),
+    "paper_scale_grid": (1024, 32, 1, 1, 0, False),
 }
 
 
@@ -70,6 +71,8 @@ def test_stopping_test_vs_oracle(route):
     M, N, nrx, ntx, cluster, plain = ROUTES[route]
     Q = 16
     F = 3 if plain else (4 if nrx > 1 or M * N > 4096 else 12)
+    if M * N > 16384:
+        F = 3
     b = synth.fractional_batch(F, seed=9400 + M + nrx, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx,
                                snr_db=(0, 10, 20, 30))
     first = _run(_plan(M, N, nrx, ntx, Q, cluster), b, ITERS, F, plain=plain)
