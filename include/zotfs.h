@@ -124,9 +124,14 @@ typedef struct zotfs_paths {
 /* ---------------------------------------------------------------- plans ------------ */
 
 /* Create a plan for frames of M delay x N Doppler bins, n_rx x n_tx antennas and square
- * Gray QAM of order qam (4, 16 or 64).  Builds the root-of-unity tables (FP64 on the host,
- * stored FP32) and the plan's scratch for the plain form.  The only allocating calls are
- * the create calls.  *out is set to NULL on failure. */
+ * Gray QAM of order qam (4, 16 or 64).  M and N are powers of two, 16 <= M <= 16384,
+ * 8 <= N <= 64, n_rx, n_tx in [1, 4].  Frames with M <= 256 and M N <= 16384 run one per CTA
+ * (or per thread-block cluster); larger frames, up to the paper's (16384, 32) operating point
+ * (M N <= 524288, M >= 32), must be SISO, run one at a time on the whole GPU (a cooperative
+ * launch), take separate pilot frames and FP32 compute, and have no plain form
+ * (ZOTFS_EUNSUPPORTED).  Builds the root-of-unity tables (FP64 on the host, stored FP32)
+ * and the plan's scratch.  The only allocating calls are the create calls.  *out is set to
+ * NULL on failure. */
 zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pulse, int qam,
                                zotfs_plan* out);
 zotfs_status zotfs_plan_set_options(zotfs_plan plan, const zotfs_options* opts);
