@@ -770,6 +770,62 @@ def impl_mimo(args):
     return 0
 
 
+# ------------------------------------------------------------- pilot-reuse workload
+
+def impl_packets(args):
+    """Pilot reuse: packets of one pilot frame and D data frames through the same channel (the
+    headline 64x32 16-QAM shape); a step is the read-off of the packets' pilots (zotfs_estimate)
+    and the fused data-frame receiver over all data frames with their packet's lists
+    (zotfs_rx_lists)."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Plan
+    D = args.packet_data
+    P = FRAMES // D
+    b = synth.packet_batch(P, D, SEED + 77, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    yp, yd = torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev)
+    nv, th = torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev)
+    ids = torch.from_numpy(b["path_ids"]).to(dev)
+    paths = plan.new_paths(P)
+    F = P * D
+    _, x, L, B, st = plan._rx_outputs(F, dev, False, False, False)
+
+    def step():
+        plan.estimate(yp, th, P, paths=paths)
+        plan.rx_lists(yd, paths, nv, ITERS, F, path_ids=ids, n_sets=P, out=(x, L, B, st))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    steps = args.steps or 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s_ = st.cpu().numpy()
+    line = {"metric": "equalized Zak-OTFS data frames/s with pilot reuse, 64x32 16-QAM", "value": F / ms * 1e3,
+            "unit": "frames/s", "n_gpus": 1, "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{P} packets x (1 pilot frame + {D} data frames through the same 6-path fractional "
+                                   "channel), M=64, N=32, 16-QAM, SNR 0..30 dB per packet, 10 CG iterations; a step "
+                                   "is the pilots' read-off + the data frames' receiver", "packets": P,
+                       "data_per_pilot": D},
+            "mbit_s": F * M * N * 4 / ms / 1e3, "status_ok": float((s_ == 0).mean()), "gpu_launches_per_step": 3}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------- paper-scale workload
 
 PAPER_M, PAPER_N = 16384, 32
@@ -909,13 +965,15 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=24, help="oracle sample per host core for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=4, help="oracle frames per host core per step (--impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper", "packets"],
                     help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
                          "mixed: the uneven FP16/BF16 batch under CUDA graphs; mimo: 4x4 128x64 64-QAM frames; "
-                         "latency: one frame per call; paper: one 16384x32 packet per call on the grid receiver")
+                         "latency: one frame per call; paper: one 16384x32 packet per call on the grid receiver; "
+                         "packets: one pilot frame per D data frames (pilot reuse)")
     ap.add_argument("--mimo-steps", type=int, default=5, help="mimo: timed steps")
     ap.add_argument("--latency-frames", type=int, default=200, help="latency: frames per shape")
     ap.add_argument("--paper-calls", type=int, default=200, help="paper: timed one-packet calls")
+    ap.add_argument("--packet-data", type=int, default=8, help="packets: data frames per pilot frame")
     ap.add_argument("--paper-pool", type=int, default=8, help="paper: synthetic packets cycled through")
     ap.add_argument("--mixed-steps", type=int, default=20, help="mixed: timed steps per storage type")
     ap.add_argument("--tune-frames", type=int, default=64, help="mixed: frames per shape group the autotuner times")
@@ -945,6 +1003,8 @@ def main():
         return impl_mimo(args)
     if args.workload == "paper":
         return impl_paper(args)
+    if args.workload == "packets":
+        return impl_packets(args)
     if args.workload == "latency":
         return impl_latency(args)
     return impl_zotfs(args)

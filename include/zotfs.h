@@ -211,6 +211,20 @@ zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const z
 zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise_var, float* llr,
                          uint8_t* bits, int n_frames, zotfs_stream stream);
 
+/* Data frames equalised and demapped with path lists estimated earlier (pilot reuse: one
+ * pilot frame's lists serve the data frames that follow it within the channel's coherence
+ * time, Sec. III-B "Channel Estimation").  Data frame f uses list set path_ids[f] of the
+ * n_sets sets in `paths` (dev int32 [n_frames]; NULL: set f, and n_sets >= n_frames); a
+ * frame whose id is outside [0, n_sets) gets status ZOTFS_EINVAL.  Fused like zotfs_rx: data
+ * Zak transform -> CGA (`iters`, lambda = noise_var[f]) -> demapping, one frame per CTA
+ * (or cluster, or the whole GPU for paper-scale grids).
+ * y_data_td: dev TD [n_frames][n_rx][MN] in the plan's in_dtype.  x_hat, llr may be NULL;
+ * bits: dev uint8 [n_frames][n_tx][MN*bps/8]; status: dev int32 [n_frames] (required). */
+zotfs_status zotfs_rx_lists(zotfs_plan plan, const void* y_data_td, const zotfs_paths* paths,
+                            const int32_t* path_ids, int n_sets, const float* noise_var, int iters,
+                            float* x_hat, float* llr, uint8_t* bits, int32_t* status, int n_frames,
+                            zotfs_stream stream);
+
 /* The whole receiver fused: per frame in one persistent kernel whose CTAs pull
  * frames from a device work counter: pilot Zak transforms and read-off -> path lists in
  * shared memory -> data Zak transform -> CGA -> demapping.  HBM traffic is the TD

@@ -213,6 +213,21 @@ class Plan:
                    paths.c if paths is not None else None, _p(x), _p(L), _p(B), _p(st), n_frames, _s(stream)))
         return {"paths": paths, "x_hat": x, "llr": L, "bits": B, "status": st}
 
+    def rx_lists(self, y_data_td, paths, noise_var, iters, n_frames, path_ids=None, n_sets=None, want_x=False,
+                 want_llr=False, out=None, stream=None):
+        """Data frames through Zak transform, CGA and demapping with lists estimated earlier
+        (zotfs_rx_lists): frame f uses list set ``path_ids[f]`` of ``paths`` (pilot reuse)."""
+        if out is None:
+            _, x, L, B, st = self._rx_outputs(n_frames, y_data_td.device, False, want_x, want_llr)
+        else:
+            x, L, B, st = out
+        if n_sets is None:
+            n_sets = int(paths.count.numel() // (self.n_rx * self.n_tx))
+        _need_cuda(y_data_td, noise_var, path_ids, x, L, B, st)
+        Z.check(Z.zotfs_rx_lists(self._h, _p(y_data_td), paths.c, _p(path_ids), n_sets, _p(noise_var), iters, _p(x),
+                                 _p(L), _p(B), _p(st), n_frames, _s(stream)))
+        return {"x_hat": x, "llr": L, "bits": B, "status": st}
+
 
 class Batch:
     """An uneven batch (zotfs_batch_create / zotfs_rx_batch).  ``frames`` is a list of dicts

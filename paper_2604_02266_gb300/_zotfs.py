@@ -116,6 +116,7 @@ SIGNATURES = {
     "zotfs_demap": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "zotfs_rx": (_I, [_P, _P, _P, _P, _P, _I, C.POINTER(zotfs_paths), _P, _P, _P, _P, _I, _P]),
     "zotfs_rx_plain": (_I, [_P, _P, _P, _P, _P, _I, C.POINTER(zotfs_paths), _P, _P, _P, _P, _I, _P]),
+    "zotfs_rx_lists": (_I, [_P, _P, C.POINTER(zotfs_paths), _P, _I, _P, _I, _P, _P, _P, _P, _I, _P]),
     "zotfs_equalize_static": (_I, [_I, _I, _I, _I, C.POINTER(zotfs_paths), _P, _P, _I, _P, _P, _I, _P]),
     "zotfs_batch_create": (_I, [C.POINTER(zotfs_frame_desc), _I, C.POINTER(zotfs_batch_opts), C.POINTER(_P)]),
     "zotfs_rx_batch": (_I, [_P, _P, _P]),

@@ -689,6 +689,39 @@ zotfs_status zotfs_rx(zotfs_plan plan, const void* y_pilot_td, const void* y_dat
   return launch_any(plan, plan->nrx, plan->ntx, A, stream);
 }
 
+zotfs_status zotfs_rx_lists(zotfs_plan plan, const void* y_data_td, const zotfs_paths* paths,
+                            const int32_t* path_ids, int n_sets, const float* noise_var, int iters,
+                            float* x_hat, float* llr, uint8_t* bits, int32_t* status, int n_frames,
+                            zotfs_stream stream) {
+  g_launches = 0;
+  if (!plan) return inval("plan is NULL");
+  if (n_frames < 0 || iters < 0) return inval("n_frames and iters must be >= 0");
+  zotfs_status s = check_paths(plan, paths, false);
+  if (s) return s;
+  if (n_sets < 1 || (!path_ids && n_sets < n_frames)) return inval("n_sets must cover the frames' list sets");
+  if (n_frames == 0) return ZOTFS_OK;
+  if (!y_data_td || !noise_var || !status) return inval("NULL buffer");
+  if (!aligned16(y_data_td)) return inval("TD frames must be 16-byte aligned");
+  FrameArgs A;
+  fill_plan_args(plan, A);
+  A.mode = kLoadPaths | kCG | kDemap | (x_hat ? kWriteX : 0);
+  A.n_frames = n_frames;
+  A.y_data = y_data_td;
+  A.noise_var = noise_var;
+  A.iters = iters;
+  A.x_hat = x_hat;
+  A.llr = llr;
+  A.bits = bits;
+  A.status = status;
+  A.pcount = paths->count;
+  A.pdk = paths->dk;
+  A.pdl = paths->dl;
+  A.ph = paths->h;
+  A.path_ids = path_ids;
+  A.n_path_sets = n_sets;
+  return launch_any(plan, plan->nrx, plan->ntx, A, stream);
+}
+
 zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,
                             const float* theta, int iters, const zotfs_paths* paths, float* x_hat, float* llr,
                             uint8_t* bits, int32_t* status, int n_frames, zotfs_stream stream) {

@@ -90,7 +90,11 @@ struct FrameArgs {
   const void* v_in;
   int adjoint;
   const void* x_in;
-  // path lists in global memory: read with kLoadPaths, written with kWritePaths
+  // path lists in global memory: read with kLoadPaths, written with kWritePaths.  With
+  // path_ids (kLoadPaths), frame f reads list set path_ids[f] of n_path_sets (pilot reuse:
+  // several data frames equalised with the lists of one pilot frame); else set f.
+  const int32_t* path_ids;
+  int n_path_sets;
   int32_t* pcount;
   int32_t* pstatus;
   int16_t* pdk;
@@ -136,6 +140,7 @@ struct PathIO {
   int16_t* dl;
   void* h;
   int tap_dtype;
+  int invalid;      // the frame named a list set outside the call's: load nothing, flag it
 };
 
 // Everything one frame reads and writes, resolved at the start of the frame.
@@ -712,6 +717,11 @@ __device__ __forceinline__ int load_paths(const FrameArgs& A, const PathIO& gin,
                                           int& bad) {
   using C = typename Cx<R>::C;
   const int M = A.M, N = A.N, MN = M * N;
+  if (gin.invalid) {
+    bad = 1;
+    __syncthreads();
+    return 0;
+  }
   int P = gin.count[li];
   bad = 0;
   if (P < 0 || P > A.p_max) {

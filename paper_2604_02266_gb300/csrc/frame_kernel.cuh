@@ -64,6 +64,7 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
     io.paths.dl = d.path_dl;
     io.paths.h = d.path_h;
     io.paths.tap_dtype = ZOTFS_C64;
+    io.paths.invalid = 0;
     io.status = A.status ? A.status + A.frame_ids[f] : nullptr;
     return io;
   }
@@ -86,11 +87,20 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
   io.llr = A.llr ? A.llr + (size_t)f * A.ntx * MN * A.bps : nullptr;
   io.bits = A.bits ? A.bits + (size_t)f * A.ntx * MN * A.bps / 8 : nullptr;
   io.u_out = A.u_out ? static_cast<char*>(A.u_out) + (size_t)f * nout * MN * csz : nullptr;
-  io.paths.count = A.pcount ? A.pcount + (size_t)f * nl : nullptr;
-  io.paths.status = A.pstatus ? A.pstatus + (size_t)f * nl : nullptr;
-  io.paths.dk = A.pdk ? A.pdk + (size_t)f * nl * A.p_max : nullptr;
-  io.paths.dl = A.pdl ? A.pdl + (size_t)f * nl * A.p_max : nullptr;
-  io.paths.h = A.ph ? static_cast<char*>(A.ph) + (size_t)f * nl * A.p_max * dtype_bytes(A.tap_dtype) : nullptr;
+  int ls = f;  // the frame's list set
+  io.paths.invalid = 0;
+  if (A.path_ids) {
+    ls = A.path_ids[f];
+    if (ls < 0 || ls >= A.n_path_sets) {
+      io.paths.invalid = 1;
+      ls = 0;
+    }
+  }
+  io.paths.count = A.pcount ? A.pcount + (size_t)ls * nl : nullptr;
+  io.paths.status = A.pstatus ? A.pstatus + (size_t)ls * nl : nullptr;
+  io.paths.dk = A.pdk ? A.pdk + (size_t)ls * nl * A.p_max : nullptr;
+  io.paths.dl = A.pdl ? A.pdl + (size_t)ls * nl * A.p_max : nullptr;
+  io.paths.h = A.ph ? static_cast<char*>(A.ph) + (size_t)ls * nl * A.p_max * dtype_bytes(A.tap_dtype) : nullptr;
   io.paths.tap_dtype = A.tap_dtype;
   io.status = A.status ? A.status + f : nullptr;
   return io;

@@ -28,7 +28,7 @@ sigma / a_pilot; the threshold "3 sigma" is theta = 3 sigma / a_pilot.
 import numpy as np
 
 __all__ = ["rng", "qam_map", "idzt", "channel_integer", "channel_fractional", "awgn",
-           "integer_embedded_frame", "fractional_batch", "uneven_batch"]
+           "integer_embedded_frame", "fractional_batch", "packet_batch", "uneven_batch"]
 
 
 def rng(seed):
@@ -211,6 +211,69 @@ def fractional_batch(n_frames, seed, M=64, N=32, Q=16, n_rx=1, n_tx=1, n_paths=6
         "noise_var": noise_var.astype(np.float32),
         "theta": (theta_sigmas * np.sqrt(noise_var) / a_pilot).astype(np.float32),
         "bits": bits, "snr_db": snrs, "channels": chan,
+    }
+
+
+def packet_batch(n_packets, data_per_pilot, seed, M=64, N=32, Q=16, n_rx=1, n_tx=1, n_paths=6,
+                 snr_db=tuple(range(31)), delay_max=4.0, doppler_max=3.0, dtype=np.complex64,
+                 theta_sigmas=3.0):
+    """Packets of one pilot frame (per tx antenna) and ``data_per_pilot`` data frames through
+    the same fractional channel (block-static within the coherence time), each data frame with
+    its own bits and noise at the packet's SNR.  Channel recipe as ``fractional_batch``.
+
+    Returns y_pilot_td [P, n_tx, n_rx, MN], y_data_td [P D, n_rx, MN], noise_var [P D],
+    theta [P], bits [P D, n_tx, MN*bps], path_ids [P D] (int32: the packet of each data frame).
+    Packet p uses the generator seeded with seed + p.
+    """
+    MN = M * N
+    bps = int(round(np.log2(Q)))
+    K0, L0 = M // 2, N // 2
+    a_pilot = np.sqrt(MN)
+    D = data_per_pilot
+    yp = np.zeros((n_packets, n_tx, n_rx, MN), np.complex128)
+    yd = np.zeros((n_packets * D, n_rx, MN), np.complex128)
+    noise_var = np.zeros(n_packets * D)
+    theta = np.zeros(n_packets)
+    bits = np.zeros((n_packets * D, n_tx, MN * bps), np.uint8)
+    Xp = np.zeros((M, N), np.complex128)
+    Xp[K0, L0] = a_pilot
+    xp = idzt(Xp)
+    for pk in range(n_packets):
+        g = rng(seed + pk)
+        snr = float(g.choice(np.asarray(snr_db, float)))
+        sigma2 = 10.0 ** (-snr / 10.0)
+        pairs = {}
+        for r in range(n_rx):
+            for t in range(n_tx):
+                tau = g.uniform(0.0, delay_max, size=n_paths)
+                nu = g.uniform(-doppler_max, doppler_max, size=n_paths)
+                pw = np.exp(-tau)
+                pw = pw / pw.sum()
+                h = np.sqrt(pw / 2.0) * (g.standard_normal(n_paths) + 1j * g.standard_normal(n_paths))
+                pairs[(r, t)] = (h, tau, nu)
+        for t in range(n_tx):
+            for r in range(n_rx):
+                h, tau, nu = pairs[(r, t)]
+                yp[pk, t, r] = channel_fractional(xp, h, tau, nu) + awgn(MN, sigma2, g)
+        theta[pk] = theta_sigmas * np.sqrt(sigma2) / a_pilot
+        for d in range(D):
+            f = pk * D + d
+            b = g.integers(0, 2, size=(n_tx, MN * bps)).astype(np.uint8)
+            xs = [idzt(qam_map(b[t], Q).reshape((M, N), order="F")) for t in range(n_tx)]
+            for r in range(n_rx):
+                acc = np.zeros(MN, np.complex128)
+                for t in range(n_tx):
+                    h, tau, nu = pairs[(r, t)]
+                    acc += channel_fractional(xs[t], h, tau, nu)
+                yd[f, r] = acc + awgn(MN, sigma2, g)
+            noise_var[f] = sigma2
+            bits[f] = b
+    return {
+        "M": M, "N": N, "Q": Q, "n_rx": n_rx, "n_tx": n_tx, "K0": K0, "L0": L0,
+        "a_pilot": float(a_pilot),
+        "y_pilot_td": yp.astype(dtype), "y_data_td": yd.astype(dtype),
+        "noise_var": noise_var.astype(np.float32), "theta": theta.astype(np.float32),
+        "bits": bits, "path_ids": (np.arange(n_packets * D) // D).astype(np.int32),
     }
 
 
