@@ -186,6 +186,7 @@ zotfs_equalize = _mk("zotfs_equalize")
 zotfs_demap = _mk("zotfs_demap")
 zotfs_rx = _mk("zotfs_rx")
 zotfs_rx_plain = _mk("zotfs_rx_plain")
+zotfs_rx_lists = _mk("zotfs_rx_lists")
 zotfs_equalize_static = _mk("zotfs_equalize_static")
 zotfs_batch_create = _mk("zotfs_batch_create")
 zotfs_rx_batch = _mk("zotfs_rx_batch")
