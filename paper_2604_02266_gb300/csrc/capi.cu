@@ -98,8 +98,9 @@ namespace {
 // One CTA of 1024 threads: keys are 31-bit (theta's bit pattern, or 2^30 - total paths),
 // bucketed into 256 ranges between the smallest and largest key, counted, scanned and
 // scattered (ascending key = decreasing expected work).
-__global__ void __launch_bounds__(1024) frame_order_kernel(const float* theta, const int32_t* count, int nlists,
-                                                           int n, int* order) {
+__global__ void __launch_bounds__(1024) frame_order_kernel(const float* theta, const int32_t* count,
+                                                           const int32_t* ids, int n_sets, int nlists, int n,
+                                                           int* order) {
   __shared__ unsigned lo_s, hi_s;
   __shared__ int hist[256];
   auto key = [&](int i) -> unsigned {
@@ -108,7 +109,9 @@ __global__ void __launch_bounds__(1024) frame_order_kernel(const float* theta, c
       return (t > 0.f && isfinite(t)) ? __float_as_uint(t) : 0x7f800000u;
     }
     int tot = 0;
-    for (int l = 0; l < nlists; ++l) tot += count[(size_t)i * nlists + l];
+    const int s = ids ? ids[i] : i;  // the frame's list set
+    if (s >= 0 && s < n_sets)
+      for (int l = 0; l < nlists; ++l) tot += count[(size_t)s * nlists + l];
     return (1u << 30) - (unsigned)min(max(tot, 0), 1 << 29);
   };
   if (threadIdx.x == 0) {
@@ -145,9 +148,9 @@ __global__ void __launch_bounds__(1024) frame_order_kernel(const float* theta, c
 
 }  // namespace
 
-cudaError_t launch_frame_order(const float* theta, const int32_t* count, int nlists, int n, int* order,
-                               cudaStream_t stream) {
-  frame_order_kernel<<<1, 1024, 0, stream>>>(theta, count, nlists, n, order);
+cudaError_t launch_frame_order(const float* theta, const int32_t* count, const int32_t* ids, int n_sets, int nlists,
+                               int n, int* order, cudaStream_t stream) {
+  frame_order_kernel<<<1, 1024, 0, stream>>>(theta, count, ids, n_sets, nlists, n, order);
   return cudaGetLastError();
 }
 
@@ -159,8 +162,9 @@ static const int* maybe_order(zotfs_plan_s* plan, const FrameArgs& A, int reside
   const bool by_count = !(A.mode & kEstimate) && (A.mode & kLoadPaths) && A.pcount;
   if (!by_theta && !by_count) return nullptr;
   int* order = plan->d_order + (size_t)(plan->order_next++ % kOrderSlots) * kOrderCap;
-  if (launch_frame_order(by_theta ? A.theta : nullptr, by_count ? A.pcount : nullptr, A.nrx * A.ntx, A.n_frames,
-                         order, stream) != cudaSuccess)
+  if (launch_frame_order(by_theta ? A.theta : nullptr, by_count ? A.pcount : nullptr, A.path_ids,
+                         A.path_ids ? A.n_path_sets : A.n_frames, A.nrx * A.ntx, A.n_frames, order,
+                         stream) != cudaSuccess)
     return nullptr;  // run in index order
   ++g_launches;
   return order;

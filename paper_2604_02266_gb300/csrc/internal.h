@@ -54,10 +54,12 @@ constexpr int kOrderCap = 16384, kOrderSlots = 4;
 
 // Launch a kernel that writes into `order` a permutation of [0, n) listing frames by
 // decreasing expected work: by increasing threshold theta (a lower threshold keeps more
-// taps) when `theta` is given, else by decreasing total path count over the frame's
-// `nlists` lists in `count`.  Frames with equal keys keep no particular order.
-cudaError_t launch_frame_order(const float* theta, const int32_t* count, int nlists, int n, int* order,
-                               cudaStream_t stream);
+// taps) when `theta` is given, else by decreasing total path count over the `nlists` lists
+// of the frame's list set in `count` (set ids[i] of n_sets when ids is given, else set i;
+// a set outside [0, n_sets) counts as empty).  Frames with equal keys keep no particular
+// order.
+cudaError_t launch_frame_order(const float* theta, const int32_t* count, const int32_t* ids, int n_sets, int nlists,
+                               int n, int* order, cudaStream_t stream);
 
 // Fill the constant parts of FrameArgs from a plan.
 void fill_plan_args(const zotfs_plan_s* plan, FrameArgs& A);
