@@ -212,8 +212,8 @@ zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise
                          uint8_t* bits, int n_frames, zotfs_stream stream);
 
 /* Data frames equalised and demapped with path lists estimated earlier (pilot reuse: one
- * pilot frame's lists serve the data frames that follow it within the channel's coherence
- * time, Sec. III-B "Channel Estimation").  Data frame f uses list set path_ids[f] of the
+ * pilot frame's lists serve the data frames of its packet, which Sec. III-B sizes by the
+ * channel coherence time).  Data frame f uses list set path_ids[f] of the
  * n_sets sets in `paths` (dev int32 [n_frames]; NULL: set f, and n_sets >= n_frames); a
  * frame whose id is outside [0, n_sets) gets status ZOTFS_EINVAL.  Fused like zotfs_rx: data
  * Zak transform -> CGA (`iters`, lambda = noise_var[f]) -> demapping, one frame per CTA
