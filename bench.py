@@ -826,6 +826,49 @@ def impl_packets(args):
     return 0
 
 
+# ------------------------------------------------------------- iteration-budget workload
+
+def impl_iterations(args):
+    """The BER-driven iteration budget (Sec. IV-C, Eq. ber_convergence) on Veh-A frames: BER
+    after 1 .. 30 CG iterations of the fused receiver per (grid, SNR), the convergence
+    iteration and the lowest-BER iteration of each curve, and the budget over all of them."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Plan
+    from paper_2604_02266_gb300.iterations import ber_curve, convergence_iteration, iteration_budget
+    rows, curves = [], []
+    t0 = time.time()
+    for (m, n) in ((128, 32), (32, 32)):
+        plan = Plan(m, n, 1, 1, 16)
+        for snr in range(0, 31, 5):
+            b = synth.veh_a_batch(args.iter_frames, SEED + 31 * m + snr, M=m, N=n, Q=16, snr_db=(snr,))
+            c = ber_curve(plan, torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev),
+                          torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev), b["bits"],
+                          args.iter_max)
+            curves.append(c)
+            rows.append({"M": m, "N": n, "snr_db": snr, "converged_at": convergence_iteration(c),
+                         "lowest_ber_at": int(np.argmin(c)) + 1, "ber_converged": c[convergence_iteration(c) - 1],
+                         "ber_lowest": float(min(c)), "ber_at_10": c[9] if len(c) >= 10 else None})
+    budget = iteration_budget(curves)
+    line = {"metric": "BER-driven CG iteration budget (Eq. ber_convergence), Veh-A 16-QAM", "value": budget,
+            "unit": "iterations", "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.iter_frames} Veh-A frames (Table vehAProf delays and powers, nu_max 100 Hz, "
+                                   "delta_f 30 kHz) per (grid, SNR), grids 128x32 and 32x32, SNR 0..30 dB step 5, "
+                                   f"1..{args.iter_max} CG iterations, eta 1e-2, zeta 1e-12",
+                       "frames": args.iter_frames, "max_iters": args.iter_max},
+            "paper_budget": 10, "rows": rows, "wall_s": time.time() - t0}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------- paper-scale workload
 
 PAPER_M, PAPER_N = 16384, 32
@@ -965,15 +1008,18 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=24, help="oracle sample per host core for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=4, help="oracle frames per host core per step (--impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper", "packets"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper", "packets", "iterations"],
                     help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
                          "mixed: the uneven FP16/BF16 batch under CUDA graphs; mimo: 4x4 128x64 64-QAM frames; "
                          "latency: one frame per call; paper: one 16384x32 packet per call on the grid receiver; "
-                         "packets: one pilot frame per D data frames (pilot reuse)")
+                         "packets: one pilot frame per D data frames (pilot reuse); "
+                         "iterations: the BER-driven CG iteration budget on Veh-A frames")
     ap.add_argument("--mimo-steps", type=int, default=5, help="mimo: timed steps")
     ap.add_argument("--latency-frames", type=int, default=200, help="latency: frames per shape")
     ap.add_argument("--paper-calls", type=int, default=200, help="paper: timed one-packet calls")
     ap.add_argument("--packet-data", type=int, default=8, help="packets: data frames per pilot frame")
+    ap.add_argument("--iter-frames", type=int, default=32, help="iterations: Veh-A frames per (grid, SNR)")
+    ap.add_argument("--iter-max", type=int, default=30, help="iterations: CG iterations profiled")
     ap.add_argument("--paper-pool", type=int, default=8, help="paper: synthetic packets cycled through")
     ap.add_argument("--mixed-steps", type=int, default=20, help="mixed: timed steps per storage type")
     ap.add_argument("--tune-frames", type=int, default=64, help="mixed: frames per shape group the autotuner times")
@@ -1005,6 +1051,8 @@ def main():
         return impl_paper(args)
     if args.workload == "packets":
         return impl_packets(args)
+    if args.workload == "iterations":
+        return impl_iterations(args)
     if args.workload == "latency":
         return impl_latency(args)
     return impl_zotfs(args)

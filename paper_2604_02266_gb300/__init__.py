@@ -428,3 +428,5 @@ class Server:
         ptr = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
         Z.check(Z.zotfs_server_read(self._h, tag, ptr(bits), ptr(L), ptr(pc), ptr(dk), ptr(dl), ptr(h)))
         return {"bits": bits, "llr": L, "count": pc, "dk": dk, "dl": dl, "h": h}
+
+from . import iterations  # noqa: E402,F401  (BER-driven iteration budget)

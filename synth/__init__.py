@@ -28,7 +28,13 @@ sigma / a_pilot; the threshold "3 sigma" is theta = 3 sigma / a_pilot.
 import numpy as np
 
 __all__ = ["rng", "qam_map", "idzt", "channel_integer", "channel_fractional", "awgn",
-           "integer_embedded_frame", "fractional_batch", "packet_batch", "uneven_batch"]
+           "integer_embedded_frame", "fractional_batch", "packet_batch", "veh_a_batch", "uneven_batch",
+           "VEH_A_DELAYS_US", "VEH_A_POWERS_DB"]
+
+# The Veh-A power-delay profile of Sec. V "Channel model" (Table vehAProf): excess delays in
+# microseconds and relative powers in dB of its six paths.
+VEH_A_DELAYS_US = (0.00, 0.31, 0.71, 1.09, 1.73, 2.51)
+VEH_A_POWERS_DB = (0.0, -1.0, -9.0, -10.0, -15.0, -20.0)
 
 
 def rng(seed):
@@ -274,6 +280,47 @@ def packet_batch(n_packets, data_per_pilot, seed, M=64, N=32, Q=16, n_rx=1, n_tx
         "y_pilot_td": yp.astype(dtype), "y_data_td": yd.astype(dtype),
         "noise_var": noise_var.astype(np.float32), "theta": theta.astype(np.float32),
         "bits": bits, "path_ids": (np.arange(n_packets * D) // D).astype(np.int32),
+    }
+
+
+def veh_a_batch(n_frames, seed, M=128, N=32, Q=16, snr_db=(20,), nu_max_hz=100.0, delta_f_hz=30e3,
+                dtype=np.complex64, theta_sigmas=3.0):
+    """SISO frames (separate pilot frame + data frame) through the Veh-A channel of Sec. V:
+    the six paths of Table vehAProf (delays in bins: tau_us 1e-6 M delta_f; powers normalised to
+    unit total, CN(0, power) gains), Doppler nu_p = nu_max cos(2 pi U_p), U_p ~ U(0, 1), in bins
+    of delta_f / N; both fractional.  SNR per frame from ``snr_db``.  Same return layout as
+    ``fractional_batch``.  Frame f uses the generator seeded with seed + f."""
+    MN = M * N
+    bps = int(round(np.log2(Q)))
+    K0, L0 = M // 2, N // 2
+    a_pilot = np.sqrt(MN)
+    tau = np.asarray(VEH_A_DELAYS_US) * 1e-6 * M * delta_f_hz
+    pw = 10.0 ** (np.asarray(VEH_A_POWERS_DB) / 10.0)
+    pw = pw / pw.sum()
+    yp = np.zeros((n_frames, 1, 1, MN), np.complex128)
+    yd = np.zeros((n_frames, 1, MN), np.complex128)
+    noise_var = np.zeros(n_frames)
+    bits = np.zeros((n_frames, 1, MN * bps), np.uint8)
+    Xp = np.zeros((M, N), np.complex128)
+    Xp[K0, L0] = a_pilot
+    xp = idzt(Xp)
+    for f in range(n_frames):
+        g = rng(seed + f)
+        snr = float(g.choice(np.asarray(snr_db, float)))
+        sigma2 = 10.0 ** (-snr / 10.0)
+        b = g.integers(0, 2, size=(1, MN * bps)).astype(np.uint8)
+        x = idzt(qam_map(b[0], Q).reshape((M, N), order="F"))
+        h = np.sqrt(pw / 2.0) * (g.standard_normal(6) + 1j * g.standard_normal(6))
+        nu = nu_max_hz * np.cos(2.0 * np.pi * g.uniform(0.0, 1.0, size=6)) / (delta_f_hz / N)
+        yp[f, 0, 0] = channel_fractional(xp, h, tau, nu) + awgn(MN, sigma2, g)
+        yd[f, 0] = channel_fractional(x, h, tau, nu) + awgn(MN, sigma2, g)
+        noise_var[f] = sigma2
+        bits[f] = b
+    return {
+        "M": M, "N": N, "Q": Q, "n_rx": 1, "n_tx": 1, "K0": K0, "L0": L0, "a_pilot": float(a_pilot),
+        "y_pilot_td": yp.astype(dtype), "y_data_td": yd.astype(dtype),
+        "noise_var": noise_var.astype(np.float32),
+        "theta": (theta_sigmas * np.sqrt(noise_var) / a_pilot).astype(np.float32), "bits": bits,
     }
 
 
