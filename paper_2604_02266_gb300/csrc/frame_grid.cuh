@@ -11,8 +11,6 @@
 // loaded lists), FP32.
 #pragma once
 
-#include <type_traits>
-
 #include "frame_kernel.cuh"
 
 namespace zotfs {
@@ -21,11 +19,6 @@ constexpr int kGridThreads = 256;
 constexpr int kGridE = 8;         // rows per work item: column k, rows j0 .. j0 + 7
 constexpr int kGridDftCols = 32;  // delay columns per Zak-transform tile
 constexpr uint32_t kGridMaxPolls = 1u << 22;
-// Tiled gathers: a CTA block is kGridTileCols = 2048 / N delay columns x all N rows (one item
-// per thread); its slice of the extension (plus the delay span of the frame's paths, up to
-// kGridSpanMax columns) and of the twiddle table are staged in shared memory.
-constexpr int kGridSpanMax = 64;
-__host__ __device__ __forceinline__ int grid_tile_cols(int N) { return 2048 / N; }
 
 constexpr int kGridMaxCtas = 1024;
 
@@ -201,56 +194,6 @@ __device__ __forceinline__ void grid_prefix(const int* counts, SharedHdr* S) {
   __syncthreads();
 }
 
-// One run of L paths for output rows j0 .. j0 + 7 of this thread's column, from the staged
-// extension tile xt (column-major, stride CS; tile column cb + s holds the extension column
-// of delay offset s from k) with the coefficient formed from the staged twiddle rows
-// (tabt[(dl + N/2) ts + kk] = Tab[dl][k]): the tile form of apply_run without coefficient
-// tables.
-template <int L, bool kFwd>
-__device__ __forceinline__ void grid_run(const float2* xt, int cb, const float2* tabt, int ts, int kk,
-                                         const PathRecT<float>* pl, const RunRec& rr, int N, int CS, int j0,
-                                         float2 (&accA)[kGridE], float2 (&accB)[kGridE]) {
-  constexpr int E = kGridE;
-  const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
-  const float2* a = xt + (size_t)(cb + (kFwd ? -rr.dk : rr.dk)) * CS + row0;
-  float2 W[L + E - 1];
-#pragma unroll
-  for (int w = 0; w < L + E - 1; ++w) W[w] = a[w];
-#pragma unroll
-  for (int m = 0; m < L; ++m) {
-    const PathRecT<float> rec = pl[rr.start + m];
-    const float2 t = tabt[(rr.dl0 + m + (N >> 1)) * ts + kk];
-    const float2 D = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
-    const float2 DX = make_float2(D.x, D.x), DY = make_float2(D.y, D.y);
-#pragma unroll
-    for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, W[(kFwd ? L - 1 - m : m) + i]);
-  }
-}
-
-// (H p) or (H^H u) at rows j0 .. j0 + 7 of one column from the staged tiles (SISO): the runs
-// of the list, longest first, as gather_runs does over a whole extension.
-template <bool kFwd>
-__device__ __forceinline__ void grid_gather(const float2* xt, int cb, const float2* tabt, int ts, int kk,
-                                            const PathRecT<float>* paths, const RunRec* runs, const int* nruns,
-                                            int N, int CS, int j0, float2 (&out)[kGridE]) {
-  constexpr int E = kGridE;
-  float2 accA[E], accB[E];
-#pragma unroll
-  for (int i = 0; i < E; ++i) accA[i] = accB[i] = make_float2(0.f, 0.f);
-  const int packed = nruns[0];
-  const int n4 = packed & 127, n3 = (packed >> 7) & 127, n2 = (packed >> 14) & 255, n1 = (packed >> 22) & 511;
-  int q = 0;
-  for (const int e = n4; q < e; ++q) grid_run<4, kFwd>(xt, cb, tabt, ts, kk, paths, runs[q], N, CS, j0, accA, accB);
-  for (const int e = n4 + n3; q < e; ++q)
-    grid_run<3, kFwd>(xt, cb, tabt, ts, kk, paths, runs[q], N, CS, j0, accA, accB);
-  for (const int e = n4 + n3 + n2; q < e; ++q)
-    grid_run<2, kFwd>(xt, cb, tabt, ts, kk, paths, runs[q], N, CS, j0, accA, accB);
-  for (const int e = n4 + n3 + n2 + n1; q < e; ++q)
-    grid_run<1, kFwd>(xt, cb, tabt, ts, kk, paths, runs[q], N, CS, j0, accA, accB);
-#pragma unroll
-  for (int i = 0; i < E; ++i) out[i] = make_float2(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
-}
-
 template <int EQ>
 __global__ void __launch_bounds__(kGridThreads, 2)
     grid_kernel(const __grid_constant__ FrameArgs A, GridScratch G) {
@@ -274,12 +217,6 @@ __global__ void __launch_bounds__(kGridThreads, 2)
   C* tile = reinterpret_cast<C*>(smem + off);
   off += (size_t)A.N * kGridDftCols * sizeof(C);
   C* wn = reinterpret_cast<C*>(smem + off);
-  off += (((size_t)A.N * sizeof(C)) + 127) & ~size_t(127);
-  const int TW = grid_tile_cols(A.N);              // columns of a tiled block
-  const int CSx = ext_rows(A.N, kGridE);           // rows of the extension (tile column stride)
-  C* tabt = reinterpret_cast<C*>(smem + off);      // [N][TW] twiddle rows of the block's columns
-  off += (size_t)A.N * TW * sizeof(C);
-  C* xt = reinterpret_cast<C*>(smem + off);        // [TW + span][CSx] extension tile
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM, tid = threadIdx.x;
   const int gtid = blockIdx.x * blockDim.x + tid, nthr = gridDim.x * blockDim.x;
@@ -287,7 +224,6 @@ __global__ void __launch_bounds__(kGridThreads, 2)
   const size_t blk = ext_block_elems(M, N, E);
   const bool write_paths = (A.mode & kWritePaths) != 0;
   unsigned gen = 0;  // barriers passed
-  int tab_blk = -1;  // the block whose twiddle rows are staged in tabt
   auto fail = [&](const FrameIO& io) {
     if (tid == 0 && io.status) *io.status = ZOTFS_ETIMEOUT;
   };
@@ -475,70 +411,6 @@ __global__ void __launch_bounds__(kGridThreads, 2)
     if ((A.mode & (kEstimate | kLoadPaths)) && (A.mode & (kCG | kApply)))
       build_runs<R>(paths, P, runs, sort_tmp, sort_keys, nruns);
 
-    // the delay span of the list decides between tiled gathers (extension and twiddle slices
-    // of each block staged in shared memory) and gathers from global memory; the same in
-    // every CTA (same list)
-    int dkmin = 0, dkmax = 0;
-    if ((A.mode & (kEstimate | kLoadPaths)) && (A.mode & (kCG | kApply))) {
-      if (tid == 0) {
-        int mn = 0, mx = 0;
-        for (int p = 0; p < P; ++p) {
-          const int d = paths[p].dk;
-          mn = p ? min(mn, d) : d;
-          mx = p ? max(mx, d) : d;
-        }
-        S->isc[0] = mn;
-        S->isc[5] = mx;
-      }
-      __syncthreads();
-      dkmin = S->isc[0];
-      dkmax = S->isc[5];
-      __syncthreads();
-    }
-    const int span = dkmax - dkmin;
-    const bool tiled = span <= kGridSpanMax;
-    const int nblk = M / TW;
-
-    // Calls work(k, j0, v) with v = rows j0 .. j0 + 7 of column k of H ext (kF) or H^H ext, for
-    // every item of the frame.
-    auto gather_phase = [&](auto fwd_c, const C* ext, auto&& work) {
-      constexpr bool kF = decltype(fwd_c)::value;
-      if (tiled) {
-        const int off_min = kF ? -dkmax : dkmin;  // smallest column offset the gathers read
-        const int kk = tid % TW, j0 = (tid / TW) * E;
-        for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
-          const int k0 = bi * TW;
-          if (tab_blk != bi) {
-            for (int e = tid; e < N * TW; e += blockDim.x) {
-              const int r = e / TW, c = e - r * TW;
-              tabt[e] = tab<R>(A, (size_t)r * M + k0 + c);
-            }
-            tab_blk = bi;
-          }
-          const int c0 = k0 + (M >> 1) + off_min, W = TW + span;
-          for (int e = tid; e < W * CSx; e += blockDim.x) {
-            const int r = e / W, c = e - r * W;
-            xt[(size_t)c * CSx + r] = ext[(size_t)r * (2 * M) + c0 + c];
-          }
-          __syncthreads();
-          C vv[E];
-          grid_gather<kF>(xt, kk - off_min, tabt, TW, kk, paths, runs, nruns, N, CSx, j0, vv);
-          work(k0 + kk, j0, vv);
-          __syncthreads();  // the tile is restaged for the next block
-        }
-      } else {
-        for (int it = gtid; it < items; it += nthr) {
-          const int k = it & (M - 1), j0 = (it >> logM) * E;
-          C vv[E];
-          if constexpr (kF) gather_fwd<R, E, true>(ext, blk, paths, runs, nruns, A, 0, k, j0, vv);
-          else gather_adj<R, E, true>(ext, blk, paths, runs, nruns, A, 0, k, j0, vv);
-          work(k, j0, vv);
-        }
-      }
-    };
-    using Fwd = std::integral_constant<bool, true>;
-    using Adj = std::integral_constant<bool, false>;
-
     C v[E];
     // ------------------------------------------------ one operator apply
     if (A.mode & kApply) {
@@ -550,12 +422,13 @@ __global__ void __launch_bounds__(kGridThreads, 2)
         write_ext<R, E, true>(src, A, k, j0, v);
       }
       if (!grid_sync(G.bar, gen)) return fail(io);
-      auto store = [&](int k, int j0, auto& vv) {
+      for (int it = gtid; it < items; it += nthr) {
+        const int k = it & (M - 1), j0 = (it >> logM) * E;
+        if (A.adjoint) gather_adj<R, E, true>(src, blk, paths, runs, nruns, A, 0, k, j0, v);
+        else gather_fwd<R, E, true>(src, blk, paths, runs, nruns, A, 0, k, j0, v);
 #pragma unroll
-        for (int i = 0; i < E; ++i) reinterpret_cast<C*>(io.u_out)[(size_t)(j0 + i) * M + k] = vv[i];
-      };
-      if (A.adjoint) gather_phase(Adj{}, src, store);
-      else gather_phase(Fwd{}, src, store);
+        for (int i = 0; i < E; ++i) reinterpret_cast<C*>(io.u_out)[(size_t)(j0 + i) * M + k] = v[i];
+      }
       if (!grid_sync(G.bar, gen)) return fail(io);
       if (blockIdx.x == 0 && tid == 0 && io.status) *io.status = status_from_bits(st);
       continue;
@@ -580,17 +453,19 @@ __global__ void __launch_bounds__(kGridThreads, 2)
 
       // b = H^H y;  c = b, p = b, x = 0, c_n = ||c||^2
       R part = 0;
-      gather_phase(Adj{}, G.extT, [&](int k, int j0, auto& vv) {
+      for (int it = gtid; it < items; it += nthr) {
+        const int k = it & (M - 1), j0 = (it >> logM) * E;
+        gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           const size_t o = (size_t)(j0 + i) * M + k;
-          G.Cv[o] = vv[i];
-          G.Pv[o] = vv[i];
+          G.Cv[o] = v[i];
+          G.Pv[o] = v[i];
           G.X[o] = make_float2(0.f, 0.f);
-          part = fma(vv[i].x, vv[i].x, fma(vv[i].y, vv[i].y, part));
+          part = fma(v[i].x, v[i].x, fma(v[i].y, v[i].y, part));
         }
-        write_ext<R, E, true>(G.extP, A, k, j0, vv);
-      });
+        write_ext<R, E, true>(G.extP, A, k, j0, v);
+      }
       double* const partA = G.part;               // Re(p^H a)
       double* const partC = G.part + gridDim.x;   // ||c||^2
       double d = block_sum_to_thread0(part, S);
@@ -606,21 +481,27 @@ __global__ void __launch_bounds__(kGridThreads, 2)
 
       for (int iter = 0; iter < io.iters && !S->isc[4]; ++iter) {
         // t = H p  (extP -> extT)
-        gather_phase(Fwd{}, G.extP, [&](int k, int j0, auto& vv) { write_ext<R, E, true>(G.extT, A, k, j0, vv); });
+        for (int it = gtid; it < items; it += nthr) {
+          const int k = it & (M - 1), j0 = (it >> logM) * E;
+          gather_fwd<R, E, true>(G.extP, blk, paths, runs, nruns, A, 0, k, j0, v);
+          write_ext<R, E, true>(G.extT, A, k, j0, v);
+        }
         if (!grid_sync(G.bar, gen)) return fail(io);
         // a = H^H t + lambda p;  Re(p^H a)
         part = 0;
-        gather_phase(Adj{}, G.extT, [&](int k, int j0, auto& vv) {
+        for (int it = gtid; it < items; it += nthr) {
+          const int k = it & (M - 1), j0 = (it >> logM) * E;
+          gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const size_t o = (size_t)(j0 + i) * M + k;
             const C pv = G.Pv[o];
-            vv[i].x = fma(lam, pv.x, vv[i].x);
-            vv[i].y = fma(lam, pv.y, vv[i].y);
-            part = fma(pv.x, vv[i].x, fma(pv.y, vv[i].y, part));
-            G.Vv[o] = vv[i];
+            v[i].x = fma(lam, pv.x, v[i].x);
+            v[i].y = fma(lam, pv.y, v[i].y);
+            part = fma(pv.x, v[i].x, fma(pv.y, v[i].y, part));
+            G.Vv[o] = v[i];
           }
-        });
+        }
         d = block_sum_to_thread0(part, S);
         if (tid == 0) partA[blockIdx.x] = d;
         if (!grid_sync(G.bar, gen)) return fail(io);
@@ -730,9 +611,7 @@ __host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max) {
   off += ((size_t)p_max * sizeof(PathRecT<float>) + 127) & ~size_t(127);
   off += ((size_t)((p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);
   off += (size_t)N * kGridDftCols * sizeof(float2);
-  off += ((size_t)N * sizeof(float2) + 127) & ~size_t(127);
-  off += (size_t)N * grid_tile_cols(N) * sizeof(float2);
-  off += (size_t)(grid_tile_cols(N) + kGridSpanMax) * ext_rows(N, kGridE) * sizeof(float2);
+  off += (size_t)N * sizeof(float2);
   return off;
 }
 
