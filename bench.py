@@ -1030,8 +1030,8 @@ def main():
     ap.add_argument("--pool", type=int, default=2, help="serve: synthetic frames per (M, N, antennas, QAM) class")
     ap.add_argument("--serve-mix", default="c5", choices=["c5", "c2"],
                     help="serve: c5 = mixed shapes/antennas/QAM, c2 = 64x32 SISO 16-QAM frames only")
-    ap.add_argument("--wave-frames", type=int, default=256, help="serve: frames admitted per wave")
-    ap.add_argument("--waves", type=int, default=4, help="serve: waves in flight")
+    ap.add_argument("--wave-frames", type=int, default=512, help="serve: frames admitted per wave")
+    ap.add_argument("--waves", type=int, default=16, help="serve: waves in flight")
     ap.add_argument("--light-work", type=int, default=8192,
                     help="serve (c5 mix): frames with M*N*n_rx*n_tx up to this run in their own waves")
     args = ap.parse_args()
