@@ -30,6 +30,12 @@
  *    the create/destroy calls.  Argument errors are returned synchronously; per-frame
  *    conditions (a truncated path list, a bad path, a non-finite residual, a timed-out
  *    wait) are written to a caller-supplied device status array as zotfs_status values.
+ *  - A plan is used from one host thread at a time.  Its calls may be issued on different
+ *    streams (up to 16 in flight at once) and then run concurrently, except those that use
+ *    the plan's own scratch (the
+ *    large-frame, clustered large-frame and paper-scale kernels, and the plain form): the
+ *    plan orders these after one another across streams (an event per plan; inside a CUDA
+ *    graph capture the caller's stream order alone applies).
  *  - No call throws across the ABI.  zotfs_last_error() returns a thread-local message
  *    describing the most recent failure in the calling thread.
  */

@@ -254,7 +254,42 @@ static bool big_cluster_applies(const zotfs_plan_s* plan, int nrx, int ntx, cons
          choose_big_cluster_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, 6 - first, bc);
 }
 
+// Calls that use the plan's scratch run after the previous such call, on whatever stream it
+// was issued (outside stream capture, where the caller's stream order applies).
+static cudaError_t scratch_acquire(zotfs_plan_s* plan, cudaStream_t stream, bool& capturing) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+  if (e != cudaSuccess) return e;
+  capturing = cs != cudaStreamCaptureStatusNone;
+  if (capturing || !plan->scratch_used) return cudaSuccess;
+  return cudaStreamWaitEvent(stream, plan->scratch_done, 0);
+}
+static cudaError_t scratch_release(zotfs_plan_s* plan, cudaStream_t stream, bool capturing) {
+  if (capturing) return cudaSuccess;
+  plan->scratch_used = true;
+  return cudaEventRecord(plan->scratch_done, stream);
+}
+
+static zotfs_status launch_kernels(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream);
+
 static zotfs_status launch_any(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream) {
+  // kernels without plan scratch: the cluster receiver and the shared-memory frame kernel
+  ClusterCfg cc;
+  FrameCfg fc;
+  if (!plan->d_grid && (cluster_applies(plan, nrx, ntx, A, cc) ||
+                        choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame,
+                                         fc, real_bytes_of(plan))))
+    return launch_kernels(plan, nrx, ntx, A, stream);
+  bool capturing = false;
+  cudaError_t e = scratch_acquire(plan, stream, capturing);
+  if (e != cudaSuccess) return cuda_fail(e, "plan scratch ordering");
+  const zotfs_status st = launch_kernels(plan, nrx, ntx, A, stream);
+  e = scratch_release(plan, stream, capturing);
+  if (st == ZOTFS_OK && e != cudaSuccess) return cuda_fail(e, "plan scratch ordering");
+  return st;
+}
+
+static zotfs_status launch_kernels(zotfs_plan_s* plan, int nrx, int ntx, FrameArgs& A, cudaStream_t stream) {
   if (plan->d_grid) {  // paper-scale grid: one frame at a time on the whole GPU
     if (plan->opt.pilot_mode != ZOTFS_PILOT_SEPARATE) {
       set_error("grids with M > 256 or M*N > 16384 take separate pilot frames only");
@@ -416,6 +451,7 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
   if (e == cudaSuccess) e = cudaMalloc(&p->d_W64, sizeof(double2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab64, sizeof(double2) * MN);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(int) * 64);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->scratch_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int) * kOrderCap * kOrderSlots);
   if (e == cudaSuccess && p->plain_bytes) e = cudaMalloc(&p->d_plain, p->plain_bytes);
   if (e == cudaSuccess && paper_scale) {
@@ -475,6 +511,7 @@ zotfs_status zotfs_plan_destroy(zotfs_plan plan) {
   if (plan->d_plain) cudaFree(plan->d_plain);
   if (plan->d_big) cudaFree(plan->d_big);
   if (plan->d_grid) cudaFree(plan->d_grid);
+  if (plan->scratch_done) cudaEventDestroy(plan->scratch_done);
   delete plan;
   return ZOTFS_OK;
 }
@@ -747,8 +784,14 @@ zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void*
     zotfs_status s = check_paths(plan, paths, true);
     if (s) return s;
   }
-  return run_plain(plan, y_pilot_td, y_data_td, noise_var, theta, iters, paths, x_hat, llr, bits, status, n_frames,
-                   stream);
+  bool capturing = false;
+  cudaError_t e = scratch_acquire(plan, stream, capturing);
+  if (e != cudaSuccess) return cuda_fail(e, "plan scratch ordering");
+  const zotfs_status st = run_plain(plan, y_pilot_td, y_data_td, noise_var, theta, iters, paths, x_hat, llr, bits,
+                                    status, n_frames, stream);
+  e = scratch_release(plan, stream, capturing);
+  if (st == ZOTFS_OK && e != cudaSuccess) return cuda_fail(e, "plan scratch ordering");
+  return st;
 }
 
 }  // extern "C"

@@ -35,6 +35,9 @@ struct zotfs_plan_s {
   // paper-scale grids: the grid receiver's scratch (one frame at a time)
   char* d_grid;
   size_t grid_bytes;
+  // orders the calls that use the plan's scratch (d_big, d_grid, d_plain) across streams
+  cudaEvent_t scratch_done;
+  bool scratch_used;
 };
 
 namespace zotfs {
@@ -50,7 +53,9 @@ bool is_pow2(int v);
 // with a closing radix-2 stage measured a few per cent faster than pure radix 2 at 64x32).
 constexpr int kDefaultRadix = 4;
 
-constexpr int kOrderCap = 16384, kOrderSlots = 4;
+// Frame-order arrays rotate over kOrderSlots per plan, and work counters over 64: up to
+// kOrderSlots calls of one plan may be in flight on different streams at once.
+constexpr int kOrderCap = 16384, kOrderSlots = 16;
 
 // Launch a kernel that writes into `order` a permutation of [0, n) listing frames by
 // decreasing expected work: by increasing threshold theta (a lower threshold keeps more

@@ -183,3 +183,26 @@ def test_big_cluster_equalize_given_lists(y_is_dd):
     for f in range(F):
         ref = eq.cga(grids[f], y_dd[f].reshape(-1), float(b["noise_var"][f]), iters)
         assert rel_l2(x[f].reshape(-1), ref) < TOL_X, f
+
+
+def test_plan_scratch_calls_on_two_streams_are_ordered():
+    """Calls of a large-frame plan (its kernels share the plan's scratch) issued on two
+    streams give the results of the same calls issued one after another."""
+    M, N, nrx, ntx, Q, F = 64, 32, 4, 4, 16, 12
+    b1 = synth.fractional_batch(F, seed=9400, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx)
+    b2 = synth.fractional_batch(F, seed=9401, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx)
+    plan = Plan(M, N, nrx, ntx, Q)
+    ref1, ref2 = _run(plan, b1, 10, F), _run(plan, b2, 10, F)
+    torch.cuda.synchronize()
+    ins = [[to_dev(b[k]) for k in ("y_pilot_td", "y_data_td", "noise_var", "theta")] for b in (b1, b2)]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for rep in range(3):
+        for s, (yp, yd, nv, th) in zip((s1, s2), ins):
+            with torch.cuda.stream(s):
+                outs.append(plan.rx(yp, yd, nv, th, 10, F, want_x=True, want_llr=True, stream=s))
+    torch.cuda.synchronize()
+    for i, o in enumerate(outs):
+        ref = ref1 if i % 2 == 0 else ref2
+        for key in ("x_hat", "llr", "bits", "status"):
+            assert torch.equal(o[key], ref[key]), (i, key)
