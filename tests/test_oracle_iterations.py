@@ -50,3 +50,17 @@ def test_library_matches_oracle_on_random_curves():
         curves.append(list(c))
         assert lib.convergence_iteration(c) == it.convergence_iteration(list(c))
     assert lib.iteration_budget(curves) == it.budget(curves)
+
+
+def test_veh_a_frames_decode_at_high_snr():
+    """The Veh-A generator (Table vehAProf delays and powers, Doppler nu_max cos(2 pi U)) makes
+    frames the oracle receiver decodes to a low BER at 40 dB."""
+    import synth
+    from oracle import receiver
+    M, N, Q = 32, 16, 4
+    b = synth.veh_a_batch(2, 17, M=M, N=N, Q=Q, snr_db=(40,))
+    for f in range(2):
+        out = receiver.receive(b["y_pilot_td"][f], b["y_data_td"][f], M, N, 1, 1, Q, float(b["noise_var"][f]),
+                               float(b["theta"][f]), 30, b["a_pilot"], p_max=256)
+        ber = float((out["bits"].reshape(-1) != b["bits"][f].reshape(-1)).mean())
+        assert ber < 0.02, (f, ber)
