@@ -1,9 +1,8 @@
 // The large-frame receiver on a thread-block cluster of CL CTAs per frame.  The frame's
 // vectors live in one global-memory scratch slot per cluster (as in big_kernel, where one
 // CTA owns a slot), and each CTA of the cluster owns a band of N / CL Doppler rows of every
-// antenna block.  With CL CTAs per frame, CL times fewer slots are live at once, so the
-// slots of all resident clusters fit the L2 where one slot per CTA does not, and each frame
-// finishes about CL times sooner.  The pilot read-offs and data-frame transforms are spread
+// antenna block.  With CL CTAs per frame, CL times fewer slots are live at once (a higher L2
+// hit rate for the gathers) and each frame finishes about CL times sooner.  The pilot read-offs and data-frame transforms are spread
 // over the CTAs by antenna block; the path lists are then copied to every CTA through
 // distributed shared memory.  Cluster barriers order the CTAs' global-memory vector updates,
 // and Algorithm 1's scalars are rank-ordered FP64 sums of the CTAs' partials.
