@@ -76,9 +76,16 @@ def test_rx_lists_pilot_reuse_vs_oracle(M, N, nrx, ntx, Q, cluster):
 
 
 def test_rx_lists_equals_equalize_then_demap():
-    M, N, Q, P, D = 64, 32, 16, 3, 4
-    plan, b, paths, out = _packets_vs_oracle(M, N, 1, 1, Q, P, D, seed=9960)
+    """More data frames than resident CTAs (frames taken heaviest first, by the path counts of
+    each frame's list set): bitwise the equalize-then-demap chain on the lists repeated per
+    data frame."""
+    M, N, Q, P, D = 64, 32, 16, 48, 8
+    b = synth.packet_batch(P, D, 9960, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    paths = plan.estimate(to_dev(b["y_pilot_td"]), to_dev(b["theta"]), P)
     F = P * D
+    out = plan.rx_lists(to_dev(b["y_data_td"]), paths, to_dev(b["noise_var"]), 10, F,
+                        path_ids=to_dev(b["path_ids"]), want_x=True, want_llr=True)
     ids = torch.from_numpy(b["path_ids"].astype(np.int64)).to(dev())
     full = plan.new_paths(F)  # the packets' lists repeated per data frame
     full.count.copy_(paths.count[ids])
@@ -110,3 +117,18 @@ def test_rx_lists_bad_list_id():
     assert st[1] == EINVAL and (st[[0, 2, 3]] == 0).all()
     for f in (0, 2, 3):
         assert torch.equal(out["bits"][f], good["bits"][f]), f
+
+
+def test_rx_lists_without_ids_equals_fused_rx():
+    """Without path_ids frame f takes list set f: with the lists the fused receiver estimated
+    from the same pilots, the outputs are bitwise those of zotfs_rx."""
+    M, N, Q, F = 64, 32, 16, 16
+    b = synth.fractional_batch(F, seed=9980, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    ref = plan.rx(to_dev(b["y_pilot_td"]), to_dev(b["y_data_td"]), to_dev(b["noise_var"]), to_dev(b["theta"]), 10, F,
+                  want_paths=True, want_x=True, want_llr=True)
+    out = plan.rx_lists(to_dev(b["y_data_td"]), ref["paths"], to_dev(b["noise_var"]), 10, F, want_x=True,
+                        want_llr=True)
+    torch.cuda.synchronize()
+    for key in ("x_hat", "llr", "bits", "status"):
+        assert torch.equal(out[key], ref[key]), key

@@ -153,3 +153,13 @@ def test_grid_shapes_are_siso_only():
         Plan(1024, 32, 2, 2, 16)
     with pytest.raises(ZotfsError):
         Plan(16384, 64, 1, 1, 16)  # M N above 524288
+
+
+def test_grid_embedded_pilot_is_unsupported():
+    from paper_2604_02266_gb300 import PILOT_EMBEDDED, ZotfsError
+    M, N, Q = 1024, 32, 4
+    b = synth.fractional_batch(1, seed=9906, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q, pilot_mode=PILOT_EMBEDDED)
+    yd = to_dev(b["y_data_td"])
+    with pytest.raises(ZotfsError):
+        plan.rx(yd, yd, to_dev(b["noise_var"]), to_dev(b["theta"]), 10, 1)
