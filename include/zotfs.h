@@ -392,7 +392,10 @@ typedef struct zotfs_server_s* zotfs_server;
 typedef struct zotfs_server_opts {
   int32_t p_max;            /* path-list capacity of every frame (1..256) */
   int32_t max_wave_frames;  /* frames admitted per wave, 1..4096 */
-  int32_t waves_in_flight;  /* concurrent waves, 1..16 */
+  int32_t waves_in_flight;  /* concurrent waves, 1..16; each holds its own scratch (large-frame
+                               slots for every SM); more waves let the heavy buckets of
+                               consecutive waves run side by side (16 measured best on mixed
+                               loads) */
   int32_t keep_llr;         /* also keep float32 LLRs per frame */
   int64_t arena_bytes;      /* device bytes for admitted frames' outputs */
   int32_t max_M, max_N, max_ant;  /* largest frame accepted (sizes the large-frame scratch) */
