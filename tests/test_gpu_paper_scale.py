@@ -30,8 +30,10 @@ def Plan(*a, **k):
     return P(*a, **k)
 
 
-@pytest.mark.parametrize("M,N,Q", [(1024, 32, 16), (512, 64, 4), (4096, 16, 64)])
+@pytest.mark.parametrize("M,N,Q", [(1024, 32, 16), (512, 64, 4), (4096, 16, 64), (2048, 8, 16)])
 def test_grid_rx_vs_oracle(M, N, Q):
+    """(2048, 8): M > 256 with M N = 16384 -- the shortest Doppler axis, whose extension holds
+    the rows twice over."""
     F = 2
     b = synth.fractional_batch(F, seed=9700 + M + N, M=M, N=N, Q=Q, snr_db=(10, 25))
     plan = Plan(M, N, 1, 1, Q)
