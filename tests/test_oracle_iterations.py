@@ -23,6 +23,12 @@ def test_rebound_converges_at_the_rise():
     assert it.convergence_iteration([0.3, 0.1, 0.08, 0.07], eta=0.3) == 3
 
 
+def test_relative_change_is_taken_against_the_previous_ber():
+    """Halving the BER is a relative change of 1/2 (against the previous BER), so with
+    eta = 0.6 the curve has converged at the second iteration."""
+    assert it.convergence_iteration([0.2, 0.1, 0.0999], eta=0.6) == 2
+
+
 def test_zero_ber_and_zeta_guard():
     assert it.convergence_iteration([0.0, 0.0, 0.0]) == 2
     # a fall to zero from a tiny BER is a full relative gain (r = 1), not a division by zero

@@ -110,3 +110,97 @@ def test_natural_binary_labels_are_caught(monkeypatch):
     dmin = d[d > 1e-12].min()
     adj = [(bits[a] != bits[b]).sum() for a in range(16) for b in range(16) if abs(d[a, b] - dmin) < 1e-9]
     assert max(adj) > 1
+
+
+# ------------------------------------------------- stopping test and iteration budget
+
+def _stopping_pin_holds():
+    """The pin of tests/test_oracle_equalizer.py's stopping test, as a predicate."""
+    g = np.random.default_rng(21)
+    M, N = 16, 16
+    cand = [(a, b) for a in range(-3, 3) for b in range(-3, 3)]
+    pick = g.choice(len(cand), size=5, replace=False)
+    h = (g.standard_normal(5) + 1j * g.standard_normal(5)) / np.sqrt(10)
+    pl = dc.PathList.from_offsets(M, N, M // 2, N // 2, h, [cand[c][0] for c in pick], [cand[c][1] for c in pick])
+    Hd = dc.dense_H(dc.heff_from_paths(pl), M // 2, N // 2)
+    lam = 0.02
+    A = Hd.conj().T @ Hd + lam * np.eye(M * N)
+    y = g.standard_normal(M * N) + 1j * g.standard_normal(M * N)
+    b = Hd.conj().T @ y
+    nb2 = float(np.vdot(b, b).real)
+    _, hist = eq.cga(pl, y, lam, 12, history=True)
+    k = 5
+    eps = np.sqrt(np.sqrt(hist[k] * hist[k + 1]) / nb2)
+    x = eq.cga(pl, y, lam, 12, eps=eps)
+    r = b - A @ x
+    rp = b - A @ eq.cga(pl, y, lam, k)
+    return (float(np.vdot(r, r).real) <= eps * eps * nb2 and float(np.vdot(rp, rp).real) > eps * eps * nb2
+            and np.array_equal(x, eq.cga(pl, y, lam, k + 1)))
+
+
+def test_stopping_pin_passes_unmodified():
+    assert _stopping_pin_holds()
+
+
+def test_stopping_test_slips_are_caught(monkeypatch):
+    """An absolute threshold (c_n <= eps^2, the form Sec. IV-C quotes for the original CGA, which
+    scales with MN), or a test placed before the update of c, stops at another iteration."""
+    orig = eq.cga
+
+    def planted(absolute, before_update):
+        def cga(paths, y, lam, iters, history=False, eps=0.0):
+            if eps <= 0.0:
+                return orig(paths, y, lam, iters, history)
+            op = eq.as_operator(paths)
+            b = op.adjoint(y)
+            x = np.zeros_like(b)
+            c = b.copy()
+            p = b.copy()
+            cn = float(np.vdot(c, c).real)
+            stop_at = eps * eps * (1.0 if absolute else cn)
+            prev = cn
+            for _ in range(iters):
+                if (prev if before_update else cn) <= stop_at:
+                    break
+                a = op.adjoint(op.forward(p)) + lam * p
+                alpha = cn / float(np.vdot(p, a).real)
+                x = x + alpha * p
+                prev = cn
+                c = c - alpha * a
+                cn_new = float(np.vdot(c, c).real)
+                p = c + (cn_new / cn) * p
+                cn = cn_new
+            return x
+        return cga
+
+    for absolute, before in ((True, False), (False, True)):
+        monkeypatch.setattr(eq, "cga", planted(absolute, before))
+        assert not _stopping_pin_holds(), (absolute, before)
+    monkeypatch.setattr(eq, "cga", orig)
+
+
+def test_iteration_criterion_slips_are_caught(monkeypatch):
+    """Dividing by the new BER instead of the previous one, or dropping the zeta guard's max,
+    changes a pinned convergence iteration."""
+    from oracle import iterations as it
+
+    def by_new(ber, eta=1e-2, zeta=1e-12):
+        for xi in range(2, len(ber) + 1):
+            prev, cur = ber[xi - 2], ber[xi - 1]
+            if (prev - cur) / max(cur, zeta) < eta:
+                return xi
+        return len(ber)
+
+    def no_guard(ber, eta=1e-2, zeta=1e-12):
+        for xi in range(2, len(ber) + 1):
+            prev, cur = ber[xi - 2], ber[xi - 1]
+            r = (prev - cur) / prev if prev != 0.0 else 1.0
+            if r < eta:
+                return xi
+        return len(ber)
+
+    pinned = [([0.3, 0.1, 0.08, 0.07], 0.3, 3), ([0.0, 0.0, 0.0], 1e-2, 2), ([0.2, 0.1, 0.0999], 0.6, 2)]
+    for fn in (by_new, no_guard):
+        assert any(fn(b, eta) != want for b, eta, want in pinned), fn.__name__
+    for b, eta, want in pinned:
+        assert it.convergence_iteration(b, eta) == want
