@@ -90,3 +90,23 @@ def test_argument_errors_without_gpu(libpath):
     bad = Z.zotfs_autotune_opts(-1, 0, 0)
     res = (Z.zotfs_tuning_result * 1)()
     assert Z.zotfs_autotune(d, 1, ctypes.byref(bad), res, 1, ctypes.byref(n), None) == Z.EINVAL
+
+
+def _declared_arity():
+    """Number of parameters of each function declared in the header."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(zotfs_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_arity_matches_header():
+    """Each ctypes signature has as many arguments as the header's prototype."""
+    from paper_2604_02266_gb300 import _zotfs
+    arity = _declared_arity()
+    assert set(arity) == set(_zotfs.SIGNATURES)
+    wrong = {n: (len(args), arity[n]) for n, (_, args) in _zotfs.SIGNATURES.items() if len(args) != arity[n]}
+    assert not wrong, wrong
