@@ -1018,7 +1018,7 @@ def impl_latency(args):
         yp, yd = torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev)
         nv, th = torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev)
         res = {"M": m, "N": n}
-        for name, cl in (("one_cta", 1), ("cluster2", 2)):
+        for name, cl in (("one_cta", 1), ("cluster2", 2), ("cluster4", 4)):
             plan = Plan(m, n, 1, 1, Q)
             plan.set_tuning(cluster=cl)
             outs = plan._rx_outputs(1, dev, False, False, False)
