@@ -217,6 +217,14 @@ zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const z
 zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise_var, float* llr,
                          uint8_t* bits, int n_frames, zotfs_stream stream);
 
+/* Self-check of the device-side failure detection: runs one of the library's bounded waits
+ * against a condition nothing satisfies -- which = 0: the mbarrier wait of the frame
+ * kernels' bulk copies with no copy issued; 1: the grid barrier of the paper-scale receiver
+ * with one of two CTAs leaving without arriving -- and writes the outcome to *status (dev
+ * int32): ZOTFS_ETIMEOUT once the wait gave up after max_polls polls (1 .. 2^24).  Nothing
+ * traps or hangs; the context stays usable. */
+zotfs_status zotfs_check_bounded_wait(int which, uint32_t max_polls, int32_t* status, zotfs_stream stream);
+
 /* Data frames equalised and demapped with path lists estimated earlier (pilot reuse: one
  * pilot frame's lists serve the data frames of its packet, which Sec. III-B sizes by the
  * channel coherence time).  Data frame f uses list set path_ids[f] of the

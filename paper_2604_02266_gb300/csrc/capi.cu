@@ -763,6 +763,17 @@ zotfs_status zotfs_rx_lists(zotfs_plan plan, const void* y_data_td, const zotfs_
   return launch_any(plan, plan->nrx, plan->ntx, A, stream);
 }
 
+zotfs_status zotfs_check_bounded_wait(int which, uint32_t max_polls, int32_t* status, zotfs_stream stream) {
+  g_launches = 0;
+  if (which != 0 && which != 1) return inval("which must be 0 (mbarrier wait) or 1 (grid barrier)");
+  if (max_polls < 1 || max_polls > (1u << 24)) return inval("max_polls must be in [1, 2^24]");
+  if (!status) return inval("status is NULL");
+  cudaError_t e = check_bounded_wait(which, max_polls, status, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bounded-wait check launch");
+  ++g_launches;
+  return ZOTFS_OK;
+}
+
 zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void* y_data_td, const float* noise_var,
                             const float* theta, int iters, const zotfs_paths* paths, float* x_hat, float* llr,
                             uint8_t* bits, int32_t* status, int n_frames, zotfs_stream stream) {

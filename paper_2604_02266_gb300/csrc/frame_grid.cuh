@@ -96,7 +96,7 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 // Every thread counts the barriers passed in `gen`.  Returns false in every thread of the CTA
 // when this wait or an earlier one gave up (bounded polls): the caller abandons the frame.
 // (Arrivals on per-CTA flags gathered by one warp were measured slower than one counter.)
-__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen) {
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, uint32_t max_polls = kGridMaxPolls) {
   __syncthreads();
   const unsigned g = gen;
   gen = g + 1;
@@ -113,7 +113,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen) {
       } else {
         uint32_t polls = 0;
         while (ld_acquire_gpu(&b->gen) == g) {
-          if (++polls > kGridMaxPolls) {
+          if (++polls > max_polls) {
             atomicExch(&b->err, 1);
             ok = 0;
             break;

@@ -33,7 +33,40 @@ cudaError_t grant(int EQ, size_t smem) {
   return e;
 }
 
+// Self-checks of the bounded device waits (failure detection without a fault): each runs one
+// wait against a condition nothing satisfies and stores the outcome.
+__global__ void check_mbar_wait_kernel(uint32_t max_polls, int32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, max_polls);  // nothing arrives on the barrier
+  if (threadIdx.x == 0) *status = ok ? ZOTFS_OK : ZOTFS_ETIMEOUT;
+}
+
+__device__ GridBarrier g_check_bar;
+
+__global__ void check_grid_wait_kernel(uint32_t max_polls, int32_t* status) {
+  if (blockIdx.x != 0) return;  // the other CTA leaves without arriving
+  unsigned gen = 0;
+  const bool ok = grid_sync(&g_check_bar, gen, max_polls);
+  if (threadIdx.x == 0) *status = ok ? ZOTFS_OK : ZOTFS_ETIMEOUT;
+}
+
 }  // namespace
+
+cudaError_t check_bounded_wait(int which, uint32_t max_polls, int32_t* status, cudaStream_t stream) {
+  if (which == 0) {
+    check_mbar_wait_kernel<<<1, 32, 0, stream>>>(max_polls, status);
+    return cudaGetLastError();
+  }
+  void* bar = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&bar, g_check_bar);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), stream);
+  if (e != cudaSuccess) return e;
+  void* params[] = {&max_polls, &status};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(check_grid_wait_kernel), dim3(2), dim3(32), params,
+                                     0, stream);
+}
 
 bool grid_shape(int M, int N, int nrx, int ntx) {
   return nrx == 1 && ntx == 1 && (M > 256 || M * N > 16384) && M >= kGridDftCols && M <= 16384 && N >= 8 &&

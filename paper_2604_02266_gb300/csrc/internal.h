@@ -126,6 +126,9 @@ bool grid_shape(int M, int N, int nrx, int ntx);
 cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, GridCfg& cfg);
 size_t grid_scratch_size(int M, int N, int p_max, int grid);
 cudaError_t grid_launch(const GridCfg& cfg, const FrameArgs& A, char* scratch, cudaStream_t stream);
+// Runs one bounded device wait that nothing satisfies (0: an mbarrier wait, 1: the grid
+// barrier with one CTA absent) and stores its outcome in *status.
+cudaError_t check_bounded_wait(int which, uint32_t max_polls, int32_t* status, cudaStream_t stream);
 
 // Cluster receiver (cluster_variant.cu): one SISO frame on C CTAs of a thread-block cluster.
 struct ClusterCfg {

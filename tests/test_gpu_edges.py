@@ -2,6 +2,8 @@
 frame with non-finite samples among clean ones, the smallest grid, and independence of the
 per-frame results from the order in which the persistent CTAs take the frames."""
 
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -110,3 +112,22 @@ def test_rx_results_do_not_depend_on_frame_order():
     for key in ("x_hat", "llr", "bits", "status"):
         assert torch.equal(whole[key], torch.cat([p[key] for p in parts])), key
     assert torch.equal(whole["paths"].count, torch.cat([p["paths"].count for p in parts]))
+
+
+def test_bounded_waits_give_up_with_etimeout():
+    """Failure detection without a fault: the mbarrier wait of the bulk copies and the grid
+    barrier of the paper-scale receiver, each run against a condition nothing satisfies, give
+    up after their poll limit and report ZOTFS_ETIMEOUT; the context stays usable (a receiver
+    call afterwards matches the oracle)."""
+    from paper_2604_02266_gb300 import ETIMEOUT, _zotfs as Z
+    for which in (0, 1):
+        st = torch.full((1,), -1, dtype=torch.int32, device=dev())
+        Z.check(Z.zotfs_check_bounded_wait(which, 1 << 14, ctypes.c_void_p(st.data_ptr()), None))
+        torch.cuda.synchronize()
+        assert st.item() == ETIMEOUT, which
+    M, N, Q, F = 32, 16, 16, 2
+    b = synth.fractional_batch(F, seed=76, M=M, N=N, Q=Q)
+    out = _run(Plan(M, N, 1, 1, Q), b, 10, F)
+    torch.cuda.synchronize()
+    wx, wl, mm = _check_frames(b, out, range(F), M, N, 1, 1, Q, 10, 64)
+    assert wx < TOL_X and wl < TOL_LLR and mm == 0, (wx, wl, mm)
