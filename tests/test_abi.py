@@ -110,3 +110,55 @@ def test_binding_arity_matches_header():
     assert set(arity) == set(_zotfs.SIGNATURES)
     wrong = {n: (len(args), arity[n]) for n, (_, args) in _zotfs.SIGNATURES.items() if len(args) != arity[n]}
     assert not wrong, wrong
+
+
+def test_newer_entry_points_validate_without_gpu(libpath):
+    """zotfs_rx_lists, zotfs_check_bounded_wait and zotfs_server_create reject bad arguments
+    with ZOTFS_EINVAL before any CUDA call."""
+    from paper_2604_02266_gb300 import _zotfs as Z
+    st = ctypes.c_int32(-99)
+    assert Z.zotfs_check_bounded_wait(2, 100, ctypes.byref(st), None) == Z.EINVAL
+    assert b"which" in Z.zotfs_last_error()
+    assert Z.zotfs_check_bounded_wait(-1, 100, ctypes.byref(st), None) == Z.EINVAL
+    assert Z.zotfs_check_bounded_wait(0, 0, ctypes.byref(st), None) == Z.EINVAL
+    assert Z.zotfs_check_bounded_wait(1, (1 << 24) + 1, ctypes.byref(st), None) == Z.EINVAL
+    assert b"max_polls" in Z.zotfs_last_error()
+    assert Z.zotfs_check_bounded_wait(0, 100, None, None) == Z.EINVAL
+    assert st.value == -99  # nothing was written
+    assert Z.zotfs_rx_lists(None, None, None, None, 1, None, 10, None, None, None, None, 1, None) == Z.EINVAL
+    assert b"plan" in Z.zotfs_last_error()
+    out = ctypes.c_void_p(1)
+    assert Z.zotfs_server_create(None, ctypes.byref(out)) == Z.EINVAL
+    good = dict(p_max=64, max_wave_frames=256, waves_in_flight=4, keep_llr=0, arena_bytes=1 << 20, max_M=64,
+                max_N=32, max_ant=1, light_work=0)
+    for key, bad in (("p_max", 0), ("p_max", 257), ("max_wave_frames", 4097), ("waves_in_flight", 17),
+                     ("arena_bytes", 1024), ("max_M", 48), ("max_M", 512), ("max_N", 128), ("max_ant", 5),
+                     ("light_work", -1)):
+        o = Z.zotfs_server_opts(**{**good, key: bad})
+        assert Z.zotfs_server_create(ctypes.byref(o), ctypes.byref(out)) == Z.EINVAL, key
+        assert b"out of range" in Z.zotfs_last_error(), key
+        assert out.value is None, key
+
+
+def test_tuning_file_round_trip(tmp_path, libpath):
+    """Autotuner results persist as JSON and load back as Batch(tuning=...) entries; a file of
+    another format is refused."""
+    import json
+    from paper_2604_02266_gb300 import load_tuning, save_tuning
+    res = [{"M": 64, "N": 32, "n_rx": 1, "n_tx": 1, "threads_per_frame": 256, "fft_radix": 4, "ctas_per_sm": 2,
+            "cluster": 0, "sm_ms_per_frame": 0.08, "ms_best": 0.5, "ms_default": 0.6, "n_candidates": 9,
+            "n_frames": 1024},
+           {"M": 128, "N": 64, "n_rx": 4, "n_tx": 4, "threads_per_frame": 512, "fft_radix": 2, "ctas_per_sm": 1,
+            "cluster": 4, "sm_ms_per_frame": 9.5, "ms_best": 17.0, "ms_default": 17.7, "n_candidates": 6,
+            "n_frames": 256}]
+    path = tmp_path / "tuning.json"
+    save_tuning(str(path), res, "GB300")
+    doc = json.loads(path.read_text())
+    assert doc["format"] == "zotfs-tuning-1" and doc["device"] == "GB300" and len(doc["entries"]) == 2
+    assert load_tuning(str(path)) == [
+        ((64, 32, 1, 1), {"threads_per_frame": 256, "fft_radix": 4, "ctas_per_sm": 2, "cluster": 0}),
+        ((128, 64, 4, 4), {"threads_per_frame": 512, "fft_radix": 2, "ctas_per_sm": 1, "cluster": 4})]
+    other = tmp_path / "other.json"
+    other.write_text(json.dumps({"format": "something-else", "entries": []}))
+    with pytest.raises(ValueError):
+        load_tuning(str(other))
