@@ -1,9 +1,13 @@
 """Helpers shared by the GPU parity tests: moving synthetic inputs to the device, carrying
 path lists between the oracle and the library, and the comparison rules.
 
-Comparison rules (derived in the design doc):
+Comparison rules:
 * floating point results: relative L2 error against the FP64 oracle on identical inputs
-  (x_hat <= 1e-5, LLRs <= 1e-3, Zak transform and operator applies <= 1e-5);
+  (x_hat <= 1e-5, LLRs <= 1e-3, Zak transform and operator applies <= 1e-5).  Ten FP32 CG
+  iterations track the FP64 ones to ~1e-6 on the test frames.  The max-log LLR is a
+  continuous, piecewise-linear function of x_hat, so its relative error follows x_hat's
+  (2.9e-6 against 2.2e-6 in the mixed-precision tests); 1e-3 covers the x_hat bar with room
+  and still catches a wrong label, sign or 1/lambda scale, which moves LLRs by O(1);
 * decisions taken in floating point (a tap passing the threshold, the P_max-th largest
   tap, a hard bit) must agree wherever the oracle's margin exceeds the FP32 rounding the
   library's arithmetic can make; inside that margin either outcome is valid and the test
