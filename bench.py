@@ -864,7 +864,9 @@ def impl_packets(args):
         if i >= 3:
             ts.append(t0.elapsed_time(t1))
     ts = np.array(ts)
-    two_t_ms = 2e3 * N / 30e3
+    from paper_2604_02266_gb300 import numerology
+    two_t_ms = numerology.packet_deadline(N, 30e3) * 1e3
+    packet_ms = numerology.packet_deadline(N, 30e3, D) * 1e3
     line = {"metric": "equalized Zak-OTFS data frames/s with pilot reuse, 64x32 16-QAM", "value": F / ms * 1e3,
             "unit": "frames/s", "n_gpus": 1, "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -875,7 +877,8 @@ def impl_packets(args):
             "mbit_s": F * M * N * 4 / ms / 1e3, "status_ok": float((s_ == 0).mean()), "gpu_launches_per_step": 3,
             "one_packet_per_call": {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
                                     "deadline_2T_ms": two_t_ms, "within_2T": float((ts <= two_t_ms).mean()),
-                                    "packets": int(ts.size)}}
+                                    "packet_duration_ms": packet_ms, "packets": int(ts.size)},
+            "data_per_pilot_at_100Hz": numerology.data_frames_per_pilot(100.0, N, 30e3)}
     print(json.dumps(line))
     return 0
 
