@@ -225,6 +225,13 @@ zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise
  * traps or hangs; the context stays usable. */
 zotfs_status zotfs_check_bounded_wait(int which, uint32_t max_polls, int32_t* status, zotfs_stream stream);
 
+/* Host-side fault injection for tests of the allocation-failure paths: with after = n >= 0,
+ * the library's next n device or pinned-host allocations (any call, any thread) succeed and
+ * the one after fails as if the device were out of memory; that call then returns
+ * ZOTFS_ENOMEM having freed what it had allocated, and the injection switches itself off.
+ * after = -1 switches it off.  No device work is done; ZOTFS_EINVAL for after < -1. */
+zotfs_status zotfs_debug_fail_alloc(int after);
+
 /* Data frames equalised and demapped with path lists estimated earlier (pilot reuse: one
  * pilot frame's lists serve the data frames of its packet, which Sec. III-B sizes by the
  * channel coherence time).  Data frame f uses list set path_ids[f] of the

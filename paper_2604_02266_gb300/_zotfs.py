@@ -118,6 +118,7 @@ SIGNATURES = {
     "zotfs_rx_plain": (_I, [_P, _P, _P, _P, _P, _I, C.POINTER(zotfs_paths), _P, _P, _P, _P, _I, _P]),
     "zotfs_rx_lists": (_I, [_P, _P, C.POINTER(zotfs_paths), _P, _I, _P, _I, _P, _P, _P, _P, _I, _P]),
     "zotfs_check_bounded_wait": (_I, [_I, C.c_uint32, _P, _P]),
+    "zotfs_debug_fail_alloc": (_I, [_I]),
     "zotfs_equalize_static": (_I, [_I, _I, _I, _I, C.POINTER(zotfs_paths), _P, _P, _I, _P, _P, _I, _P]),
     "zotfs_batch_create": (_I, [C.POINTER(zotfs_frame_desc), _I, C.POINTER(zotfs_batch_opts), C.POINTER(_P)]),
     "zotfs_rx_batch": (_I, [_P, _P, _P]),
@@ -189,6 +190,7 @@ zotfs_rx = _mk("zotfs_rx")
 zotfs_rx_plain = _mk("zotfs_rx_plain")
 zotfs_rx_lists = _mk("zotfs_rx_lists")
 zotfs_check_bounded_wait = _mk("zotfs_check_bounded_wait")
+zotfs_debug_fail_alloc = _mk("zotfs_debug_fail_alloc")
 zotfs_equalize_static = _mk("zotfs_equalize_static")
 zotfs_batch_create = _mk("zotfs_batch_create")
 zotfs_rx_batch = _mk("zotfs_rx_batch")

@@ -75,8 +75,8 @@ zotfs_status make_shape_tables(int M, int N, float2** dW, float2** dTab) {
   }
   for (int dl = -N / 2; dl < N / 2; ++dl)
     for (int k = 0; k < M; ++k) Tab[(size_t)(dl + N / 2) * M + k] = W[(size_t)(((long long)dl * k) & (MN - 1))];
-  cudaError_t e = cudaMalloc(dW, sizeof(float2) * MN);
-  if (e == cudaSuccess) e = cudaMalloc(dTab, sizeof(float2) * MN);
+  cudaError_t e = dev_alloc(dW, sizeof(float2) * MN);
+  if (e == cudaSuccess) e = dev_alloc(dTab, sizeof(float2) * MN);
   if (e == cudaSuccess) e = cudaMemcpy(*dW, W.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(*dTab, Tab.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "batch tables");
@@ -289,9 +289,9 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     ids.insert(ids.end(), B.ids.begin(), B.ids.end());
   }
   if (st == ZOTFS_OK && n_frames > 0) {
-    e = cudaMalloc(&b->d_descs, sizeof(zotfs_frame_desc) * n_frames);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_ids, sizeof(int) * n_frames);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * std::max<size_t>(1, b->buckets.size()));
+    e = dev_alloc(&b->d_descs, sizeof(zotfs_frame_desc) * n_frames);
+    if (e == cudaSuccess) e = dev_alloc(&b->d_ids, sizeof(int) * n_frames);
+    if (e == cudaSuccess) e = dev_alloc(&b->d_counters, sizeof(int) * std::max<size_t>(1, b->buckets.size()));
     if (e == cudaSuccess)
       e = cudaMemcpy(b->d_descs, D.data(), sizeof(zotfs_frame_desc) * n_frames, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_ids, ids.data(), sizeof(int) * n_frames, cudaMemcpyHostToDevice);
@@ -310,7 +310,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     B.d_W = it->second.first;
     B.d_Tab = it->second.second;
     if (B.big) {
-      e = cudaMalloc(&B.d_big, (B.bigc ? B.bccfg.slot_bytes : B.bigcfg.slot_bytes) * (size_t)B.grid);
+      e = dev_alloc(&B.d_big, (B.bigc ? B.bccfg.slot_bytes : B.bigcfg.slot_bytes) * (size_t)B.grid);
       if (e != cudaSuccess) {
         st = e == cudaErrorMemoryAllocation ? ZOTFS_ENOMEM : cuda_fail(e, "large-frame scratch");
         if (st == ZOTFS_ENOMEM) set_error("large-frame scratch allocation failed");

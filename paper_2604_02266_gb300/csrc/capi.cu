@@ -1,5 +1,6 @@
 // C ABI of the zotfs library: plans, argument validation and dispatch to the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,7 +18,34 @@ void set_error(const std::string& msg) { g_err = msg; }
 
 zotfs_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
-  return ZOTFS_ECUDA;
+  return e == cudaErrorMemoryAllocation ? ZOTFS_ENOMEM : ZOTFS_ECUDA;
+}
+
+// Allocation countdown of zotfs_debug_fail_alloc: -1 off; n >= 0 lets n more allocations
+// through and fails the next one, which switches it off again.
+static std::atomic<int> g_fail_after{-1};
+
+static bool injected_failure() {
+  int n = g_fail_after.load();
+  while (n >= 0)
+    if (g_fail_after.compare_exchange_weak(n, n - 1)) return n == 0;
+  return false;
+}
+
+cudaError_t dev_alloc_bytes(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // not sticky: keep it out of later launch checks
+  return e;
+}
+
+cudaError_t host_alloc_bytes(void** p, size_t bytes, unsigned flags) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaHostAlloc(p, bytes, flags);
+  if (e == cudaErrorMemoryAllocation) cudaGetLastError();
+  return e;
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -446,18 +474,18 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
       Tab64[(size_t)(dl + N / 2) * M + k] = W64[src];
     }
   p->plain_bytes = paper_scale ? 0 : plain_scratch_bytes(M, N, n_rx, n_tx, 256);
-  e = cudaMalloc(&p->d_W, sizeof(float2) * MN);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab, sizeof(float2) * MN);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_W64, sizeof(double2) * MN);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_Tab64, sizeof(double2) * MN);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_counters, sizeof(int) * 64);
+  e = dev_alloc(&p->d_W, sizeof(float2) * MN);
+  if (e == cudaSuccess) e = dev_alloc(&p->d_Tab, sizeof(float2) * MN);
+  if (e == cudaSuccess) e = dev_alloc(&p->d_W64, sizeof(double2) * MN);
+  if (e == cudaSuccess) e = dev_alloc(&p->d_Tab64, sizeof(double2) * MN);
+  if (e == cudaSuccess) e = dev_alloc(&p->d_counters, sizeof(int) * 64);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->scratch_done, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_order, sizeof(int) * kOrderCap * kOrderSlots);
-  if (e == cudaSuccess && p->plain_bytes) e = cudaMalloc(&p->d_plain, p->plain_bytes);
+  if (e == cudaSuccess) e = dev_alloc(&p->d_order, sizeof(int) * kOrderCap * kOrderSlots);
+  if (e == cudaSuccess && p->plain_bytes) e = dev_alloc(&p->d_plain, p->plain_bytes);
   if (e == cudaSuccess && paper_scale) {
     // scratch for the largest grid the receiver launches (two CTAs per SM) and p_max 256
     p->grid_bytes = grid_scratch_size(M, N, 256, 2 * p->sm_count);
-    e = cudaMalloc(&p->d_grid, p->grid_bytes);
+    e = dev_alloc(&p->d_grid, p->grid_bytes);
   }
   {
     FrameCfg fc;
@@ -480,7 +508,7 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
           p->big_bytes = std::max(p->big_bytes, cc.slot_bytes * (size_t)clusters);
         }
       }
-      if (e == cudaSuccess) e = cudaMalloc(&p->d_big, p->big_bytes);
+      if (e == cudaSuccess) e = dev_alloc(&p->d_big, p->big_bytes);
     }
   }
   if (e == cudaSuccess) e = cudaMemcpy(p->d_W, W.data(), sizeof(float2) * MN, cudaMemcpyHostToDevice);
@@ -771,6 +799,12 @@ zotfs_status zotfs_check_bounded_wait(int which, uint32_t max_polls, int32_t* st
   cudaError_t e = check_bounded_wait(which, max_polls, status, stream);
   if (e != cudaSuccess) return cuda_fail(e, "bounded-wait check launch");
   ++g_launches;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_debug_fail_alloc(int after) {
+  if (after < -1) return inval("after must be >= -1");
+  g_fail_after.store(after);
   return ZOTFS_OK;
 }
 

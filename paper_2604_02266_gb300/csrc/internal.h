@@ -45,7 +45,23 @@ namespace zotfs {
 using PathRec = PathRecT<float>;
 
 void set_error(const std::string& msg);
+// Records `what` and the CUDA error; returns ZOTFS_ENOMEM for an allocation failure, else
+// ZOTFS_ECUDA.
 zotfs_status cuda_fail(cudaError_t e, const char* what);
+
+// Every device and pinned-host allocation of the library goes through these, so that
+// zotfs_debug_fail_alloc can make a chosen one fail (cudaErrorMemoryAllocation, *p = NULL)
+// without touching the device.
+cudaError_t dev_alloc_bytes(void** p, size_t bytes);
+cudaError_t host_alloc_bytes(void** p, size_t bytes, unsigned flags);
+template <class T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t host_alloc(T** p, size_t bytes, unsigned flags) {
+  return host_alloc_bytes(reinterpret_cast<void**>(p), bytes, flags);
+}
 int ilog2(int v);
 bool is_pow2(int v);
 

@@ -491,7 +491,7 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
   s->big_slots = s->big_slot_bytes ? s->sm_count : 0;
   s->arena_bytes = (size_t)o.arena_bytes;
   if (!st) {
-    e = cudaMalloc(&s->arena, s->arena_bytes);
+    e = dev_alloc(&s->arena, s->arena_bytes);
     if (e != cudaSuccess) st = cuda_fail(e, "server arena");
     else s->free_list[0] = s->arena_bytes;
   }
@@ -502,15 +502,15 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
   for (Wave& w : s->waves) {
     if (st) break;
     const int n = o.max_wave_frames;
-    e = cudaHostAlloc(&w.h_desc, sizeof(zotfs_frame_desc) * n, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_desc, sizeof(zotfs_frame_desc) * n);
-    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_ids, sizeof(int) * n, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_ids, sizeof(int) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_counters, sizeof(int) * kMaxBuckets);
-    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_status, sizeof(int32_t) * n, cudaHostAllocMapped);
+    e = host_alloc(&w.h_desc, sizeof(zotfs_frame_desc) * n, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = dev_alloc(&w.d_desc, sizeof(zotfs_frame_desc) * n);
+    if (e == cudaSuccess) e = host_alloc(&w.h_ids, sizeof(int) * n, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = dev_alloc(&w.d_ids, sizeof(int) * n);
+    if (e == cudaSuccess) e = dev_alloc(&w.d_counters, sizeof(int) * kMaxBuckets);
+    if (e == cudaSuccess) e = host_alloc(&w.h_status, sizeof(int32_t) * n, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&w.d_status), w.h_status, 0);
     if (e == cudaSuccess && s->big_slots)
-      e = cudaMalloc(&w.d_big, s->big_slot_bytes * (size_t)s->big_slots);
+      e = dev_alloc(&w.d_big, s->big_slot_bytes * (size_t)s->big_slots);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.main, cudaStreamNonBlocking);
     for (int i = 0; i < kWorkers && e == cudaSuccess; ++i) {
       e = cudaStreamCreateWithFlags(&w.work[i], cudaStreamNonBlocking);

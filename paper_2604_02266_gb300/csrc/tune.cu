@@ -189,8 +189,8 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
   uint8_t* d_bits = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const size_t slot = (most_bits + 255) & ~size_t(255);
-  e = cudaMalloc(&d_status, sizeof(int32_t) * (size_t)target);
-  if (e == cudaSuccess && !groups.empty()) e = cudaMalloc(&d_bits, slot * (size_t)target);
+  e = dev_alloc(&d_status, sizeof(int32_t) * (size_t)target);
+  if (e == cudaSuccess && !groups.empty()) e = dev_alloc(&d_bits, slot * (size_t)target);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   zotfs_status st = e == cudaSuccess ? ZOTFS_OK : cuda_fail(e, "autotune setup");

@@ -125,6 +125,8 @@ def test_newer_entry_points_validate_without_gpu(libpath):
     assert b"max_polls" in Z.zotfs_last_error()
     assert Z.zotfs_check_bounded_wait(0, 100, None, None) == Z.EINVAL
     assert st.value == -99  # nothing was written
+    assert Z.zotfs_debug_fail_alloc(-2) == Z.EINVAL
+    assert Z.zotfs_debug_fail_alloc(3) == Z.OK and Z.zotfs_debug_fail_alloc(-1) == Z.OK
     assert Z.zotfs_rx_lists(None, None, None, None, 1, None, 10, None, None, None, None, 1, None) == Z.EINVAL
     assert b"plan" in Z.zotfs_last_error()
     out = ctypes.c_void_p(1)
