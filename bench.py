@@ -131,6 +131,9 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- work model
 
+PATH_HIST_EDGES = [0, 8, 16, 24, 32, 40, 48, 56, 64, 65]
+
+
 def flops_per_frame(P, iters=ITERS, M=M, N=N, Q=Q):
     """Algorithmic flops of one frame: CGA (two SS applies of 8 flops per tap-element plus
     24 flops of vector updates per element and iteration, one adjoint for b), the two Zak
@@ -475,7 +478,10 @@ def impl_zotfs(args):
                            "frame_latency_p99_ms": float(np.percentile(lat, 99))},
             "speedup_vs_plain": value / plain_fps / ws,
             "paths": {"mean": float(P.mean()), "min": int(P.min()), "max": int(P.max()),
-                      "truncated_frames": int((status == 6).sum())},
+                      "truncated_frames": int((status == 6).sum()),
+                      # P_est histogram: [0, 8), [8, 16), ..., [56, 64), and exactly 64 (= p_max)
+                      "hist_edges": PATH_HIST_EDGES,
+                      "hist_counts": np.histogram(P, bins=PATH_HIST_EDGES)[0].tolist()},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
