@@ -1,7 +1,8 @@
 """Allocation failures injected on the host (zotfs_debug_fail_alloc): plan, batch, server and
 autotuner creation fail cleanly at every allocation they make -- ZOTFS_ENOMEM, no handle,
-nothing left allocated -- and what is created afterwards runs bit for bit like before.  No
-device work fails: the injected allocation is refused before CUDA is asked."""
+nothing left allocated -- and a batch created once the injection is off runs bit for bit like
+one created normally.  No device work fails: the injected allocation is refused before CUDA
+is asked."""
 
 import ctypes
 
