@@ -146,6 +146,22 @@ def test_noiseless_separate_pilot_recovery(Q, seed):
     assert (out["bits"].reshape(-1) == b["bits"][0, 0]).all()
 
 
+def _mimo_bit_errors(n_rx, n_tx, seed, Q=4):
+    b = synth.fractional_batch(1, seed=seed, M=16, N=16, Q=Q, n_rx=n_rx, n_tx=n_tx, snr_db=(60,), integer=True,
+                               dtype=np.complex128)
+    out = receiver.receive(b["y_pilot_td"][0], b["y_data_td"][0], 16, 16, n_rx, n_tx, Q, float(b["noise_var"][0]),
+                           float(b["theta"][0]), 512, b["a_pilot"])
+    return int((out["bits"].reshape(n_tx, -1) != b["bits"][0]).sum())
+
+
+@pytest.mark.parametrize("n_rx,n_tx,seed", [(2, 2, 50), (2, 2, 51), (2, 1, 52), (3, 2, 53)])
+def test_noiseless_mimo_recovery(n_rx, n_tx, seed):
+    """MIMO stacking against the independent transmitter: with one pilot frame per tx antenna
+    and one path list per (rx, tx) pair, a noiseless integer-channel frame with at least as
+    many rx as tx antennas decodes to every transmitted bit of every stream."""
+    assert _mimo_bit_errors(n_rx, n_tx, seed) == 0
+
+
 def test_cg_stopping_test_against_the_dense_residual():
     """The optional residual-norm stopping test (Sec. IV-C's description of the original CGA,
     read relative to ||b||^2).  With the threshold placed between two consecutive squared

@@ -204,3 +204,16 @@ def test_iteration_criterion_slips_are_caught(monkeypatch):
         assert any(fn(b, eta) != want for b, eta, want in pinned), fn.__name__
     for b, eta, want in pinned:
         assert it.convergence_iteration(b, eta) == want
+
+
+def test_swapped_antenna_pairing_is_caught(monkeypatch):
+    """Pairing rx r with tx t's list as if it were (t, r) -- a transposed list grid -- breaks
+    the noiseless MIMO pin."""
+    from tests.test_oracle_equalizer import _mimo_bit_errors
+    assert _mimo_bit_errors(2, 2, 50) == 0
+    orig = eq.StackedOperator.__init__
+
+    def transposed(self, grid):
+        orig(self, [list(col) for col in zip(*grid)])
+    monkeypatch.setattr(eq.StackedOperator, "__init__", transposed)
+    assert _mimo_bit_errors(2, 2, 50) > 0
