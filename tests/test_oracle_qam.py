@@ -41,6 +41,44 @@ def test_qpsk_closed_form():
     np.testing.assert_allclose(llr[:, 1], -4 * d * x.imag / lam, rtol=1e-12, atol=1e-12)
 
 
+def test_16qam_closed_form():
+    """16-QAM, per axis u (Re x for the I bits, Im x for the Q bits), levels -3d, -d, d, 3d with
+    Gray labels 00, 01, 11, 10 and d = 1/sqrt(10): the max-log LLRs are the piecewise-linear
+    forms derived by hand from the nearest level of each label class --
+    sign bit: -4 d u / lambda for |u| <= 2d, else -8 d (u - d sgn u) / lambda;
+    second bit: 4 d (|u| - 2d) / lambda."""
+    g = np.random.default_rng(16)
+    x = (g.standard_normal(2000) + 1j * g.standard_normal(2000)) * 0.9
+    lam = 0.23
+    d = 1 / np.sqrt(10)
+
+    def axis(u):
+        msb = np.where(np.abs(u) <= 2 * d, -4 * d * u, -8 * d * (u - d * np.sign(u))) / lam
+        lsb = 4 * d * (np.abs(u) - 2 * d) / lam
+        return msb, lsb
+    llr = qam.maxlog_llr(x, lam, 16)
+    for col, ref in zip(range(4), (*axis(x.real), *axis(x.imag))):
+        np.testing.assert_allclose(llr[:, col], ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("Q", [16, 64])
+def test_llr_axis_separability_and_reflection_symmetry(Q):
+    """Square Gray QAM labelled I-axis first: the I bits' LLRs depend on Re x only and the Q
+    bits' on Im x only; mirroring an axis negates its sign bit's LLR and leaves the other bits'
+    unchanged (the reflected Gray code's symmetry)."""
+    h = int(np.log2(Q)) // 2
+    g = np.random.default_rng(Q + 1)
+    x = (g.standard_normal(500) + 1j * g.standard_normal(500)) * 0.9
+    other = (g.standard_normal(500) + 1j * g.standard_normal(500)) * 0.9
+    lam = 0.4
+    a = qam.maxlog_llr(x, lam, Q)
+    np.testing.assert_allclose(qam.maxlog_llr(x.real + 1j * other.imag, lam, Q)[:, :h], a[:, :h], atol=1e-12)
+    np.testing.assert_allclose(qam.maxlog_llr(other.real + 1j * x.imag, lam, Q)[:, h:], a[:, h:], atol=1e-12)
+    m = qam.maxlog_llr(-x.real + 1j * x.imag, lam, Q)
+    np.testing.assert_allclose(m[:, 0], -a[:, 0], atol=1e-12)
+    np.testing.assert_allclose(m[:, 1:], a[:, 1:], atol=1e-12)
+
+
 @pytest.mark.parametrize("Q", [4, 16, 64])
 def test_tx_mapping_roundtrip(Q):
     """synth's TX mapping and the oracle's demapper agree on every label."""
