@@ -170,9 +170,11 @@ def test_threshold_order_and_truncation_brute_force():
     heff[3, 1] = 0.5
     heff[0, 3] = 0.5  # equal magnitude tie
     theta = 0.12
+    heff[5, 2] = -theta  # exactly at the threshold: Eq. heff_thres's strict inequality drops it
     pl = dc.threshold_paths(heff, M // 2, N // 2, theta)
     expect = [q for q in range(M * N) if abs(heff[q % M, q // M]) > theta]
     assert list(pl.lp * M + pl.kp) == expect
+    assert 2 * M + 5 not in expect
     assert not pl.truncated
     for p_max in (1, 2, 3, len(expect) - 1):
         pt = dc.threshold_paths(heff, M // 2, N // 2, theta, p_max=p_max)
