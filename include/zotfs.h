@@ -15,7 +15,8 @@
  *  - A DD grid X[k, l] (delay bin k < M, Doppler bin l < N) is stored vectorised as
  *    q = l*M + k (Sec. IV-B, "We index the q-th row ... q = l M + k").
  *  - A time-domain (TD) frame y[i], i = k + n*M < M*N, is stored in sample order.
- *  - M and N are powers of two with 16 <= M <= 256, 8 <= N <= 64 and M*N <= 16384.
+ *  - M and N are powers of two with 16 <= M <= 256, 8 <= N <= 64 and M*N <= 16384; plans
+ *    also take SISO grids up to 16384 x 32 (see zotfs_plan_create).
  *  - MIMO (n_rx x n_tx, not in the paper): unknowns are stacked per tx antenna,
  *    observations per rx antenna, one path list per (rx, tx) pair, and tx antenna t
  *    sends its own pilot frame (time-orthogonal pilots).  Layouts, per frame f:
@@ -136,8 +137,9 @@ typedef struct zotfs_paths {
  * (M N <= 524288, M >= 32), must be SISO, run one at a time on the whole GPU (a cooperative
  * launch), take separate pilot frames and FP32 compute, and have no plain form
  * (ZOTFS_EUNSUPPORTED).  Builds the root-of-unity tables (FP64 on the host, stored FP32)
- * and the plan's scratch.  The only allocating calls are the create calls.  *out is set to
- * NULL on failure. */
+ * and the plan's scratch.  The only allocating calls are the create calls (and the
+ * autotuner); when an allocation fails they free what they had allocated and return
+ * ZOTFS_ENOMEM.  *out is set to NULL on failure. */
 zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pulse, int qam,
                                zotfs_plan* out);
 zotfs_status zotfs_plan_set_options(zotfs_plan plan, const zotfs_options* opts);
