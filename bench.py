@@ -1,15 +1,15 @@
 """Benchmark of the fused Zak-OTFS receiver (SS-CGA) on the 64x32 16-QAM batch workload.
 
 One step = the whole receiver (pilot Zak transforms, read-off and thresholding, data Zak
-transform, 10 CGA iterations, max-log demapping) over a batch of 1024 frames of 64 delay x
+transform, 10 CGA iterations, max-log demapping to soft LLRs and hard bits) over a batch of 1024 frames of 64 delay x
 32 Doppler bins, each with its own pilot frame, a 6-path fractional channel and an SNR drawn
 from 0..30 dB, through the library's C ABI (zotfs_rx).  Inputs are synthetic (synth/) and
 resident in HBM; 8 copies of the batch are rotated so the timed inputs exceed the 129 MB L2.
 
 Reported (one JSON line on rank 0):
   value         frames/s over all ranks (device time, CUDA events)
-  e2e           the same metric with pinned host inputs copied in and the hard bits copied
-                back inside the timed region
+  e2e           the same metric with pinned host inputs copied in and the LLRs, hard bits
+                and statuses copied back inside the timed region
   plain_form    the plain single-frame FP32 form (one launch per stage) on the same frames
   roofline      the fused kernel against the FP32 FMA peak (algorithmic flops per launch)
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same frames
@@ -145,11 +145,13 @@ def flops_per_frame(P, iters=ITERS, M=M, N=N, Q=Q):
     return cg + dzt + demap
 
 
-def hbm_bytes_per_frame(M=M, N=N, Q=Q):
+def hbm_bytes_per_frame(M=M, N=N, Q=Q, llr=True):
     """Algorithmic HBM bytes of one frame in the fused kernel: pilot + data TD frames in
-    (complex64), hard bits out (LLRs and x_hat are not written in the timed step)."""
+    (complex64), float32 LLRs (when written), hard bits and the status word out (x_hat is
+    not written in the timed step)."""
     MN = M * N
-    return 2 * MN * 8 + MN * int(np.log2(Q)) // 8 + 4
+    bps = int(np.log2(Q))
+    return 2 * MN * 8 + (MN * bps * 4 if llr else 0) + MN * bps // 8 + 4
 
 
 def kernel_source_hash():
@@ -174,6 +176,8 @@ def profiled_traffic():
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    if vals.get("llr_written") != "yes":  # the timed step stores LLRs; a bits-only capture does not count
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -313,7 +317,8 @@ def impl_zotfs(args):
     yd = [torch.from_numpy(batch["y_data_td"]).to(dev) for _ in range(copies)]
     nv = torch.from_numpy(batch["noise_var"]).to(dev)
     th = torch.from_numpy(batch["theta"]).to(dev)
-    outs = plan._rx_outputs(FRAMES, dev, False, False, False)
+    outs = plan._rx_outputs(FRAMES, dev, False, False, True)  # soft output: LLRs + hard bits
+    outs_hard = plan._rx_outputs(FRAMES, dev, False, False, False)
     stream = torch.cuda.current_stream()
 
     # path counts of this batch (same data every step) for the flop count
@@ -346,6 +351,20 @@ def impl_zotfs(args):
     dev_s = max_over_ranks(float(step_ms.sum()) / 1e3, ws, dev)
     value = whole_job_rate(FRAMES, ws, args.steps, dev_s)
 
+    # ---- secondary: the same steps with hard bits only (no LLR store)
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(args.warmup):
+        plan.rx(yp[i % copies], yd[i % copies], nv, th, ITERS, FRAMES, out=outs_hard)
+    torch.cuda.synchronize()
+    h0.record(stream)
+    for i in range(args.steps):
+        plan.rx(yp[i % copies], yd[i % copies], nv, th, ITERS, FRAMES, out=outs_hard)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    hard_s = max_over_ranks(h0.elapsed_time(h1) / 1e3, ws, dev)
+    hard_only = {"value": whole_job_rate(FRAMES, ws, args.steps, hard_s), "unit": "frames/s",
+                 "ms_per_step": 1e3 * hard_s / args.steps, "note": "hard bits and statuses only, no LLR store"}
+
     # ---- end to end: pinned host frames in, hard bits out, every step.  Two streams with their
     # own device buffers alternate, so one step's copies overlap the other's receiver (the way
     # a receive chain streams frames); every step still copies its own inputs and results.
@@ -353,9 +372,10 @@ def impl_zotfs(args):
     hd = torch.from_numpy(batch["y_data_td"]).pin_memory()
     lanes = []
     for _ in range(2):
-        o = plan._rx_outputs(FRAMES, dev, False, False, False)
+        o = plan._rx_outputs(FRAMES, dev, False, False, True)
         lanes.append({"s": torch.cuda.Stream(device=dev), "dp": torch.empty_like(yp[0]), "dd": torch.empty_like(yd[0]),
-                      "out": o, "hb": torch.empty_like(o[3], device="cpu").pin_memory(),
+                      "out": o, "hl": torch.empty_like(o[2], device="cpu").pin_memory(),
+                      "hb": torch.empty_like(o[3], device="cpu").pin_memory(),
                       "hs": torch.empty_like(o[4], device="cpu").pin_memory()})
 
     def e2e_step(i):
@@ -364,6 +384,7 @@ def impl_zotfs(args):
             ln["dp"].copy_(hp, non_blocking=True)
             ln["dd"].copy_(hd, non_blocking=True)
             plan.rx(ln["dp"], ln["dd"], nv, th, ITERS, FRAMES, out=ln["out"], stream=ln["s"])
+            ln["hl"].copy_(ln["out"][2], non_blocking=True)
             ln["hb"].copy_(ln["out"][3], non_blocking=True)
             ln["hs"].copy_(ln["out"][4], non_blocking=True)
 
@@ -383,7 +404,7 @@ def impl_zotfs(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws, dev)
-    hb0, hs0 = lanes[0]["hb"], lanes[0]["hs"]
+    hl0, hb0, hs0 = lanes[0]["hl"], lanes[0]["hb"], lanes[0]["hs"]
 
     # ---- the same device-resident steps on the two streams (consecutive batches overlap)
     def dev_step(i):
@@ -408,12 +429,12 @@ def impl_zotfs(args):
                  "note": "inputs resident in HBM; consecutive batches on two streams overlap"}
     e2e = {"value": whole_job_rate(FRAMES, ws, args.steps, e2e_s), "unit": "frames/s",
            "h2d_bytes_per_step": int(hp.numel() * hp.element_size() + hd.numel() * hd.element_size()),
-           "d2h_bytes_per_step": int(hb0.numel() + hs0.numel() * 4),
+           "d2h_bytes_per_step": int(hl0.numel() * 4 + hb0.numel() + hs0.numel() * 4),
            "pipelined": "2 streams: step i+1's host-device copies overlap step i's receiver"}
 
     # ---- plain form: one frame at a time, one launch per stage
     n_plain = args.plain_frames
-    pout = plan._rx_outputs(1, dev, False, False, False)
+    pout = plan._rx_outputs(1, dev, False, False, True)
     lat = []
     for f in range(n_plain + 2):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -486,6 +507,7 @@ def impl_zotfs(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "pipelined": pipelined,
+            "hard_output_only": hard_only,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "wall_s_timed": wall,

@@ -270,23 +270,26 @@ zotfs_status zotfs_rx_plain(zotfs_plan plan, const void* y_pilot_td, const void*
 
 /* Equalisation that allocates nothing, for callers that must not allocate device memory
  * while they run: a real-time receive loop working to a slot deadline (cudaMalloc and
- * cudaFree synchronise the device and can stall it for milliseconds), a thread running
- * inside CUDA stream capture, or a process whose device memory is fully budgeted up front.
- * It needs no plan.  The paper has no counterpart: this is the plain-form CGA of
- * zotfs_rx_plain (b = H^H y and `iters` iterations of Algorithm 1, one kernel per step, FP32
- * with FP64 alpha/beta) with its working vectors and root-of-unity table in one fixed
- * 768 KiB array inside the library image.  Every GPU that loads the library holds that
- * array until the process exits.
+ * cudaFree synchronise the device and can stall it for milliseconds), or a process whose
+ * device memory is fully budgeted up front (an allocation made behind the budget's back can
+ * fail, or push another part of the process out of memory).  It needs no plan.  The paper
+ * has no counterpart: this is the plain-form CGA of zotfs_rx_plain (b = H^H y and `iters`
+ * iterations of Algorithm 1, one kernel per step, FP32 with FP64 alpha/beta) with its
+ * working vectors and root-of-unity table in one fixed 768 KiB array inside the library
+ * image.  Every GPU that loads the library holds that array until the process exits.
  *   Limits: M*N <= 4096, n_rx, n_tx <= 4, path taps ZOTFS_C64 with p_max <= 64; larger
  *   problems return ZOTFS_EUNSUPPORTED and nothing runs.
  *   paths:     host struct of dev pointers, lists [frame][rx][tx] as for zotfs_equalize.
  *   y_dd:      dev DD grids [n_frames][n_rx][MN] C64;  noise_var: dev float [n_frames].
- *   x_hat:     dev [n_frames][n_tx][MN] C64;  status: dev int32 [n_frames] or NULL.
- * The first call on a device looks up the array's device address; make that first call
- * outside any stream capture.  All calls share the one array and it keeps what the last
- * call left there (each call re-initialises everything it reads), so calls whose work can
- * overlap on the GPU -- on different streams, or from different threads -- race with each
- * other: keep them on one stream. */
+ *   x_hat:     dev [n_frames][n_tx][MN] C64;  status: dev int32 [n_frames] or NULL: per frame
+ *              ZOTFS_OK, ZOTFS_EINVAL (a count outside [0, p_max] or an offset outside the
+ *              centred range; such entries are dropped) or ZOTFS_ENONFINITE.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the one array -- vectors, path
+ * records, flags and the root-of-unity table, which each call rewrites -- and it keeps what
+ * the last call left there (each call re-initialises everything it reads), so calls whose
+ * work can overlap on the GPU -- on different streams, or from different threads -- race
+ * with each other: keep them on one stream. */
 zotfs_status zotfs_equalize_static(int M, int N, int n_rx, int n_tx, const zotfs_paths* paths, const float* y_dd,
                                    const float* noise_var, int iters, float* x_hat, int32_t* status, int n_frames,
                                    zotfs_stream stream);

@@ -146,3 +146,26 @@ def one_cta_plan(M, N, nrx, ntx, Q, **opts):
     plan = Plan(M, N, nrx, ntx, Q, **opts)
     plan.set_tuning(cluster=1)
     return plan
+
+
+def oracle_on_lists(lists, y_dd, lam, Q, iters, M, N, nrx, ntx, cg_eps=0.0):
+    """The FP64 oracle's CGA (Algorithm 1) and max-log demapper (Eq. demod) on one frame,
+    run with path lists the library produced (``lists`` in [rx][tx] order, each (dk, dl, h)
+    as stored).  Returns (x_hat, LLRs [n_tx*MN, bps])."""
+    from oracle import equalizer as eq, qam
+    grid = [[pathlist_from_lib(M, N, *lists[r * ntx + t]) for t in range(ntx)] for r in range(nrx)]
+    x = eq.cga(grid, y_dd, lam, iters, eps=cg_eps)
+    return x, qam.maxlog_llr(x, lam, Q)
+
+
+def hard_bit_mismatches(bits_packed, llr_ref, lam, Q):
+    """Hard bits (LSB-first packed bytes of one frame) differing from the oracle's decisions,
+    counted only where the oracle's LLR margin |LLR| lam exceeds 1e-4 d_min^2 (inside it
+    either decision is valid)."""
+    from oracle import qam
+    bits = np.unpackbits(np.asarray(bits_packed, np.uint8).reshape(-1), bitorder="little")
+    bref = qam.hard_bits_from_llr(llr_ref).reshape(-1)
+    dmin2 = (2 * qam.pam_levels(Q)[0]) ** 2
+    clear = np.abs(llr_ref.reshape(-1)) * lam > 1e-4 * dmin2
+    assert bits.size == bref.size
+    return int((bits[clear] != bref[clear]).sum())

@@ -31,8 +31,10 @@ def test_flops_per_frame_at_the_benchmark_shape(bench):
 
 
 def test_hbm_bytes_per_frame(bench):
-    """Pilot and data TD frames in (complex64), packed hard bits and the status word out."""
-    assert bench.hbm_bytes_per_frame() == 2 * 2048 * 8 + 2048 * 4 // 8 + 4 == 33796
+    """Pilot and data TD frames in (complex64), float32 LLRs (4 per 16-QAM symbol), packed hard
+    bits and the status word out; without LLRs only the bits and the status."""
+    assert bench.hbm_bytes_per_frame() == 2 * 2048 * 8 + 2048 * 4 * 4 + 2048 * 4 // 8 + 4 == 66564
+    assert bench.hbm_bytes_per_frame(llr=False) == 2 * 2048 * 8 + 2048 * 4 // 8 + 4 == 33796
 
 
 def test_profiled_traffic_needs_a_matching_kernel_hash(bench, monkeypatch):

@@ -1,8 +1,10 @@
 """GPU tests of the serving loop (zotfs_server_*): continuous batching of frames of mixed
-shapes, antenna counts and QAM orders.  Each served frame's results are bitwise those of the
-same frame run alone through zotfs_rx (and those match the FP64 oracle, see test_gpu_rx.py);
-memory-based admission holds frames back until released outputs make room; arrival, admission
-and completion times are consistent."""
+shapes, antenna counts and QAM orders.  Served frames of every class the server routes are
+checked against the FP64 oracle (path lists against its effective channel, LLRs and hard bits
+against its CGA and demapper run on the served lists); each served frame's results are also
+bitwise those of the same frame run alone through zotfs_rx; memory-based admission holds
+frames back until released outputs make room; arrival, admission and completion times are
+consistent."""
 
 import time
 
@@ -11,7 +13,9 @@ import pytest
 import torch
 
 import synth
-from tests.gpu_util import TOL_LLR, TOL_X, dev, served_plan, to_dev
+from oracle import ddchannel as dc, zak
+from tests.gpu_util import (TOL_LLR, TOL_X, check_path_list, dev, hard_bit_mismatches, oracle_on_lists,
+                             rel_l2, served_plan, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -90,6 +94,66 @@ def test_served_mix_equals_alone():
             assert np.array_equal(served["count"], alone["paths"].count.cpu().numpy()), i
             srv.release(i)
         assert srv.stats()["arena_in_use"] == 0
+    finally:
+        srv.close()
+
+
+# One frame of every class the server routes differently: SISO frames on one CTA's shared
+# memory and on the large-frame kernel (256 x 64, 256 x 32), MIMO frames that fit one CTA
+# (2x2 32x16, 4x4 64x16) and MIMO frames too large for it, which the server runs on 2-CTA
+# clusters (2x2 and 4x4 at 128x64); all three QAM orders; 8-path channels; two frames ask
+# for the CG stopping test.  (M, N, n_rx, n_tx, Q, SNR dB, cg_eps)
+ORACLE_CLASSES = [(64, 32, 1, 1, 16, 12, 0.0), (32, 16, 2, 2, 4, 25, 0.0), (64, 16, 4, 4, 64, 30, 0.0),
+                  (128, 64, 2, 2, 16, 20, 0.0), (128, 64, 4, 4, 64, 28, 0.0), (256, 64, 1, 1, 64, 30, 0.0),
+                  (256, 32, 1, 1, 4, 5, 0.0), (128, 32, 1, 1, 16, 18, 0.05), (64, 64, 2, 2, 16, 22, 0.05)]
+
+
+def test_served_frames_match_oracle():
+    """Every served class against the FP64 oracle: the served path lists are valid for the
+    oracle's effective channel (taps above the threshold listed, gains to FP32 accuracy), and
+    the oracle's CGA + max-log demapper run on exactly those lists give the served LLRs to
+    1e-3 relative L2 and the served hard bits wherever the decision is not within FP32
+    rounding of a boundary."""
+    from paper_2604_02266_gb300 import Server
+    frames = []
+    for i, (M, N, nrx, ntx, Q, snr, eps) in enumerate(ORACLE_CLASSES):
+        b = synth.fractional_batch(1, seed=7100 + i, M=M, N=N, Q=Q, n_rx=nrx, n_tx=ntx, n_paths=8, snr_db=(snr,))
+        frames.append(dict(M=M, N=N, nrx=nrx, ntx=ntx, Q=Q, eps=eps, b=b, yp=to_dev(b["y_pilot_td"][0]),
+                           yd=to_dev(b["y_data_td"][0]), iters=10))
+    srv = Server(p_max=64, max_wave_frames=4, waves_in_flight=3, keep_llr=True, arena_bytes=256 << 20, max_M=256,
+                 max_N=64, max_ant=4)
+    try:
+        reqs = [Server.request(i, fr["yp"], fr["yd"], fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"], fr["iters"],
+                               float(fr["b"]["noise_var"][0]), float(fr["b"]["theta"][0]), cg_eps=fr["eps"])
+                for i, fr in enumerate(frames)]
+        srv.submit(reqs[:4])
+        srv.submit(reqs[4:])  # while the first waves run
+        got = _drain(srv, len(frames))
+        for i, fr in enumerate(frames):
+            M, N, nrx, ntx, Q, b = fr["M"], fr["N"], fr["nrx"], fr["ntx"], fr["Q"], fr["b"]
+            assert got[i][0] in (0, 6), (i, got[i][0])
+            nl, bps, MN = nrx * ntx, int(np.log2(Q)), M * N
+            served = srv.read(i, ntx, MN, bps, nl, llr=True)
+            lam, theta = float(b["noise_var"][0]), float(b["theta"][0])
+            dk = served["dk"].reshape(nl, -1)
+            dl = served["dl"].reshape(nl, -1)
+            h = served["h"].reshape(nl, -1).astype(complex)
+            lists = []
+            for r in range(nrx):
+                for t in range(ntx):
+                    li = r * ntx + t
+                    P = int(served["count"][li])
+                    lst = (dk[li, :P].astype(int), dl[li, :P].astype(int), h[li, :P])
+                    heff = dc.heff_readoff(zak.dzt(b["y_pilot_td"][0, t, r].astype(complex), M, N), M // 2, N // 2,
+                                           b["a_pilot"])
+                    check_path_list(M, N, lst, heff, theta, 64)
+                    lists.append(lst)
+            y_dd = np.concatenate([zak.vec(zak.dzt(b["y_data_td"][0, r].astype(complex), M, N)) for r in range(nrx)])
+            _, llr_ref = oracle_on_lists(lists, y_dd, lam, Q, fr["iters"], M, N, nrx, ntx, cg_eps=fr["eps"])
+            err = rel_l2(served["llr"], llr_ref.reshape(-1))
+            assert err < TOL_LLR, (ORACLE_CLASSES[i], err)
+            assert hard_bit_mismatches(served["bits"], llr_ref, lam, Q) == 0, ORACLE_CLASSES[i]
+            srv.release(i)
     finally:
         srv.close()
 
