@@ -18,9 +18,11 @@ Modules, each citing the passage it follows:
   compute-aware CGA (Algorithm 1), direct LMMSE by Cholesky (Eq. lmmse), MIMO stacking
 * :mod:`oracle.qam`        -- Gray square QAM, hard demodulation (Eq. demod), max-log LLRs
 * :mod:`oracle.receiver`   -- the receiver stages composed per frame, as the GPU batch runs them
+* :mod:`oracle.mrc`        -- SS-MRC, the maximal-ratio-combining decision-feedback equaliser
+  (Sec. III-B "Equalization", MRC paragraph), in the delay-time domain
 
 Every function whose result is not pinned by a test against something other than
 itself says "parity unpinned" in its docstring; at present there is none.
 """
 
-from . import zak, ddchannel, equalizer, qam, receiver  # noqa: F401
+from . import zak, ddchannel, equalizer, qam, receiver, mrc  # noqa: F401

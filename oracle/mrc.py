@@ -98,6 +98,25 @@ def dt_apply(paths, V_dt):
     return out
 
 
+def combine_row(gk, D, x_row, dy):
+    """MRC of one symbol vector: x_row + D^-1 sum_d conj(G_d) dy[target_d] (DT domain);
+    entries no branch reaches keep x_row."""
+    g = np.zeros(len(x_row), np.complex128)
+    for G, kt, nt in gk:
+        g += np.conj(G) * dy[kt, nt]
+    c = np.asarray(x_row, np.complex128).copy()
+    ok = D > 0
+    c[ok] += g[ok] / D[ok]
+    return c
+
+
+def feed_back(gk, delta, dy):
+    """Decision feedback: remove a symbol vector's change from the residual of every branch
+    it reaches (dy updated in place)."""
+    for G, kt, nt in gk:
+        dy[kt, nt] -= G * delta
+
+
 def mrc(paths, y_dd_vec, iters, Q, return_decisions=False):
     """SS-MRC on one SISO frame.  y_dd_vec: DD grid vectorised q = l M + k.  Returns the soft
     estimate x_hat (vectorised like y) of the last iteration (and the decided points)."""
@@ -122,18 +141,11 @@ def mrc(paths, y_dd_vec, iters, Q, return_decisions=False):
     for _ in range(iters):
         for k in range(M):
             gk, D = gains[k]
-            g = np.zeros(N, np.complex128)
-            for G, kt, nt in gk:
-                g += np.conj(G) * dy[kt, nt]
-            c = x_dt[k].copy()
-            ok = D > 0
-            c[ok] += g[ok] / D[ok]
+            c = combine_row(gk, D, x_dt[k], dy)
             c_dd = dt_to_dd(c[None, :])[0]
             s = pts[np.argmin(np.abs(c_dd[:, None] - pts[None, :]) ** 2, axis=1)]
             new_dt = dd_to_dt(s[None, :])[0]
-            delta = new_dt - x_dt[k]
-            for G, kt, nt in gk:
-                dy[kt, nt] -= G * delta
+            feed_back(gk, new_dt - x_dt[k], dy)
             x_dt[k] = new_dt
             x_dec[k] = s
             soft[k] = c_dd
@@ -143,4 +155,4 @@ def mrc(paths, y_dd_vec, iters, Q, return_decisions=False):
     return x_hat
 
 
-__all__ = ["dd_to_dt", "dt_to_dd", "branches", "branch_gain", "dt_apply", "mrc"]
+__all__ = ["dd_to_dt", "dt_to_dd", "branches", "branch_gain", "dt_apply", "combine_row", "feed_back", "mrc"]

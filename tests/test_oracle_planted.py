@@ -217,3 +217,76 @@ def test_swapped_antenna_pairing_is_caught(monkeypatch):
         orig(self, [list(col) for col in zip(*grid)])
     monkeypatch.setattr(eq.StackedOperator, "__init__", transposed)
     assert _mimo_bit_errors(2, 2, 50) > 0
+
+
+# ------------------------------------------------------------------- SS-MRC (oracle/mrc.py)
+
+def _mrc_pins_ok():
+    """The SS-MRC pins of tests/test_oracle_mrc.py on one case each."""
+    from oracle import mrc
+    from tests import test_oracle_mrc as T
+    g = np.random.default_rng(7)
+    M, N = 16, 8
+    pl = T._paths(g, M, N, 6, edge=True)
+    H = dc.dense_H(dc.heff_from_paths(pl), M // 2, N // 2)
+    V = g.standard_normal((M, N)) + 1j * g.standard_normal((M, N))
+    op_ok = np.abs(mrc.dt_to_dd(mrc.dt_apply(pl, mrc.dd_to_dt(V))) - zak.unvec(H @ zak.vec(V), M, N)).max() < 1e-12
+    pl2 = T._paths(g, M, N, 6, edge=False)
+    H2 = dc.dense_H(dc.heff_from_paths(pl2), M // 2, N // 2)
+    x_tx = qam.constellation(4)[g.integers(0, 4, M * N)]
+    y = H2 @ x_tx + 0.05 * (g.standard_normal(M * N) + 1j * g.standard_normal(M * N))
+    soft, dec = mrc.mrc(pl2, y, 2, 4, return_decisions=True)
+    soft_ref, dec_ref = T._dense_gauss_seidel_ls(H2, y, M, N, 2, 4)
+    ls_ok = np.abs(soft - soft_ref).max() < 1e-9 and np.array_equal(dec, dec_ref)
+    return bool(op_ok), bool(ls_ok)
+
+
+def test_mrc_pins_pass_unmodified():
+    assert _mrc_pins_ok() == (True, True)
+
+
+def test_mrc_wrong_time_shift_is_caught(monkeypatch):
+    from oracle import mrc
+    orig = mrc.branch_gain
+
+    def bad(paths_d, k, d, M, N):
+        G, kt, f = orig(paths_d, k, d, M, N)
+        return G, kt, -f  # the wrap into the previous time block taken the wrong way
+    monkeypatch.setattr(mrc, "branch_gain", bad)
+    assert _mrc_pins_ok() == (False, False)
+
+
+def test_mrc_dropped_wrap_in_gain_phase_is_caught(monkeypatch):
+    from oracle import mrc
+
+    def bad(paths_d, k, d, M, N):
+        hs, ls = paths_d
+        kt, f = (k + d) % M, (k + d) // M
+        n = np.arange(N)
+        G = np.zeros(N, complex)
+        for h, l in zip(hs, ls):
+            G += h * np.exp(2j * np.pi * np.mod(l * (kt - d + n * M), M * N) / (M * N))  # f M term dropped
+        return G, kt, f
+    monkeypatch.setattr(mrc, "branch_gain", bad)
+    assert not _mrc_pins_ok()[0]
+
+
+def test_mrc_missing_conjugate_in_combining_is_caught(monkeypatch):
+    from oracle import mrc
+
+    def bad(gk, D, x_row, dy):
+        g = np.zeros(len(x_row), complex)
+        for G, kt, nt in gk:
+            g += G * dy[kt, nt]
+        c = np.asarray(x_row, complex).copy()
+        ok = D > 0
+        c[ok] += g[ok] / D[ok]
+        return c
+    monkeypatch.setattr(mrc, "combine_row", bad)
+    assert _mrc_pins_ok()[1] is False
+
+
+def test_mrc_dropped_decision_feedback_is_caught(monkeypatch):
+    from oracle import mrc
+    monkeypatch.setattr(mrc, "feed_back", lambda gk, delta, dy: None)
+    assert _mrc_pins_ok()[1] is False
