@@ -211,6 +211,29 @@ zotfs_status zotfs_equalize(zotfs_plan plan, const void* y, int y_is_dd, const z
                             const float* noise_var, int iters, float* x_hat, int n_frames,
                             int32_t* status, zotfs_stream stream);
 
+/* SS-MRC equalisation (Sec. III-B "Equalization", the maximal-ratio-combining paragraph; SS-MRC
+ * of the evaluation): the decision-feedback MRC equaliser on the structured-sparse path list.
+ * Per iteration the delay bins k = 0 .. M-1 are visited in order; the symbol vector of bin k
+ * (all N Doppler bins) collects its components from every delay branch (the paths of one
+ * delay offset) of the residual y - H x_hat, with the current estimates of the other vectors
+ * cancelled, combines them with the conjugate branch gains normalised by their total power,
+ * and is decided to the nearest points of the plan's QAM (Eq. demod), which are fed back into
+ * the residual.  The combining runs on the delay-time grid (the DD grid's Doppler axis taken
+ * back to time), where every branch is a diagonal gain and a cyclic time shift.  No noise
+ * term enters (maximal ratio); `iters` sweeps, iters = 0 returns x_hat = 0.
+ * x_hat receives the soft estimate of the last sweep (before the decision), which
+ * zotfs_demap turns into LLRs and hard bits.  One warp per frame, FP32.
+ *   Plans: SISO, FP32, separate pilot frames, M <= 256, M*N <= 16384, p_max <= 256, else
+ *   ZOTFS_EUNSUPPORTED.
+ *   y:      dev data frames, TD [n_frames][MN] in the plan's in_dtype when y_is_dd == 0, else
+ *           DD [n_frames][MN] C64.
+ *   paths:  host struct of dev pointers, one list per frame (as for zotfs_equalize).
+ *   x_hat:  dev [n_frames][MN] C64 (may be NULL).  status: dev int32 [n_frames] or NULL:
+ *           ZOTFS_OK, ZOTFS_EINVAL (bad count or offset; such entries are dropped) or
+ *           ZOTFS_ENONFINITE. */
+zotfs_status zotfs_equalize_mrc(zotfs_plan plan, const void* y, int y_is_dd, const zotfs_paths* paths, int iters,
+                                float* x_hat, int32_t* status, int n_frames, zotfs_stream stream);
+
 /* Demapping (Eq. demod extended to soft output): per bit j the max-log LLR
  * (min_{s: b_j=1} |x-s|^2 - min_{s: b_j=0} |x-s|^2) / noise_var[f] over the plan's Gray
  * square QAM with unit mean energy, and the hard bit (LLR < 0).  llr (dev float

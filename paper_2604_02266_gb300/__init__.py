@@ -185,6 +185,16 @@ class Plan:
                                  n_frames, _p(status), _s(stream)))
         return x_hat
 
+    def equalize_mrc(self, y, paths, iters, n_frames, y_is_dd=False, x_hat=None, status=None, stream=None):
+        """SS-MRC (zotfs_equalize_mrc): decision-feedback maximal-ratio combining on the path
+        lists; returns the soft estimate of the last sweep."""
+        x_hat = (torch.empty(n_frames, 1, self.MN, dtype=torch.complex64, device=y.device)
+                 if x_hat is None else x_hat)
+        _need_cuda(y, x_hat, status)
+        Z.check(Z.zotfs_equalize_mrc(self._h, _p(y), int(bool(y_is_dd)), paths.c, iters, _p(x_hat), _p(status),
+                                     n_frames, _s(stream)))
+        return x_hat
+
     def demap(self, x_hat, noise_var, n_frames, llr=True, bits=True, stream=None):
         dev = x_hat.device
         L = torch.empty(n_frames, self.n_tx, self.MN, self.bps, dtype=torch.float32, device=dev) if llr else None

@@ -35,7 +35,8 @@ def _units():
              ("batch.cu", [], "batch.o"), ("big_variant.cu", [], "big_variant.o"),
              ("server.cu", [], "server.o"), ("tune.cu", [], "tune.o"),
              ("cluster_variant.cu", [], "cluster_variant.o"),
-             ("big_cluster_variant.cu", [], "big_cluster_variant.o"), ("grid_variant.cu", [], "grid_variant.o")]
+             ("big_cluster_variant.cu", [], "big_cluster_variant.o"), ("grid_variant.cu", [], "grid_variant.o"),
+             ("mrc.cu", [], "mrc.o")]
     for i in range(N_VARIANTS):
         units.append(("frame_variant.cu", [f"-DZOTFS_VARIANT={i}"], f"frame_v{i}.o"))
     return units
