@@ -954,6 +954,147 @@ def impl_iterations(args):
     return 0
 
 
+# ------------------------------------------------------------------ BER vs SNR workload
+
+def unpack_bits(packed, n_frames):
+    """Packed hard bits (uint8, LSB first, as the library writes them) -> [n_frames, bits] 0/1."""
+    a = np.asarray(packed, np.uint8).reshape(n_frames, -1)
+    return np.unpackbits(a, axis=1, bitorder="little")
+
+
+def bit_errors(packed, tx_bits, n_frames):
+    """Bit errors per frame between the library's packed hard bits and the transmitted bits."""
+    got = unpack_bits(packed, n_frames)
+    ref = np.asarray(tx_bits, np.uint8).reshape(n_frames, -1)
+    return (got != ref).sum(axis=1)
+
+
+def _lmmse_bits(y_data_td, dk, dl, h, M, N, Q, lam):
+    """Worker: the oracle's direct LMMSE (Eq. lmmse, dense Eq. Hdd from the given path list,
+    Cholesky) on one SISO frame, and its hard bits (Eq. demod)."""
+    from oracle import ddchannel as dc, equalizer as eq, qam, zak
+    pl = dc.PathList.from_offsets(M, N, M // 2, N // 2, np.asarray(h, complex), dk, dl)
+    H = dc.dense_H(dc.heff_from_paths(pl), M // 2, N // 2)
+    y = zak.vec(zak.dzt(np.asarray(y_data_td, complex), M, N))
+    x = eq.lmmse_direct(H, y, lam)
+    return qam.hard_demod(x, Q)[1].reshape(-1).astype(np.uint8)
+
+
+def ber_claims(rows, factor=2.0, min_errors=20, sigmas=3.0):
+    """The paper's qualitative BER claims (SS-CGA matches LMMSE and beats SS-MRC) checked on
+    the sweep's rows.  Ratios SS-CGA / LMMSE use only points where the pair rests on at least
+    `min_errors` bit errors; "SS-CGA at or below SS-MRC" holds at a point unless SS-CGA's BER
+    exceeds SS-MRC's by more than `sigmas` binomial standard deviations of the difference."""
+    out = {"factor": factor, "sigmas": sigmas}
+    for key in ("cga", "cga20"):
+        ratios = [r[f"ber_{key}"] / r["ber_lmmse"] for r in rows
+                  if min(r[f"ber_{key}"], r["ber_lmmse"]) * r["bits"] >= min_errors]
+        out[f"worst_ratio_{key}_lmmse"] = max(ratios) if ratios else None
+        out[f"{key}_within_factor_of_lmmse"] = (max(ratios) <= factor) if ratios else None
+        out[f"{key}_points_compared"] = len(ratios)
+    worse = []
+    for r in rows:
+        pc, pm, nb = r["ber_cga"], r["ber_mrc"], r["bits"]
+        sd = np.sqrt((pc * (1 - pc) + pm * (1 - pm)) / nb)
+        if pc - pm > sigmas * sd and (pc - pm) * nb >= 1:
+            worse.append({k: r[k] for k in ("M", "N", "qam", "snr_db")})
+    out["cga_at_or_below_mrc"] = not worse
+    out["cga_worse_than_mrc_at"] = worse
+    return out
+
+
+def impl_ber(args):
+    """BER against SNR on Veh-A frames (Sec. VI's BER study; Table vehAProf): the library's
+    SS-CGA (Algorithm 1) and SS-MRC, 10 iterations each as in the paper (and SS-CGA at 20), and
+    the FP64 oracle's direct LMMSE (dense Eq. Hdd, Cholesky) on the same estimated path lists,
+    QPSK and 16-QAM, grids 32x32 and 128x32.  Also the equalisers' throughput on 1024 frames of
+    64x32 16-QAM with given lists."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    cores = host_cores()
+    pool = OraclePool(cores)  # spawned workers for the LMMSE leg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Plan
+    rows = []
+    t0 = time.time()
+    try:
+        for (m, n, frames) in ((32, 32, args.ber_frames), (128, 32, args.ber_frames_large)):
+            for q in (4, 16):
+                plan = Plan(m, n, 1, 1, q)
+                for snr in range(0, 31, 5):
+                    b = synth.veh_a_batch(frames, SEED + 7 * m + q + snr, M=m, N=n, Q=q, snr_db=(snr,))
+                    yp, yd = torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev)
+                    nv, th = torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev)
+                    paths = plan.estimate(yp, th, frames)
+                    res = {}
+                    for name, it in (("cga", 10), ("cga20", 20)):
+                        x = plan.equalize(yd, paths, nv, it, frames)
+                        _, bits = plan.demap(x, nv, frames, llr=False)
+                        res[name] = int(bit_errors(bits.cpu().numpy(), b["bits"], frames).sum())
+                    x = plan.equalize_mrc(yd, paths, 10, frames)
+                    _, bits = plan.demap(x, nv, frames, llr=False)
+                    res["mrc"] = int(bit_errors(bits.cpu().numpy(), b["bits"], frames).sum())
+                    lists = paths.to_host()
+                    futs = [pool.ex.submit(_lmmse_bits, b["y_data_td"][f, 0], lists[f][0], lists[f][1], lists[f][2], m,
+                                           n, q, float(b["noise_var"][f])) for f in range(frames)]
+                    lm = np.stack([fu.result() for fu in futs])
+                    res["lmmse"] = int((lm != b["bits"].reshape(frames, -1)).sum())
+                    nbits = int(b["bits"].size)
+                    rows.append({"M": m, "N": n, "qam": q, "snr_db": snr, "frames": frames, "bits": nbits,
+                                 "paths_mean": float(paths.count.float().mean().item()),
+                                 "ber_cga": res["cga"] / nbits, "ber_cga20": res["cga20"] / nbits,
+                                 "ber_mrc": res["mrc"] / nbits, "ber_lmmse": res["lmmse"] / nbits})
+    finally:
+        pool.close()
+    sweep_s = time.time() - t0
+
+    # equaliser throughput with given lists: 1024 frames of 64x32 16-QAM, 10 iterations
+    F = FRAMES
+    b = synth.fractional_batch(F, seed=SEED + 5, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    yd, nv = torch.from_numpy(b["y_data_td"]).to(dev), torch.from_numpy(b["noise_var"]).to(dev)
+    paths = plan.estimate(torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["theta"]).to(dev), F)
+    x = torch.empty(F, 1, M * N, dtype=torch.complex64, device=dev)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_cga = timed(lambda: plan.equalize(yd, paths, nv, ITERS, F, x_hat=x))
+    ms_mrc = timed(lambda: plan.equalize_mrc(yd, paths, ITERS, F, x_hat=x))
+    claims = ber_claims(rows)
+    line = {"metric": "BER vs SNR: SS-CGA, SS-MRC and LMMSE on Veh-A frames",
+            "value": claims["worst_ratio_cga20_lmmse"], "unit": "worst BER ratio SS-CGA (20 iterations) / LMMSE",
+            "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (LMMSE: f64 oracle)", "data": "synthetic",
+            "config": {"workload": "Veh-A frames (Table vehAProf delays and powers, nu_max 100 Hz, delta_f 30 kHz), "
+                                   "separate pilot frame per frame, threshold 3 sigma, p_max 64, SNR 0..30 dB step 5, "
+                                   "QPSK and 16-QAM; grids 32x32 and 128x32; 10 iterations (SS-CGA also 20); "
+                                   "LMMSE = the FP64 oracle's dense Cholesky solve on the library's path lists",
+                       "frames_32x32": args.ber_frames, "frames_128x32": args.ber_frames_large},
+            "claims": claims, "rows": rows, "sweep_wall_s": sweep_s, "host_cores": cores,
+            "equalizer_throughput": {"workload": f"{F} frames 64x32 16-QAM, given path lists (mean P "
+                                                 f"{float(paths.count.float().mean().item()):.1f}), {ITERS} iterations",
+                                     "ss_cga_frames_s": F / ms_cga * 1e3, "ss_mrc_frames_s": F / ms_mrc * 1e3,
+                                     "ss_cga_ms": ms_cga, "ss_mrc_ms": ms_mrc}}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------- paper-scale workload
 
 PAPER_M, PAPER_N = 16384, 32
@@ -977,6 +1118,8 @@ def impl_paper(args):
     M, N, pool = PAPER_M, PAPER_N, args.paper_pool
     b = synth.fractional_batch(pool, seed=SEED + 16384, M=M, N=N, Q=Q, snr_db=tuple(range(0, 31, 2)))
     plan = Plan(M, N, 1, 1, Q)
+    if args.ctas:
+        plan.set_tuning(ctas_per_sm=args.ctas)
     yp, yd = torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["y_data_td"]).to(dev)
     nv, th = torch.from_numpy(b["noise_var"]).to(dev), torch.from_numpy(b["theta"]).to(dev)
     outs = plan._rx_outputs(1, dev, True, False, False)
@@ -1093,7 +1236,7 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=24, help="oracle sample per host core for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=4, help="oracle frames per host core per step (--impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper", "packets", "iterations"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper", "packets", "iterations", "ber"],
                     help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
                          "mixed: the uneven FP16/BF16 batch under CUDA graphs; mimo: 4x4 128x64 64-QAM frames; "
                          "latency: one frame per call; paper: one 16384x32 packet per call on the grid receiver; "
@@ -1105,6 +1248,8 @@ def main():
     ap.add_argument("--packet-data", type=int, default=8, help="packets: data frames per pilot frame")
     ap.add_argument("--iter-frames", type=int, default=32, help="iterations: Veh-A frames per (grid, SNR)")
     ap.add_argument("--iter-max", type=int, default=30, help="iterations: CG iterations profiled")
+    ap.add_argument("--ber-frames", type=int, default=32, help="ber: Veh-A frames per 32x32 point")
+    ap.add_argument("--ber-frames-large", type=int, default=8, help="ber: Veh-A frames per 128x32 point")
     ap.add_argument("--paper-pool", type=int, default=8, help="paper: synthetic packets cycled through")
     ap.add_argument("--mixed-steps", type=int, default=20, help="mixed: timed steps per storage type")
     ap.add_argument("--tune-frames", type=int, default=64, help="mixed: frames per shape group the autotuner times")
@@ -1140,6 +1285,8 @@ def main():
         return impl_iterations(args)
     if args.workload == "latency":
         return impl_latency(args)
+    if args.workload == "ber":
+        return impl_ber(args)
     return impl_zotfs(args)
 
 

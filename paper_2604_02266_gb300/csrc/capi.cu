@@ -324,7 +324,7 @@ static zotfs_status launch_kernels(zotfs_plan_s* plan, int nrx, int ntx, FrameAr
       return ZOTFS_EUNSUPPORTED;
     }
     GridCfg gc;
-    cudaError_t e = choose_grid_cfg(plan->M, plan->N, plan->opt.p_max, plan->sm_count, gc);
+    cudaError_t e = choose_grid_cfg(plan->M, plan->N, plan->opt.p_max, plan->sm_count, plan->tune.ctas_per_sm, gc);
     if (e != cudaSuccess) return cuda_fail(e, "grid receiver configuration");
     if (grid_scratch_size(plan->M, plan->N, plan->opt.p_max, gc.grid) > plan->grid_bytes) {
       set_error("grid receiver scratch too small");
@@ -483,8 +483,8 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
   if (e == cudaSuccess) e = dev_alloc(&p->d_order, sizeof(int) * kOrderCap * kOrderSlots);
   if (e == cudaSuccess && p->plain_bytes) e = dev_alloc(&p->d_plain, p->plain_bytes);
   if (e == cudaSuccess && paper_scale) {
-    // scratch for the largest grid the receiver launches (two CTAs per SM) and p_max 256
-    p->grid_bytes = grid_scratch_size(M, N, 256, 2 * p->sm_count);
+    // scratch for the largest grid the receiver launches (kGridMaxCtasPerSm CTAs per SM) and p_max 256
+    p->grid_bytes = grid_scratch_size(M, N, 256, kGridMaxCtasPerSm * p->sm_count);
     e = dev_alloc(&p->d_grid, p->grid_bytes);
   }
   {

@@ -200,6 +200,9 @@ __host__ __device__ __forceinline__ size_t frame_smem_bytes(int M, int N, int E,
 
 constexpr uint32_t kMaxPolls = 1u << 22;
 
+// Most CTAs per SM the paper-scale grid receiver launches (its scratch holds their partials).
+constexpr int kGridMaxCtasPerSm = 2;
+
 // ------------------------------------------------------------------ staging + DZT
 
 // Copy one TD grid (MN complex of `dtype`) into dst[0, MN) as complex R by a bulk async

@@ -16,16 +16,15 @@
 namespace zotfs {
 
 constexpr int kGridThreads = 256;
-constexpr int kGridE = 8;         // rows per work item: column k, rows j0 .. j0 + 7
+constexpr int kGridE = 8;         // most rows per work item (column k, rows j0 .. j0 + E - 1): sizes the scratch
 constexpr int kGridDftCols = 32;  // delay columns per Zak-transform tile
 constexpr uint32_t kGridMaxPolls = 1u << 22;
 
 constexpr int kGridMaxCtas = 1024;
 
 struct GridBarrier {
-  unsigned count;  // CTAs arrived at the current barrier
-  unsigned gen;    // barriers completed
-  int err;         // a wait gave up: every CTA leaves at its next barrier
+  unsigned long long count;  // CTA arrivals since the launch began (zeroed before each launch)
+  int err;                   // a wait gave up: every CTA leaves at its next barrier
   int pad;
 };
 
@@ -86,16 +85,21 @@ __host__ __device__ __forceinline__ GridScratch grid_scratch_carve(char* base, i
   return G;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Barrier over all CTAs of the cooperative grid (co-resident by construction of the launch).
-// Every thread counts the barriers passed in `gen`.  Returns false in every thread of the CTA
-// when this wait or an earlier one gave up (bounded polls): the caller abandons the frame.
-// (Arrivals on per-CTA flags gathered by one warp were measured slower than one counter.)
+// The arrival counter only grows: barrier g (0-based, counted per thread in `gen`) is complete
+// once it holds (g + 1) gridDim.x arrivals, so an arriving CTA adds one with a release
+// reduction (no round trip, no reset by a last arriver) and polls with acquire loads.
+// Returns false in every thread of the CTA when this wait or an earlier one gave up (bounded
+// polls): the caller abandons the frame.
 __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, uint32_t max_polls = kGridMaxPolls) {
   __syncthreads();
   const unsigned g = gen;
@@ -105,21 +109,16 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, uint32_
     if (*reinterpret_cast<volatile int*>(&b->err) != 0) {
       ok = 0;
     } else {
-      __threadfence();
-      if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-        atomicExch(&b->count, 0u);
-        __threadfence();
-        atomicExch(&b->gen, g + 1);
-      } else {
-        uint32_t polls = 0;
-        while (ld_acquire_gpu(&b->gen) == g) {
-          if (++polls > max_polls) {
-            atomicExch(&b->err, 1);
-            ok = 0;
-            break;
-          }
-          __nanosleep(32);
+      red_release_gpu_add(&b->count, 1ull);
+      const unsigned long long target = (unsigned long long)(g + 1) * gridDim.x;
+      uint32_t polls = 0;
+      while (ld_acquire_gpu_u64(&b->count) < target) {
+        if (++polls > max_polls) {
+          atomicExch(&b->err, 1);
+          ok = 0;
+          break;
         }
+        __nanosleep(32);
       }
       __threadfence();
     }
@@ -127,12 +126,33 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, uint32_
   return __syncthreads_and(ok) != 0;
 }
 
+// Store DD value v of (delay k, Doppler l) into a row-major quasi-periodic extension (element
+// (A, r) at r 2M + A + M/2, rows N + E + 3): the main column, the halo column with its
+// quasi-periodic phase, and the periodic halo rows -- what write_ext<R, E, true> stores for one
+// element.
+template <int E>
+__device__ __forceinline__ void ext_store_rm(float2* ext, const FrameArgs& A, int k, int l, float2 v) {
+  const int M = A.M, N = A.N, Hk = M >> 1, MN = M * N;
+  const bool low = k < Hk;
+  const int mc = k + Hk, hc = (low ? k + M : k - M) + Hk;
+  const int widx = low ? (l << A.logM) : ((MN - (l << A.logM)) & (MN - 1));
+  const float2 hv = cmul(v, tw<float>(A, widx));
+  for (int r = l; r < N + E + 3; r += N) {
+    ext[(size_t)r * 2 * M + mc] = v;
+    ext[(size_t)r * 2 * M + hc] = hv;
+  }
+}
+
 // Y[l M + k] = N^-1/2 sum_n y[k + n M] W_N^{-n l} (Eq. zak) for all columns: tiles of
-// kGridDftCols columns over all N rows staged in shared memory (coalesced along k), then one
-// direct N-point DFT per output.  `tile` holds N kGridDftCols values, `wn` N twiddles.
-__device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, const FrameArgs& A, float2* tile,
-                                         float2* wn) {
-  const int M = A.M, N = A.N, logM = A.logM;
+// kGridDftCols columns over all N rows staged in shared memory (coalesced along k), an
+// in-place radix-2 decimation-in-frequency FFT along n per column (log2 N stages of N/2
+// butterflies), and the outputs read back from bit-reversed rows.  The result goes to Y
+// (q = l M + k) and/or straight into a row-major quasi-periodic extension `ext` (E rows per
+// item), either may be NULL.  `tile` holds N kGridDftCols values, `wn` N twiddles.
+template <int E>
+__device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, float2* ext, const FrameArgs& A,
+                                         float2* tile, float2* wn) {
+  const int M = A.M, N = A.N, logM = A.logM, logN = A.logN;
   for (int i = threadIdx.x; i < N; i += blockDim.x) wn[i] = conjf2(tw<float>(A, (size_t)i << logM));
   const float s = (float)A.inv_sqrtN;
   const int ntiles = M / kGridDftCols;
@@ -144,15 +164,24 @@ __device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, 
       tile[e] = load_complex<float2>(src, (size_t)n * M + k0 + kk, dtype);
     }
     __syncthreads();
+    for (int h = N >> 1; h >= 1; h >>= 1) {
+      const int tws = N / (2 * h);
+      for (int b = threadIdx.x; b < (N >> 1) * kGridDftCols; b += blockDim.x) {
+        const int kk = b & (kGridDftCols - 1), g = b / kGridDftCols;
+        const int gi = g & (h - 1);
+        const int n = ((g - gi) << 1) + gi;
+        float2* p0 = tile + n * kGridDftCols + kk;
+        const float2 u = p0[0], v = p0[h * kGridDftCols];
+        p0[0] = cadd(u, v);
+        p0[h * kGridDftCols] = cmul(csub(u, v), wn[gi * tws]);
+      }
+      __syncthreads();
+    }
     for (int e = threadIdx.x; e < N * kGridDftCols; e += blockDim.x) {
       const int l = e / kGridDftCols, kk = e - l * kGridDftCols;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int n = 0; n < N; ++n) {
-        const float2 w = wn[(n * l) & (N - 1)], v = tile[n * kGridDftCols + kk];
-        acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
-        acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
-      }
-      Y[(size_t)l * M + k0 + kk] = cscale(acc, s);
+      const float2 v = cscale(tile[bitrev(l, logN) * kGridDftCols + kk], s);
+      if (Y) Y[(size_t)l * M + k0 + kk] = v;
+      if (ext) ext_store_rm<E>(ext, A, k0 + kk, l, v);
     }
     __syncthreads();
   }
@@ -194,13 +223,14 @@ __device__ __forceinline__ void grid_prefix(const int* counts, SharedHdr* S) {
   __syncthreads();
 }
 
-template <int EQ>
-__global__ void __launch_bounds__(kGridThreads, 2)
+// EQ: pilot-grid entries per thread in the read-off; E: rows per CG work item (column k, rows
+// j0 .. j0 + E - 1); MINB: CTAs per SM the launch bounds are set for.
+template <int EQ, int E, int MINB>
+__global__ void __launch_bounds__(kGridThreads, MINB)
     grid_kernel(const __grid_constant__ FrameArgs A, GridScratch G) {
   using R = float;
   using C = float2;
   using PathRec = PathRecT<R>;
-  constexpr int E = kGridE;
   extern __shared__ __align__(128) unsigned char smem[];
   SharedHdr* S = reinterpret_cast<SharedHdr*>(smem);
   size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
@@ -236,7 +266,7 @@ __global__ void __launch_bounds__(kGridThreads, 2)
 
     // ------------------------------------------------ Zak transform only
     if (A.mode & kDzt) {
-      grid_dzt(io.y_data, A.in_dtype, reinterpret_cast<C*>(io.u_out), A, tile, wn);
+      grid_dzt<E>(io.y_data, A.in_dtype, reinterpret_cast<C*>(io.u_out), nullptr, A, tile, wn);
       if (!grid_sync(G.bar, gen)) return fail(io);
       if (blockIdx.x == 0 && tid == 0 && io.status) *io.status = ZOTFS_OK;
       continue;
@@ -245,7 +275,7 @@ __global__ void __launch_bounds__(kGridThreads, 2)
     // ------------------------------------------------ path list
     int P = 0;
     if (A.mode & kEstimate) {
-      grid_dzt(io.y_pilot, A.in_dtype, G.Y, A, tile, wn);
+      grid_dzt<E>(io.y_pilot, A.in_dtype, G.Y, nullptr, A, tile, wn);
       if (!grid_sync(G.bar, gen)) return fail(io);
       // read-off: thread g owns q in [g EQ, g EQ + EQ) (Eq. heff_hadamard over the pilot grid)
       const R scale = (R)(1.0 / io.a_pilot);
@@ -437,17 +467,17 @@ __global__ void __launch_bounds__(kGridThreads, 2)
     // ------------------------------------------------ equalisation (Algorithm 1)
     if (A.mode & kCG) {
       const R lam = (R)io.lam;
-      const C* Yd = reinterpret_cast<const C*>(io.y_data);
       if (!A.y_is_dd) {
-        grid_dzt(io.y_data, A.in_dtype, G.Y, A, tile, wn);
-        if (!grid_sync(G.bar, gen)) return fail(io);
-        Yd = G.Y;
-      }
-      for (int it = gtid; it < items; it += nthr) {
-        const int k = it & (M - 1), j0 = (it >> logM) * E;
+        // the data frame's Zak transform writes the extension of y directly
+        grid_dzt<E>(io.y_data, A.in_dtype, nullptr, G.extT, A, tile, wn);
+      } else {
+        const C* Yd = reinterpret_cast<const C*>(io.y_data);
+        for (int it = gtid; it < items; it += nthr) {
+          const int k = it & (M - 1), j0 = (it >> logM) * E;
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = Yd[(size_t)(j0 + i) * M + k];
-        write_ext<R, E, true>(G.extT, A, k, j0, v);
+          for (int i = 0; i < E; ++i) v[i] = Yd[(size_t)(j0 + i) * M + k];
+          write_ext<R, E, true>(G.extT, A, k, j0, v);
+        }
       }
       if (!grid_sync(G.bar, gen)) return fail(io);
 

@@ -10,26 +10,28 @@ namespace {
 
 using GridKern = void (*)(const FrameArgs, GridScratch);
 
-GridKern kern_of(int EQ) {
-  switch (EQ) {
-    case 8: return grid_kernel<8>;
-    case 16: return grid_kernel<16>;
-    case 32: return grid_kernel<32>;
-    default: return nullptr;
-  }
-}
+// Instantiations: (read-off entries per thread EQ, CG rows per item E, CTAs per SM MINB).
+// Items of 4 rows at three CTAs per SM were measured slower than 8 rows at two (0.86 against
+// 0.56 ms per 16384 x 32 packet: the per-path work of a gather is amortised over half the rows,
+// and 80 registers spill), so every variant takes 8-row items.
+struct GridVariant {
+  int EQ, E, minb;
+  GridKern k;
+};
+const GridVariant kGridVariants[] = {
+    {8, 8, 2, grid_kernel<8, 8, 2>}, {16, 8, 2, grid_kernel<16, 8, 2>}, {32, 8, 2, grid_kernel<32, 8, 2>}};
+constexpr int kNumGridVariants = sizeof(kGridVariants) / sizeof(kGridVariants[0]);
 
-cudaError_t grant(int EQ, size_t smem) {
+cudaError_t grant(int v, size_t smem) {
   static std::mutex mu;
-  static int granted[3][64] = {{0}};
+  static int granted[kNumGridVariants][64] = {{0}};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const int slot = EQ == 8 ? 0 : (EQ == 16 ? 1 : 2);
   std::lock_guard<std::mutex> lk(mu);
-  if (dev < 64 && granted[slot][dev] >= (int)smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(kern_of(EQ), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && dev < 64) granted[slot][dev] = (int)smem;
+  if (dev < 64 && granted[v][dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kGridVariants[v].k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev < 64) granted[v][dev] = (int)smem;
   return e;
 }
 
@@ -73,22 +75,27 @@ bool grid_shape(int M, int N, int nrx, int ntx) {
          N <= 64 && (size_t)M * N <= kGridMaxElems;
 }
 
-cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, GridCfg& cfg) {
+cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, int ctas_per_sm, GridCfg& cfg) {
   cfg.smem = grid_smem_bytes(N, p_max);
   cfg.T = kGridThreads;
   cfg.EQ = 0;
-  for (int EQ : {8, 16, 32}) {
-    cudaError_t e = grant(EQ, cfg.smem);
+  for (int v = 0; v < kNumGridVariants; ++v) {
+    const GridVariant& gv = kGridVariants[v];
+    cudaError_t e = grant(v, cfg.smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern_of(EQ), kGridThreads, cfg.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gv.k, kGridThreads, cfg.smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) continue;
-    if (occ > 2) occ = 2;  // the plan's scratch holds partials for two CTAs per SM
+    if (occ > gv.minb) occ = gv.minb;
+    if (ctas_per_sm > 0 && occ > ctas_per_sm) occ = ctas_per_sm;
+    if (occ > kGridMaxCtasPerSm) occ = kGridMaxCtasPerSm;  // the plan's scratch holds partials for that many
     const int grid = occ * sm_count;
     if (grid > kGridMaxCtas) return cudaErrorInvalidConfiguration;
-    if ((long long)grid * kGridThreads * EQ >= (long long)M * N) {
-      cfg.EQ = EQ;
+    if ((long long)grid * kGridThreads * gv.EQ >= (long long)M * N) {
+      cfg.EQ = gv.EQ;
+      cfg.E = gv.E;
+      cfg.variant = v;
       cfg.grid = grid;
       return cudaSuccess;
     }
@@ -99,9 +106,9 @@ cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, GridCfg& cfg)
 size_t grid_scratch_size(int M, int N, int p_max, int grid) { return grid_scratch_bytes(M, N, p_max, grid); }
 
 cudaError_t grid_launch(const GridCfg& cfg, const FrameArgs& A, char* scratch, cudaStream_t stream) {
-  GridKern k = kern_of(cfg.EQ);
-  if (!k) return cudaErrorInvalidValue;
-  cudaError_t e = grant(cfg.EQ, cfg.smem);
+  if (cfg.variant < 0 || cfg.variant >= kNumGridVariants) return cudaErrorInvalidValue;
+  GridKern k = kGridVariants[cfg.variant].k;
+  cudaError_t e = grant(cfg.variant, cfg.smem);
   if (e != cudaSuccess) return e;
   GridScratch G = grid_scratch_carve(scratch, A.M, A.N, A.p_max, cfg.grid);
   e = cudaMemsetAsync(G.bar, 0, sizeof(GridBarrier), stream);

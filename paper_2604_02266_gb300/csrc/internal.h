@@ -135,11 +135,13 @@ int big_cluster_count(const BigClusterCfg& cfg, int max_active, int sm_count, in
 // cooperative launch whose CTAs meet at grid barriers; frames with M > 256 or M N > 16384.
 constexpr size_t kGridMaxElems = (size_t)1 << 19;  // M N up to 524288 (16384 x 32)
 struct GridCfg {
-  int T, EQ, grid;
+  int T, EQ, E, grid, variant;
   size_t smem;
 };
 bool grid_shape(int M, int N, int nrx, int ntx);
-cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, GridCfg& cfg);
+// ctas_per_sm: the plan's tuning, CTAs per SM of the cooperative launch (0: as many as fit, at
+// most two).
+cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, int ctas_per_sm, GridCfg& cfg);
 size_t grid_scratch_size(int M, int N, int p_max, int grid);
 cudaError_t grid_launch(const GridCfg& cfg, const FrameArgs& A, char* scratch, cudaStream_t stream);
 // Runs one bounded device wait that nothing satisfies (0: an mbarrier wait, 1: the grid

@@ -44,6 +44,21 @@ def test_grid_rx_vs_oracle(M, N, Q):
     assert wx < TOL_X and wl < TOL_LLR and mm == 0, (wx, wl, mm)
 
 
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_grid_rx_ctas_per_sm(ctas):
+    """The grid receiver at one and at two CTAs per SM (the grid barrier's arrival count and
+    the per-CTA partials follow the grid size)."""
+    M, N, Q, F = 1024, 32, 16, 2
+    b = synth.fractional_batch(F, seed=9750 + ctas, M=M, N=N, Q=Q, snr_db=(12, 28))
+    plan = Plan(M, N, 1, 1, Q)
+    plan.set_tuning(ctas_per_sm=ctas)
+    out = _run(plan, b, 10, F)
+    torch.cuda.synchronize()
+    assert set(out["status"].cpu().numpy().tolist()) <= {0, 6}
+    wx, wl, mm = _check_frames(b, out, range(F), M, N, 1, 1, Q, 10, plan.p_max)
+    assert wx < TOL_X and wl < TOL_LLR and mm == 0, (wx, wl, mm)
+
+
 def test_grid_rx_paper_operating_point_16384x32():
     """One frame at the paper's headline grid (M, N) = (16384, 32), 16-QAM: 524288 DD bins,
     4 MB per FP32 vector."""
