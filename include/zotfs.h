@@ -250,6 +250,12 @@ zotfs_status zotfs_demap(zotfs_plan plan, const float* x_hat, const float* noise
  * traps or hangs; the context stays usable. */
 zotfs_status zotfs_check_bounded_wait(int which, uint32_t max_polls, int32_t* status, zotfs_stream stream);
 
+/* Self-check of the CG's scalar division: q[i] = (float) of alpha-style ratio a[i] / b[i] as the
+ * FP32 kernels form it (FP64, by one Newton-Raphson step on the FP32 reciprocal of b, or a full
+ * division when float(b) is not a normal number; 0 when b = 0), for n pairs.  a, b: dev double
+ * [n]; q: dev float [n].  For testing the kernels' arithmetic against IEEE division. */
+zotfs_status zotfs_check_cg_ratio(const double* a, const double* b, float* q, int n, zotfs_stream stream);
+
 /* Host-side fault injection for tests of the allocation-failure paths: with after = n >= 0,
  * the library's next n device or pinned-host allocations (any call, any thread) succeed and
  * the one after fails as if the device were out of memory; that call then returns

@@ -114,6 +114,7 @@ SIGNATURES = {
     "zotfs_ss_apply": (_I, [_P, C.POINTER(zotfs_paths), _P, _P, _I, _I, _P, _P]),
     "zotfs_equalize": (_I, [_P, _P, _I, C.POINTER(zotfs_paths), _P, _I, _P, _I, _P, _P]),
     "zotfs_equalize_mrc": (_I, [_P, _P, _I, C.POINTER(zotfs_paths), _I, _P, _P, _I, _P]),
+    "zotfs_check_cg_ratio": (_I, [_P, _P, _P, _I, _P]),
     "zotfs_demap": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "zotfs_rx": (_I, [_P, _P, _P, _P, _P, _I, C.POINTER(zotfs_paths), _P, _P, _P, _P, _I, _P]),
     "zotfs_rx_plain": (_I, [_P, _P, _P, _P, _P, _I, C.POINTER(zotfs_paths), _P, _P, _P, _P, _I, _P]),
@@ -187,6 +188,7 @@ zotfs_estimate = _mk("zotfs_estimate")
 zotfs_ss_apply = _mk("zotfs_ss_apply")
 zotfs_equalize = _mk("zotfs_equalize")
 zotfs_equalize_mrc = _mk("zotfs_equalize_mrc")
+zotfs_check_cg_ratio = _mk("zotfs_check_cg_ratio")
 zotfs_demap = _mk("zotfs_demap")
 zotfs_rx = _mk("zotfs_rx")
 zotfs_rx_plain = _mk("zotfs_rx_plain")

@@ -105,6 +105,7 @@ void bucket_args(int M, int N, int nrx, int ntx, int pilot_mode, int guard, int 
   A.inv_sqrtN = 1.0 / std::sqrt((double)N);
   A.sqrtN = std::sqrt((double)N);
   A.pam_d = std::sqrt(3.0 / 6.0);
+  for (int hb = 1; hb <= 3; ++hb) A.pam_d_hb[hb] = std::sqrt(3.0 / (2.0 * ((1 << (2 * hb)) - 1)));
   A.W = W;
   A.Tab = Tab;
   A.mode = kEstimate | kCG | kDemap | kWritePaths | kWriteX;

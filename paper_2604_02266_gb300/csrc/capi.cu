@@ -81,6 +81,7 @@ void fill_plan_args(const zotfs_plan_s* plan, FrameArgs& A) {
   A.inv_sqrtN = 1.0 / std::sqrt((double)plan->N);
   A.sqrtN = std::sqrt((double)plan->N);
   A.pam_d = std::sqrt(3.0 / (2.0 * (plan->qam - 1)));
+  for (int hb = 1; hb <= 3; ++hb) A.pam_d_hb[hb] = std::sqrt(3.0 / (2.0 * ((1 << (2 * hb)) - 1)));
   A.eps2 = (double)plan->opt.cg_eps * (double)plan->opt.cg_eps;
   const bool fp64 = plan->opt.compute == ZOTFS_COMPUTE_FP64;
   A.W = fp64 ? (const void*)plan->d_W64 : (const void*)plan->d_W;
@@ -402,6 +403,19 @@ static_assert(sizeof(zotfs_tuning) == 16, "zotfs_tuning layout");
 static_assert(sizeof(zotfs_frame_desc) == 16 * 4 + 9 * 8, "zotfs_frame_desc layout");
 static_assert(sizeof(zotfs_batch_opts) == 32, "zotfs_batch_opts layout");
 static_assert(sizeof(zotfs_request) == 10 * 4 + 3 * 8, "zotfs_request layout");
+
+namespace zotfs {
+namespace {
+__global__ void cg_ratio_check_kernel(const double* a, const double* b, float* q, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) q[i] = (float)cg_ratio<float>(a[i], b[i]);
+}
+}  // namespace
+cudaError_t launch_cg_ratio_check(const double* a, const double* b, float* q, int n, cudaStream_t stream) {
+  cg_ratio_check_kernel<<<(n + 255) / 256, 256, 0, stream>>>(a, b, q, n);
+  return cudaGetLastError();
+}
+}  // namespace zotfs
 
 extern "C" {
 
@@ -798,6 +812,17 @@ zotfs_status zotfs_check_bounded_wait(int which, uint32_t max_polls, int32_t* st
   if (!status) return inval("status is NULL");
   cudaError_t e = check_bounded_wait(which, max_polls, status, stream);
   if (e != cudaSuccess) return cuda_fail(e, "bounded-wait check launch");
+  ++g_launches;
+  return ZOTFS_OK;
+}
+
+zotfs_status zotfs_check_cg_ratio(const double* a, const double* b, float* q, int n, zotfs_stream stream) {
+  g_launches = 0;
+  if (n < 0) return inval("n < 0");
+  if (n == 0) return ZOTFS_OK;
+  if (!a || !b || !q) return inval("NULL buffer");
+  cudaError_t e = launch_cg_ratio_check(a, b, q, n, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cg ratio check launch");
   ++g_launches;
   return ZOTFS_OK;
 }

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
             }
           }
         const double pa = block_sum_to_thread0(part, S);
-        if (tid == 0) S->fsc[0] = (pa != 0.0) ? cn / pa : 0.0;
+        if (tid == 0) S->fsc[0] = cg_ratio<R>(cn, pa);
         __syncthreads();
         const R alpha = (R)S->fsc[0];
         part = 0;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kBigThreads, 1)
           }
         const double cn_new = block_sum_to_thread0(part, S);
         if (tid == 0) {
-          S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;
+          S->fsc[1] = cg_ratio<R>(cn_new, cn);
           if (!isfinite(cn_new)) S->isc[1] = 1;
           if (cn_new <= stop_at) S->isc[4] = 1;
           cn = cn_new;

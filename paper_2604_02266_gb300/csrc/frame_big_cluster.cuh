@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(TMAX, 1)
         }
       const double pa = cluster_sum<CL>(cluster, cs, set, block_sum_to_thread0(part, S));
       set ^= 1;
-      if (tid == 0) S->fsc[0] = (pa != 0.0) ? cn / pa : 0.0;
+      if (tid == 0) S->fsc[0] = cg_ratio<float>(cn, pa);
       __syncthreads();
       const R alpha = (R)S->fsc[0];
       part = 0;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(TMAX, 1)
       const double cn_new = cluster_sum<CL>(cluster, cs, set, block_sum_to_thread0(part, S));
       set ^= 1;
       if (tid == 0) {
-        S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;
+        S->fsc[1] = cg_ratio<float>(cn_new, cn);
         if (!isfinite(cn_new)) S->isc[1] = 1;
         if (cn_new <= stop_at) S->isc[4] = 1;
         cn = cn_new;

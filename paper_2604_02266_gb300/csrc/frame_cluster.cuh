@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(TMAX, 1) cluster_kernel(const __grid_constant_
       }
       const double pa = cluster_sum<C>(cluster, cs, set, block_sum_to_thread0(part, S));
       set ^= 1;
-      if (tid == 0) S->fsc[0] = (pa != 0.0) ? cn / pa : 0.0;  // alpha, FP64, the same in every CTA
+      if (tid == 0) S->fsc[0] = cg_ratio<float>(cn, pa);  // alpha, FP64, the same in every CTA
       __syncthreads();
       const R alpha = (R)S->fsc[0];
       part = 0;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(TMAX, 1) cluster_kernel(const __grid_constant_
       const double cn_new = cluster_sum<C>(cluster, cs, set, block_sum_to_thread0(part, S));
       set ^= 1;
       if (tid == 0) {
-        S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;  // beta, FP64
+        S->fsc[1] = cg_ratio<float>(cn_new, cn);  // beta, FP64
         if (!isfinite(cn_new)) S->isc[1] = 1;
         if (cn_new <= stop_at) S->isc[4] = 1;
         cn = cn_new;

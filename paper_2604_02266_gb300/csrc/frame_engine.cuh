@@ -28,6 +28,8 @@
 // Everything is templated on the arithmetic type R (float, or double for FP64 plans).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace zotfs {
@@ -74,6 +76,7 @@ struct FrameArgs {
   int M, N, logM, logN, nrx, ntx, T;
   int K0, L0, pilot_mode, guard, p_max, in_dtype, tap_dtype, qam, bps;
   double a_pilot, inv_sqrtN, sqrtN, pam_d;
+  double pam_d_hb[4];  // PAM half-spacing by bits per axis (1: QPSK, 2: 16-QAM, 3: 64-QAM), for descriptors
   const void* W;    // W[t] = exp(j2pi t/(MN)), t in [0, MN), complex R
   const void* Tab;  // Tab[(dl + N/2) M + k] = W[(dl k) mod MN], complex R
   // work distribution
@@ -202,6 +205,32 @@ constexpr uint32_t kMaxPolls = 1u << 22;
 
 // Most CTAs per SM the paper-scale grid receiver launches (its scratch holds their partials).
 constexpr int kGridMaxCtasPerSm = 2;
+
+// Algorithm 1's scalar ratios alpha = c_n / Re(p^H a) and beta = c_n' / c_n from their FP64
+// inner products, with the readings alpha = 0 when Re(p^H a) = 0 and beta = 0 when c_n = 0.
+// For FP32 arithmetic (R = float) the quotient is only used rounded to FP32, so it is formed
+// in FP64 by one Newton-Raphson step on the FP32 reciprocal of the divisor (Markstein's
+// correction): r0 = 1/float(b), e = 1 - b r0, r1 = r0 + r0 e, q = a r1.  r0 carries a relative
+// error |d| of about 2^-23, r1 one of d^2 < 2^-44, so q rounds to the same float as a / b
+// unless a / b lies within 2^-44 (relative) of a rounding boundary.  A full FP64 division costs
+// several hundred cycles on this part and sits on the CTA's critical path twice per iteration;
+// this costs three dependent FP64 operations.  Divisors whose FP32 image is not a normal
+// number, and FP64 plans (R = double), take the full division.
+template <typename R>
+__device__ __forceinline__ double cg_ratio(double a, double b) {
+  if (b == 0.0) return 0.0;
+  if constexpr (std::is_same<R, float>::value) {
+    const float bf = (float)b;
+    const float abf = fabsf(bf);
+    if (abf >= 1e-30f && abf <= 1e30f) {
+      const double r0 = (double)__frcp_rn(bf);
+      const double e = fma(-b, r0, 1.0);
+      const double r1 = fma(r0, e, r0);
+      return a * r1;
+    }
+  }
+  return a / b;
+}
 
 // ------------------------------------------------------------------ staging + DZT
 

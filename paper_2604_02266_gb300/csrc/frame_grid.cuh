@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         if (tid == 0) partA[blockIdx.x] = d;
         if (!grid_sync(G.bar, gen)) return fail(io);
         const double pa = grid_partials(partA);
-        if (tid == 0) S->fsc[0] = (pa != 0.0) ? cn / pa : 0.0;  // alpha, FP64
+        if (tid == 0) S->fsc[0] = cg_ratio<R>(cn, pa);  // alpha, FP64
         __syncthreads();
         const R alpha = (R)S->fsc[0];
         // x += alpha p;  c -= alpha a;  c_n' = ||c||^2
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         if (!grid_sync(G.bar, gen)) return fail(io);
         const double cn_new = grid_partials(partC);
         if (tid == 0) {
-          S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;  // beta, FP64
+          S->fsc[1] = cg_ratio<R>(cn_new, cn);  // beta, FP64
           if (!isfinite(cn_new)) S->isc[1] = 1;
           if (cn_new <= stop_at) S->isc[4] = 1;
           cn = cn_new;

@@ -52,7 +52,7 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
     io.iters = d.iters;
     io.eps2 = (double)d.cg_eps * (double)d.cg_eps;
     io.bps = 31 - __clz(d.qam);
-    io.pam_d = sqrt(3.0 / (2.0 * (d.qam - 1)));
+    io.pam_d = A.pam_d_hb[(io.bps >> 1) & 3];  // filled on the host: no per-thread FP64 sqrt / divide
     io.a_pilot = d.a_pilot;
     io.x_hat = reinterpret_cast<char*>(d.x_hat);
     io.llr = d.llr;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             }
           }
         const double pa = block_sum_to_thread0(part, S);
-        if (tid == 0) S->fsc[0] = (pa != 0.0) ? cn / pa : 0.0;  // alpha, FP64
+        if (tid == 0) S->fsc[0] = cg_ratio<R>(cn, pa);  // alpha, FP64
         __syncthreads();
         const R alpha = (R)S->fsc[0];
         // x += alpha p;  c -= alpha a;  c_n' = ||c||^2
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             }
         const double cn_new = block_sum_to_thread0(part, S);
         if (tid == 0) {
-          S->fsc[1] = (cn != 0.0) ? cn_new / cn : 0.0;  // beta, FP64
+          S->fsc[1] = cg_ratio<R>(cn_new, cn);  // beta, FP64
           if (!isfinite(cn_new)) S->isc[1] = 1;
           if (cn_new <= stop_at) S->isc[4] = 1;
           cn = cn_new;

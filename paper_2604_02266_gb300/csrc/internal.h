@@ -173,6 +173,9 @@ zotfs_status run_plain(zotfs_plan_s* plan, const void* y_pilot_td, const void* y
                        const float* theta, int iters, const zotfs_paths* paths, float* x_hat, float* llr,
                        uint8_t* bits, int32_t* status, int n_frames, cudaStream_t stream);
 
+// Self-check of cg_ratio<float> (capi.cu): q[i] = float(cg_ratio(a[i], b[i])).
+cudaError_t launch_cg_ratio_check(const double* a, const double* b, float* q, int n, cudaStream_t stream);
+
 extern thread_local int g_launches;
 
 }  // namespace zotfs

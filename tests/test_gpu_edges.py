@@ -131,3 +131,30 @@ def test_bounded_waits_give_up_with_etimeout():
     torch.cuda.synchronize()
     wx, wl, mm = _check_frames(b, out, range(F), M, N, 1, 1, Q, 10, 64)
     assert wx < TOL_X and wl < TOL_LLR and mm == 0, (wx, wl, mm)
+
+
+def test_cg_ratio_matches_ieee_division():
+    """The CG's alpha / beta division (one Newton-Raphson step on an FP32 reciprocal, in FP64)
+    gives the float that IEEE double division rounded to float gives, on a million random
+    pairs over wide magnitude ranges; a disagreement can only come from a quotient within
+    2^-44 of a float rounding boundary, and is then one unit in the last place.  Zero, tiny and
+    huge divisors take the exact path."""
+    import ctypes as C
+    from paper_2604_02266_gb300 import _zotfs as Z
+    g = np.random.default_rng(123)
+    n = 1 << 20
+    a = (g.uniform(0.5, 2.0, n) * 10.0 ** g.uniform(-20, 20, n)) * g.choice([-1.0, 1.0], n)
+    b = (g.uniform(0.5, 2.0, n) * 10.0 ** g.uniform(-25, 25, n)) * g.choice([-1.0, 1.0], n)
+    b[:6] = [0.0, 1e-35, -1e-40, 1e35, 3e-300, 1.0]
+    a[:6] = [1.0, 1.0, 2.0, 5.0, 1e-290, 0.0]
+    ad, bd = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    q = torch.empty(n, dtype=torch.float32, device="cuda")
+    assert Z.zotfs_check_cg_ratio(C.c_void_p(ad.data_ptr()), C.c_void_p(bd.data_ptr()), C.c_void_p(q.data_ptr()), n,
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream)) == Z.OK
+    got = q.cpu().numpy()
+    with np.errstate(divide="ignore", over="ignore"):
+        ref = np.where(b == 0.0, 0.0, a / np.where(b == 0.0, 1.0, b)).astype(np.float32)
+    diff = got.view(np.int32).astype(np.int64) - ref.view(np.int32).astype(np.int64)
+    assert np.abs(diff).max() <= 1
+    assert int((diff != 0).sum()) <= 4, int((diff != 0).sum())
+    assert got[0] == 0.0 and got[5] == 0.0
