@@ -17,10 +17,18 @@
 
 namespace zotfs {
 
-// Complex elements of one cluster's slot: CL staging grids, the p and t extensions, x, c, p, a.
+// Complex elements of one cluster's slot: the p and t extensions (p itself is read from the
+// main columns of its extension), x, and one region that holds c and a during the CG and the CL
+// staging grids of the Zak transforms (and the demapper's labels) outside it.  Keeping the slot
+// small keeps the live slots of a loaded GPU in L2.
+__host__ __device__ __forceinline__ size_t big_cluster_union_elems(int M, int N, int ntx, int CL) {
+  const size_t MN = (size_t)M * N, cv = (size_t)2 * ntx * MN, st = (size_t)CL * MN;
+  return cv > st ? cv : st;
+}
 __host__ __device__ __forceinline__ size_t big_cluster_slot_elems(int M, int N, int nrx, int ntx, int CL) {
   const size_t MN = (size_t)M * N;
-  return (size_t)CL * MN + (size_t)(nrx + ntx) * ext_block_elems(M, N, kBigChunk) + (size_t)4 * ntx * MN;
+  return (size_t)(nrx + ntx) * ext_block_elems(M, N, kBigChunk) + (size_t)ntx * MN +
+         big_cluster_union_elems(M, N, ntx, CL);
 }
 
 // OR of one status word per CTA over the cluster, the same in every CTA (the flag sets of
@@ -80,13 +88,12 @@ __global__ void __launch_bounds__(TMAX, 1)
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM, T = blockDim.x;
   const size_t blk = ext_block_elems(M, N, E);
   char* slot = scratch + (size_t)(blockIdx.x / CL) * slot_bytes;
-  C* stage = reinterpret_cast<C*>(slot) + (size_t)rank * MN;  // this CTA's staging grid
-  C* extP = reinterpret_cast<C*>(slot) + (size_t)CL * MN;
+  C* extP = reinterpret_cast<C*>(slot);
   C* extT = extP + (size_t)A.ntx * blk;
   C* Xv = extT + (size_t)A.nrx * blk;
-  C* Cv = Xv + (size_t)A.ntx * MN;
-  C* Pv = Cv + (size_t)A.ntx * MN;
-  C* Vv = Pv + (size_t)A.ntx * MN;
+  C* Cv = Xv + (size_t)A.ntx * MN;    // c and a share their region with the staging grids:
+  C* Vv = Cv + (size_t)A.ntx * MN;    // the grids are used only before b = H^H y and in the
+  C* stage = Cv + (size_t)rank * MN;  // demapper (labels), when c and a are dead
   const int tid = threadIdx.x;
   const int k = tid & (M - 1);
   const int band = N / CL;
@@ -96,6 +103,10 @@ __global__ void __launch_bounds__(TMAX, 1)
   int fset = 0;
 
   auto own = [&](int c, int i) { return (size_t)(jw + c * E + i) * M + k; };
+  // p's value at an own element: the main column of its extension
+  auto p_at = [&](int t, int c, int i) -> C& {
+    return extP[(size_t)t * blk + (size_t)(jw + c * E + i) * 2 * M + k + (M >> 1)];
+  };
   auto load_grid = [&](const char* src) {  // TD grid -> this CTA's staging grid, all threads
     __syncthreads();
     for (int e = tid; e < MN; e += T) stage[e] = load_complex<C>(src, (size_t)e, A.in_dtype);
@@ -189,7 +200,6 @@ __global__ void __launch_bounds__(TMAX, 1)
         for (int i = 0; i < E; ++i) {
           const size_t o = (size_t)t * MN + own(c, i);
           Cv[o] = v[i];
-          Pv[o] = v[i];
           Xv[o] = make_float2(0.f, 0.f);
           part = fma(v[i].x, v[i].x, fma(v[i].y, v[i].y, part));
         }
@@ -222,7 +232,7 @@ __global__ void __launch_bounds__(TMAX, 1)
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const size_t o = (size_t)t * MN + own(c, i);
-            const C pv = Pv[o];
+            const C pv = p_at(t, c, i);
             v[i].x = fma(lam, pv.x, v[i].x);
             v[i].y = fma(lam, pv.y, v[i].y);
             part = fma(pv.x, v[i].x, fma(pv.y, v[i].y, part));
@@ -240,7 +250,7 @@ __global__ void __launch_bounds__(TMAX, 1)
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const size_t o = (size_t)t * MN + own(c, i);
-            const C pv = Pv[o], av = Vv[o];
+            const C pv = p_at(t, c, i), av = Vv[o];
             C xv = Xv[o], cv = Cv[o];
             xv.x = fma(alpha, pv.x, xv.x);
             xv.y = fma(alpha, pv.y, xv.y);
@@ -268,10 +278,9 @@ __global__ void __launch_bounds__(TMAX, 1)
             for (int i = 0; i < E; ++i) {
               const size_t o = (size_t)t * MN + own(c, i);
               const C cv = Cv[o];
-              C pv = Pv[o];
+              C pv = p_at(t, c, i);  // this thread's own element: no other thread writes it
               pv.x = fma(beta, pv.x, cv.x);
               pv.y = fma(beta, pv.y, cv.y);
-              Pv[o] = pv;
               v[i] = pv;
             }
             write_ext<R, E, true>(extP + t * blk, A, k, jw + c * E, v);
