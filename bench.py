@@ -525,6 +525,8 @@ SERVE_WORKLOAD = ("serving loop: Poisson arrivals, M in {32,64,128,256}, N in {1
                   "{4,16,64}, all uniform, 8-path fractional channels, SNR 0..30 dB, 10 CG iterations, "
                   "0.5 ms deadline from arrival, outputs kept in a device arena until released")
 DEADLINE_MS = 0.5
+# latency classes of the serving report: M N n_rx n_tx in (lo, hi]
+SERVE_WORK_BUCKETS = ((0, 2048), (2048, 8192), (8192, 32768), (32768, 131072), (131072, 1 << 30))
 
 
 def impl_serve(args):
@@ -606,18 +608,32 @@ def impl_serve(args):
             lat = (done - arr) * 1e-6
             wall = (done.max() - arr.min()) * 1e-9
             bits = sum(a * m * nn * int(np.log2(q)) for (m, nn, a, q) in meta)
+            def lat_stats(sel):
+                return {"frames": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                        "p99_ms": float(np.percentile(lat[sel], 99)),
+                        "deadline_met": float((lat[sel] <= DEADLINE_MS).mean())}
             by_ant = {}
             for a in SERVE_ANT:
                 sel = np.array([mt[2] == a for mt in meta])
                 if sel.any():
-                    by_ant[f"{a}x{a}"] = {"p50_ms": float(np.percentile(lat[sel], 50)),
-                                          "p99_ms": float(np.percentile(lat[sel], 99)),
-                                          "deadline_met": float((lat[sel] <= DEADLINE_MS).mean())}
+                    by_ant[f"{a}x{a}"] = lat_stats(sel)
+            # per class: work buckets of M N n_rx n_tx, and every SISO shape on its own
+            work = np.array([m * nn * a * a for (m, nn, a, q) in meta])
+            by_work = {}
+            for lo, hi in SERVE_WORK_BUCKETS:
+                sel = (work > lo) & (work <= hi)
+                if sel.any():
+                    by_work[f"({lo},{hi}]"] = lat_stats(sel)
+            by_siso_shape = {}
+            for (m, nn) in sorted({(mt[0], mt[1]) for mt in meta if mt[2] == 1}):
+                sel = np.array([mt[0] == m and mt[1] == nn and mt[2] == 1 for mt in meta])
+                by_siso_shape[f"{m}x{nn}"] = lat_stats(sel)
             runs.append({"offered_frames_s": rate, "frames": n, "completed_frames_s": n / wall,
                          "mbit_s": bits / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)), "deadline_met": float((lat <= DEADLINE_MS).mean()),
                          "queue_p99_ms": float(np.percentile((adm - arr) * 1e-6, 99)),
-                         "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()), "by_antennas": by_ant})
+                         "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()), "by_antennas": by_ant,
+                         "by_work": by_work, "by_siso_shape": by_siso_shape})
         stats = srv.stats()
     finally:
         srv.close()
@@ -745,7 +761,7 @@ def impl_mixed(args):
             "ms_per_step_graph": ms_graph, "ms_per_step_tuned_eager": ms_eager, "ms_per_step_default_eager": ms_default,
             "status_ok_or_truncated": float(np.isin(st, (0, 6)).mean()),
             "tuning": [{k: t[k] for k in ("M", "N", "n_rx", "n_tx", "threads_per_frame", "fft_radix", "ctas_per_sm", "cluster",
-                                          "sm_ms_per_frame", "ms_best", "ms_default")} for t in tuning]}
+                                          "frames_per_cta", "sm_ms_per_frame", "ms_best", "ms_default")} for t in tuning]}
         del tuned, frames, keep
     head = out["storage"]["fp16"]
     line = {"metric": "equalized Zak-OTFS frames/s, uneven mixed-precision batch", "value": head["frames_s"],

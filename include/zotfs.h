@@ -166,6 +166,10 @@ typedef struct zotfs_tuning {
                            per two SMs, else the clustered large-frame kernel, 4 CTAs when the
                            call has at most one frame per four SMs and 2 otherwise (MIMO
                            frames only: loaded SISO calls keep one CTA per frame).  1: never */
+  int32_t frames_per_cta;  /* frames of the one-CTA shared-memory kernel packed into one CTA, each
+                              on its own threads_per_frame threads and slice of shared memory with
+                              its own barriers (0 or 1: one; at most 8, reduced to what the
+                              kernel's thread limit and the SM's shared memory allow) */
 } zotfs_tuning;
 zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* tuning);
 zotfs_status zotfs_plan_get_tuning(zotfs_plan plan, zotfs_tuning* tuning);

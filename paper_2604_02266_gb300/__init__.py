@@ -131,15 +131,15 @@ class Plan:
             setattr(o, k, v)
         Z.check(Z.zotfs_plan_set_options(self._h, C.byref(o)))
 
-    def set_tuning(self, threads_per_frame=0, fft_radix=0, ctas_per_sm=0, cluster=0):
-        t = Z.zotfs_tuning(threads_per_frame, fft_radix, ctas_per_sm, cluster)
+    def set_tuning(self, threads_per_frame=0, fft_radix=0, ctas_per_sm=0, cluster=0, frames_per_cta=0):
+        t = Z.zotfs_tuning(threads_per_frame, fft_radix, ctas_per_sm, cluster, frames_per_cta)
         Z.check(Z.zotfs_plan_set_tuning(self._h, C.byref(t)))
 
     def tuning(self):
         t = Z.zotfs_tuning()
         Z.check(Z.zotfs_plan_get_tuning(self._h, C.byref(t)))
         return {"threads_per_frame": t.threads_per_frame, "fft_radix": t.fft_radix, "ctas_per_sm": t.ctas_per_sm,
-                "cluster": t.cluster}
+                "cluster": t.cluster, "frames_per_cta": t.frames_per_cta}
 
     @property
     def p_max(self):
@@ -273,7 +273,8 @@ class Batch:
         for i, (shape, tun) in enumerate(entries):
             tarr[i].M, tarr[i].N, tarr[i].n_rx, tarr[i].n_tx = shape
             tarr[i].tuning = Z.zotfs_tuning(tun.get("threads_per_frame", 0), tun.get("fft_radix", 0),
-                                            tun.get("ctas_per_sm", 0), tun.get("cluster", 0))
+                                            tun.get("ctas_per_sm", 0), tun.get("cluster", 0),
+                                            tun.get("frames_per_cta", 0))
         opts = Z.zotfs_batch_opts(threads_per_frame, ctas_per_sm, fft_radix, len(entries), tarr, max_sms, cluster)
         h = C.c_void_p()
         Z.check(Z.zotfs_batch_create(arr, n, C.byref(opts), C.byref(h)))
@@ -343,6 +344,7 @@ def autotune(frames, warmup=0, reps=0, max_frames=0, stream=None):
         out.append({"M": b.M, "N": b.N, "n_rx": b.n_rx, "n_tx": b.n_tx,
                     "threads_per_frame": b.tuning.threads_per_frame, "fft_radix": b.tuning.fft_radix,
                     "ctas_per_sm": b.tuning.ctas_per_sm, "cluster": b.tuning.cluster,
+                    "frames_per_cta": b.tuning.frames_per_cta,
                     "sm_ms_per_frame": r.sm_ms_per_frame, "ms_best": r.ms_best,
                     "ms_default": r.ms_default,
                     "n_candidates": r.n_candidates, "n_frames": r.n_frames})
@@ -367,7 +369,8 @@ def load_tuning(path):
     out = []
     for e in doc["entries"]:
         shape = (int(e["M"]), int(e["N"]), int(e["n_rx"]), int(e["n_tx"]))
-        out.append((shape, {k: int(e.get(k, 0)) for k in ("threads_per_frame", "fft_radix", "ctas_per_sm", "cluster")}))
+        out.append((shape, {k: int(e.get(k, 0)) for k in ("threads_per_frame", "fft_radix", "ctas_per_sm", "cluster",
+                                                           "frames_per_cta")}))
     return out
 
 

@@ -43,7 +43,7 @@ class zotfs_paths(C.Structure):
 
 class zotfs_tuning(C.Structure):
     _fields_ = [("threads_per_frame", C.c_int32), ("fft_radix", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("cluster", C.c_int32)]
+                ("cluster", C.c_int32), ("frames_per_cta", C.c_int32)]
 
 
 class zotfs_frame_desc(C.Structure):

@@ -26,6 +26,7 @@ struct Bucket {
   FrameCfg cfg{};
   int radix = 2;
   int ctas_per_sm = 0;
+  int fpc = 1;  // frames packed into one CTA (shared-memory kernel)
   int grid = 0;
   int ids_off = 0;
   float2* d_W = nullptr;
@@ -217,7 +218,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
   std::vector<int> occ(b->buckets.size(), 0);
   for (size_t bi = 0; bi < b->buckets.size() && st == ZOTFS_OK; ++bi) {
     Bucket& B = b->buckets[bi];
-    int tpf = o.threads_per_frame, radix = o.fft_radix, cps = o.ctas_per_sm, cl = o.cluster;
+    int tpf = o.threads_per_frame, radix = o.fft_radix, cps = o.ctas_per_sm, cl = o.cluster, fpc = 0;
     for (int j = 0; j < o.n_tuning; ++j) {
       const zotfs_tuning_entry& te = o.tuning[j];
       if (te.M == B.M && te.N == B.N && te.n_rx == B.nrx && te.n_tx == B.ntx) {
@@ -225,6 +226,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
         if (!o.fft_radix) radix = te.tuning.fft_radix;
         if (!o.ctas_per_sm) cps = te.tuning.ctas_per_sm;
         if (!o.cluster) cl = te.tuning.cluster;
+        fpc = te.tuning.frames_per_cta;
       }
     }
     B.radix = radix == 2 ? 2 : (radix == 4 ? 4 : kDefaultRadix);
@@ -249,8 +251,11 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
       e = big_cluster_max_active(B.bccfg, clusters);
       occ[bi] = std::max(1, clusters * B.bccfg.CL / std::max(1, b->sm_count));  // CTAs per SM
       if (e == cudaSuccess && clusters < 1) e = cudaErrorInvalidConfiguration;
+    } else if (B.big) {
+      e = big_occupancy(B.bigcfg, occ[bi]);
     } else {
-      e = B.big ? big_occupancy(B.bigcfg, occ[bi]) : frame_variant_occupancy(B.cfg.variant, B.cfg.T, B.cfg.smem, occ[bi]);
+      B.fpc = frames_per_cta_for(B.cfg, fpc);
+      e = frame_variant_occupancy(B.cfg.variant, B.cfg.T, B.cfg.smem, occ[bi], B.fpc);
     }
     if (e != cudaSuccess) {
       st = cuda_fail(e, "occupancy query");
@@ -271,7 +276,7 @@ zotfs_status zotfs_batch_create(const zotfs_frame_desc* descs, int n_frames, con
     const double share = total_work > 0 ? B.work / total_work : 1.0;
     int sms = (int)std::ceil(share * avail);
     sms = std::max(1, std::min(sms, avail));
-    B.grid = std::max(1, std::min((int)B.ids.size(), sms * occ[bi]));
+    B.grid = std::max(1, std::min(((int)B.ids.size() + B.fpc - 1) / B.fpc, sms * occ[bi]));
     if (B.bigc) B.grid = std::max(1, std::min((int)B.ids.size(), sms * occ[bi] / B.bccfg.CL));  // clusters
   }
   // each bucket's CTAs take its frames heaviest first (lowest threshold first: more taps pass
@@ -373,7 +378,7 @@ zotfs_status zotfs_rx_batch(zotfs_batch b, int32_t* status, zotfs_stream stream)
     A.frame_ids = b->d_ids + B.ids_off;
     e = B.bigc  ? big_cluster_launch(B.bccfg, A, B.radix, B.grid, B.d_big, s)
         : B.big ? big_launch(B.bigcfg, A, B.radix, B.grid, B.d_big, s)
-                : frame_variant_launch(B.cfg.variant, A, B.radix, B.grid, B.cfg.T, B.cfg.smem, s);
+                : frame_variant_launch(B.cfg.variant, A, B.radix, B.grid, B.cfg.T, B.cfg.smem, s, B.fpc);
     if (e != cudaSuccess) return cuda_fail(e, "bucket kernel launch");
     ++g_launches;
     e = cudaEventRecord(b->events[1 + bi], s);

@@ -199,14 +199,24 @@ static const int* maybe_order(zotfs_plan_s* plan, const FrameArgs& A, int reside
   return order;
 }
 
+int frames_per_cta_for(const FrameCfg& cfg, int want) {
+  int E, NB, TMAX, rb, minb, coef;
+  if (want <= 1 || !frame_variant_packs(cfg.variant) || !frame_variant_info(cfg.variant, E, NB, TMAX, rb, minb, coef))
+    return 1;
+  int f = want > kMaxFramesPerCta ? kMaxFramesPerCta : want;
+  while (f > 1 && (cfg.T * f > TMAX || ((cfg.smem + 127) & ~size_t(127)) * (size_t)f > 227 * 1024)) --f;
+  return f;
+}
+
 zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameArgs& A, int radix, int ctas_per_sm,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, int frames_per_cta) {
   int* counter = plan->d_counters + (plan->counter_next++ & 63);
   A.work_counter = counter;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(work counter)");
+  const int fpc = frames_per_cta_for(cfg, frames_per_cta);
   int blocks = 0;
-  e = frame_variant_occupancy(cfg.variant, cfg.T, cfg.smem, blocks);
+  e = frame_variant_occupancy(cfg.variant, cfg.T, cfg.smem, blocks, fpc);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   if (blocks < 1) {
     set_error("frame kernel does not fit on an SM (registers or shared memory)");
@@ -214,9 +224,9 @@ zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameA
   }
   if (ctas_per_sm > 0 && ctas_per_sm < blocks) blocks = ctas_per_sm;
   long long grid = (long long)plan->sm_count * blocks;
-  if (const int* order = maybe_order(plan, A, (int)grid, stream)) A.frame_ids = order;
-  if (grid > A.n_frames) grid = A.n_frames;
-  e = frame_variant_launch(cfg.variant, A, radix, (int)grid, cfg.T, cfg.smem, stream);
+  if (const int* order = maybe_order(plan, A, (int)(grid * fpc), stream)) A.frame_ids = order;
+  if (grid * fpc > A.n_frames) grid = (A.n_frames + fpc - 1) / fpc;
+  e = frame_variant_launch(cfg.variant, A, radix, (int)grid, cfg.T, cfg.smem, stream, fpc);
   if (e != cudaSuccess) return cuda_fail(e, "frame kernel launch");
   ++g_launches;
   return ZOTFS_OK;
@@ -354,7 +364,8 @@ static zotfs_status launch_kernels(zotfs_plan_s* plan, int nrx, int ntx, FrameAr
   FrameCfg cfg;
   if (choose_frame_cfg(plan->M, plan->N, nrx, ntx, plan->opt.p_max, plan->tune.threads_per_frame, cfg,
                        real_bytes_of(plan)))
-    return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream);
+    return launch_frame_kernel(plan, cfg, A, radix_of(plan), plan->tune.ctas_per_sm, stream,
+                               plan->tune.frames_per_cta);
   BigClusterCfg bcc;
   if (big_cluster_applies(plan, nrx, ntx, A, bcc)) {
     int clusters = 0;
@@ -399,7 +410,7 @@ using namespace zotfs;
 
 // The ABI's struct sizes (mirrored by the Python binding's ctypes structures).
 static_assert(sizeof(zotfs_options) == 40, "zotfs_options layout");
-static_assert(sizeof(zotfs_tuning) == 16, "zotfs_tuning layout");
+static_assert(sizeof(zotfs_tuning) == 20, "zotfs_tuning layout");
 static_assert(sizeof(zotfs_frame_desc) == 16 * 4 + 9 * 8, "zotfs_frame_desc layout");
 static_assert(sizeof(zotfs_batch_opts) == 32, "zotfs_batch_opts layout");
 static_assert(sizeof(zotfs_request) == 10 * 4 + 3 * 8, "zotfs_request layout");
@@ -464,6 +475,7 @@ zotfs_status zotfs_plan_create(int M, int N, int n_rx, int n_tx, zotfs_pulse pul
   p->tune.threads_per_frame = 0;
   p->tune.fft_radix = kDefaultRadix;
   p->tune.ctas_per_sm = 0;
+  p->tune.frames_per_cta = 0;
 
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
@@ -601,6 +613,7 @@ zotfs_status zotfs_plan_set_tuning(zotfs_plan plan, const zotfs_tuning* t) {
   if (t->threads_per_frame < 0 || t->threads_per_frame > 1024) return inval("threads_per_frame");
   if (t->ctas_per_sm < 0) return inval("ctas_per_sm");
   if (t->cluster < 0 || t->cluster == 3 || t->cluster > 4) return inval("cluster must be 0, 1, 2 or 4");
+  if (t->frames_per_cta < 0 || t->frames_per_cta > kMaxFramesPerCta) return inval("frames_per_cta must be 0..8");
   zotfs_tuning n = *t;
   if (n.fft_radix == 0) n.fft_radix = kDefaultRadix;
   if (n.threads_per_frame > 0) {

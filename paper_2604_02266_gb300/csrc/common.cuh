@@ -100,6 +100,36 @@ __host__ __device__ __forceinline__ int dtype_bytes(int dtype) {
   return dtype == ZOTFS_C128 ? 16 : dtype == ZOTFS_C64 ? 8 : 4;
 }
 
+// ------------------------------------------------------------ frame-scope barriers
+
+// Barrier over the threads working on one frame.  A kernel launched with a one-dimensional
+// block runs one frame per CTA at a time: the CTA barrier.  The frame kernel launched with a
+// two-dimensional block packs blockDim.y frames into a CTA, blockDim.x threads (whole warps)
+// each: row threadIdx.y synchronises on its own named barrier 1 + threadIdx.y, so the frames of
+// one CTA never wait for each other.  Every helper below works on one frame: threadIdx.x and
+// blockDim.x are the thread's index in, and the size of, its frame's row.
+__device__ __forceinline__ void frame_sync() {
+  if (blockDim.y == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + threadIdx.y), "r"(blockDim.x) : "memory");
+  }
+}
+// frame_sync() that also returns whether `pred` is nonzero in any thread of the frame.
+__device__ __forceinline__ int frame_sync_or(int pred) {
+  if (blockDim.y == 1) return __syncthreads_or(pred);
+  int out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"(pred), "r"(1 + threadIdx.y), "r"(blockDim.x)
+      : "memory");
+  return out;
+}
+
 // ------------------------------------------------------------------- reductions
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -134,7 +164,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int& to
     if (lane >= o) inc += n;
   }
   if (lane == 31) scratch[warp] = inc;
-  __syncthreads();
+  frame_sync();
   if (warp == 0) {
     int w = lane < nwarps ? scratch[lane] : 0;
     int winc = w;
@@ -146,10 +176,10 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int& to
     scratch[lane] = winc - w;  // exclusive offset of warp `lane`
     if (lane == 31) scratch[32] = winc;
   }
-  __syncthreads();
+  frame_sync();
   total = scratch[32];
   const int off = scratch[warp];
-  __syncthreads();  // scratch may be reused by the next call
+  frame_sync();  // scratch may be reused by the next call
   return off + inc - v;
 }
 
@@ -158,10 +188,10 @@ __device__ __forceinline__ int block_sum_i(int v, int* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
   v = warp_sum_i(v);
   if (lane == 0) scratch[warp] = v;
-  __syncthreads();
+  frame_sync();
   int t = 0;
   for (int w = 0; w < nwarps; ++w) t += scratch[w];
-  __syncthreads();
+  frame_sync();
   return t;
 }
 

@@ -123,7 +123,7 @@ struct FrameArgs {
 // finished the frame's outputs (barrier) and they are fenced at system scope first, so a host
 // that sees the status may read the outputs.
 __device__ __forceinline__ void publish_status(const FrameArgs& A, int32_t* status, int st_bits) {
-  if (A.status_fence) __syncthreads();
+  if (A.status_fence) frame_sync();
   if (status && threadIdx.x == 0) {
     if (A.status_fence) {
       __threadfence_system();
@@ -245,7 +245,7 @@ __device__ __forceinline__ bool stage_grid(typename Cx<R>::C* dst, const void* s
   const uint32_t bytes = (uint32_t)MN * (uint32_t)dtype_bytes(dtype);
   const bool native = dtype == Cx<R>::kIoDtype;
   char* d = reinterpret_cast<char*>(dst) + (native ? 0 : (size_t)MN * sizeof(C) - bytes);
-  __syncthreads();  // earlier generic accesses to dst are complete
+  frame_sync();  // earlier generic accesses to dst are complete
   if (tid == 0) {
     fence_proxy_async_smem();
     bulk_g2s(d, src, bytes, bar);
@@ -253,15 +253,15 @@ __device__ __forceinline__ bool stage_grid(typename Cx<R>::C* dst, const void* s
   bool ok = mbar_wait_bounded(bar, phase, kMaxPolls);
   if (!ok) ok = mbar_wait_bounded(bar, phase, kMaxPolls);  // let an in-flight copy land
   phase ^= 1u;
-  if (__syncthreads_or(!ok)) return false;
+  if (frame_sync_or(!ok)) return false;
   if (!native) {
     C tmp[E];  // MN == T * E
 #pragma unroll
     for (int i = 0; i < E; ++i) tmp[i] = load_complex<C>(d, (size_t)tid + (size_t)i * T, dtype);
-    __syncthreads();
+    frame_sync();
 #pragma unroll
     for (int i = 0; i < E; ++i) dst[tid + i * T] = tmp[i];
-    __syncthreads();
+    frame_sync();
   }
   return true;
 }
@@ -305,7 +305,7 @@ __device__ __forceinline__ void dzt_inplace(typename Cx<R>::C* X, const FrameArg
         p0[(size_t)2 * q * M] = cadd(a2, a3);
         p0[(size_t)3 * q * M] = cmul(csub(a2, a3), w2);
       }
-      __syncthreads();
+      frame_sync();
     }
   }
   for (; h >= 1; h >>= 1) {
@@ -320,7 +320,7 @@ __device__ __forceinline__ void dzt_inplace(typename Cx<R>::C* X, const FrameArg
       p0[0] = cadd(u, v);
       p0[(size_t)h * M] = cmul(csub(u, v), w);
     }
-    __syncthreads();
+    frame_sync();
   }
 }
 
@@ -368,34 +368,102 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
 // of path 0; path p at ct[p M]) -- hf W[dl k] for kFwd, h W[dl k] for the adjoint, whose
 // conjugate the caller's final combine applies -- else they are formed here from the path
 // record and the twiddle table.
+//
+// A run is applied in two phases: load_run gathers its window and its L coefficients into
+// registers, mac_run accumulates.  Kernels whose extensions live in global memory issue two
+// runs' loads before either accumulates (two L2 round trips in flight per thread instead of
+// one after the other).
 template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
-__device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
-                                          const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
-                                          int j0, typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
+__device__ __forceinline__ void load_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
+                                         const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
+                                         int j0, typename Cx<R>::C (&W)[L + E - 1], typename Cx<R>::C (&D)[L]) {
   using C = typename Cx<R>::C;
   const int M = A.M, N = A.N;
   const int CS = kRowMajor ? 1 : N + E + 3;
   const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;
   const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
   const C* a = src + (size_t)row0 * RS + (kFwd ? -rr.dk : rr.dk) * CS;
-  C W[L + E - 1];
 #pragma unroll
   for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
   const C* cr = kCoef ? ct + (size_t)rr.start * M : nullptr;
 #pragma unroll
   for (int m = 0; m < L; ++m) {
-    C D;
     if constexpr (kCoef) {
-      D = cr[(size_t)m * M];
+      D[m] = cr[(size_t)m * M];
     } else {
       const PathRecT<R> rec = pl[rr.start + m];
       const C t = tab<R>(A, (rr.dl0 + m + (N >> 1)) * M + k);
-      D = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+      D[m] = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
     }
-    const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
+  }
+}
+
+template <typename R, int E, int L, bool kFwd>
+__device__ __forceinline__ void mac_run(const typename Cx<R>::C (&W)[L + E - 1], const typename Cx<R>::C (&D)[L],
+                                        typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
+  using C = typename Cx<R>::C;
+#pragma unroll
+  for (int m = 0; m < L; ++m) {
+    const C DX = Cx<R>::make(D[m].x, D[m].x), DY = Cx<R>::make(D[m].y, D[m].y);
 #pragma unroll
     for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, W[(kFwd ? L - 1 - m : m) + i]);
   }
+}
+
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
+__device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
+                                          const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
+                                          int j0, typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
+  using C = typename Cx<R>::C;
+  if constexpr (kRowMajor) {
+    C W[L + E - 1], D[L];
+    load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, W, D);
+    mac_run<R, E, L, kFwd>(W, D, accA, accB);
+  } else {
+    // shared-memory extension: each coefficient is loaded right before its MACs (fewer live
+    // registers in the kernels that keep the CG vectors in registers)
+    const int M = A.M, N = A.N, CS = N + E + 3;
+    const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
+    const C* a = src + (size_t)row0 + (kFwd ? -rr.dk : rr.dk) * CS;
+    C W[L + E - 1];
+#pragma unroll
+    for (int w = 0; w < L + E - 1; ++w) W[w] = a[w];
+    const C* cr = kCoef ? ct + (size_t)rr.start * M : nullptr;
+#pragma unroll
+    for (int m = 0; m < L; ++m) {
+      C D;
+      if constexpr (kCoef) {
+        D = cr[(size_t)m * M];
+      } else {
+        const PathRecT<R> rec = pl[rr.start + m];
+        const C t = tab<R>(A, (rr.dl0 + m + (N >> 1)) * M + k);
+        D = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+      }
+      const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
+#pragma unroll
+      for (int i = 0; i < E; ++i) cmac_split(accA[i], accB[i], DX, DY, W[(kFwd ? L - 1 - m : m) + i]);
+    }
+  }
+}
+
+// Runs [q, end) of one length class, two at a time when the extension is in global memory.
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
+__device__ __forceinline__ int apply_runs(const typename Cx<R>::C* src, const PathRecT<R>* pl,
+                                          const typename Cx<R>::C* ct, const RunRec* rl, int q, int end,
+                                          const FrameArgs& A, int k, int j0, typename Cx<R>::C (&accA)[E],
+                                          typename Cx<R>::C (&accB)[E]) {
+  using C = typename Cx<R>::C;
+  if constexpr (kRowMajor) {
+    for (; q + 1 < end; q += 2) {
+      C W0[L + E - 1], D0[L], W1[L + E - 1], D1[L];
+      load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, W0, D0);
+      load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q + 1], A, k, j0, W1, D1);
+      mac_run<R, E, L, kFwd>(W0, D0, accA, accB);
+      mac_run<R, E, L, kFwd>(W1, D1, accA, accB);
+    }
+  }
+  for (; q < end; ++q) apply_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+  return q;
 }
 
 // Forward rows (kFwd) of output block b: out[i] = (H p)_b[k, j0 + i], summed over the tx blocks
@@ -425,8 +493,8 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
     const int n4 = packed & 127, n3 = (packed >> 7) & 127, n2 = (packed >> 14) & 255, n1 = (packed >> 22) & 511;
     int q = 0;
     if constexpr (kLMax == 4) {
-      for (const int e4 = n4; q < e4; ++q) apply_run<R, E, 4, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
-      for (const int e3 = n4 + n3; q < e3; ++q) apply_run<R, E, 3, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+      q = apply_runs<R, E, 4, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4, A, k, j0, accA, accB);
+      q = apply_runs<R, E, 3, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4 + n3, A, k, j0, accA, accB);
     } else {
       for (const int e3 = n4 + n3; q < e3; ++q) {  // split into runs of at most kLMax paths
         const RunRec rr = rl[q];
@@ -440,7 +508,7 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
       }
     }
     if constexpr (kLMax >= 2) {
-      for (const int e2 = n4 + n3 + n2; q < e2; ++q) apply_run<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+      q = apply_runs<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4 + n3 + n2, A, k, j0, accA, accB);
     } else {
       for (const int e2 = n4 + n3 + n2; q < e2; ++q) {
         RunRec sub = rl[q];
@@ -450,7 +518,7 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
         apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
       }
     }
-    for (const int e1 = n4 + n3 + n2 + n1; q < e1; ++q) apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+    apply_runs<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4 + n3 + n2 + n1, A, k, j0, accA, accB);
   }
   // accA = sum D.x W, accB = sum D.y W: D W = (A.x - B.y, A.y + B.x); for the adjoint's table
   // entries c (D = conj(c)): (A.x + B.y, A.y - B.x)
@@ -517,7 +585,7 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
                                           int* nruns_out, Side side) {
   const int P4 = (P + 3) & ~3;
   for (int p = threadIdx.x; p < P4; p += blockDim.x) keys[p] = p < P ? pl[p].dk * 256 + pl[p].dl : 0x7fffffff;
-  __syncthreads();
+  frame_sync();
   for (int p = threadIdx.x; p < P; p += blockDim.x) {  // keys are distinct: ranks are a permutation
     const int key = keys[p];
     int rank = 0;
@@ -527,9 +595,9 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
     }
     tmp[rank] = pl[p];
   }
-  __syncthreads();
+  frame_sync();
   for (int p = threadIdx.x; p < P; p += blockDim.x) pl[p] = tmp[p];
-  __syncthreads();
+  frame_sync();
   if (threadIdx.x < 32) {  // warp 0 cuts and places the runs from bit masks, 32 paths per word
     const int lane = threadIdx.x;
     const unsigned lt = (1u << lane) - 1u, le = lt | (1u << lane);
@@ -587,10 +655,10 @@ __device__ __forceinline__ int build_runs(PathRecT<R>* pl, int P, RunRec* runs, 
   } else {
     side((int)threadIdx.x - 32, (int)blockDim.x - 32);
   }
-  __syncthreads();
+  frame_sync();
   if (blockDim.x == 32) {  // one warp: the side work follows the cutting
     side((int)threadIdx.x, 32);
-    __syncthreads();
+    frame_sync();
   }
   const int packed = *nruns_out;
   return (packed & 127) + ((packed >> 7) & 127) + ((packed >> 14) & 255) + ((packed >> 22) & 511);
@@ -648,14 +716,14 @@ __device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const
     int kleft = K;  // rank of the wanted value among the taps that match `prefix`
     const int lane = tid & 31;
     for (int b = tid; b < 128; b += blockDim.x) S->hist[b] = 0;
-    __syncthreads();
+    frame_sync();
     for (int hb = kKeyBits; hb > 0; hb -= 7) {
       const int w = hb < 7 ? hb : 7, sh = hb - w;
 #pragma unroll
       for (int i = 0; i < EQ; ++i)
         if (((pass >> i) & 1u) && ((mb[i] ^ prefix) & fixed) == 0)
           atomicAdd(&S->hist[(int)((mb[i] >> sh) & (Key)127)], 1);
-      __syncthreads();
+      frame_sync();
       if (tid < 32) {
         int c[4], sum = 0;
 #pragma unroll
@@ -680,7 +748,7 @@ __device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const
           acc += c[j];
         }
       }
-      __syncthreads();
+      frame_sync();
       const int bin = S->isc[2];
       kleft = S->isc[3];
       prefix |= (Key)bin << sh;
@@ -739,7 +807,7 @@ __device__ __forceinline__ int readoff_compact(const typename Cx<R>::C* X, const
     gout->count[li] = total;
     if (gout->status) gout->status[li] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
   }
-  __syncthreads();
+  frame_sync();
   return total;
 }
 
@@ -751,7 +819,7 @@ __device__ __forceinline__ int load_paths(const FrameArgs& A, const PathIO& gin,
   const int M = A.M, N = A.N, MN = M * N;
   if (gin.invalid) {
     bad = 1;
-    __syncthreads();
+    frame_sync();
     return 0;
   }
   int P = gin.count[li];
@@ -778,7 +846,7 @@ __device__ __forceinline__ int load_paths(const FrameArgs& A, const PathIO& gin,
     rec.pad0 = rec.pad1 = 0;
     out[p] = rec;
   }
-  bad = __syncthreads_or(bad);
+  bad = frame_sync_or(bad);
   return P;
 }
 

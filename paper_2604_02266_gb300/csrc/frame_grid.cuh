@@ -20,7 +20,7 @@ constexpr int kGridE = 8;         // most rows per work item (column k, rows j0 
 constexpr int kGridDftCols = 32;  // delay columns per Zak-transform tile
 constexpr uint32_t kGridMaxPolls = 1u << 22;
 
-constexpr int kGridMaxCtas = 1024;
+constexpr int kGridMaxCtas = 512;  // two CTAs per SM on up to 256 SMs
 
 struct GridBarrier {
   unsigned long long count;  // CTA arrivals since the launch began (zeroed before each launch)
@@ -188,16 +188,27 @@ __device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, 
 }
 
 // Sum of the CTAs' partials (each CTA's thread 0 stored part[blockIdx.x] before the barrier),
-// by warp 0 in a fixed order -- lane j adds CTAs j, j + 32, ..., then a butterfly over the
-// lanes -- so every CTA gets the same value; valid in thread 0.  Consecutive reductions
+// by warp 0 in a fixed order -- lane j loads CTAs j, j + 32, ..., j + 32 (kGridMaxCtas / 32 - 1)
+// (zero past the grid) and adds them pairwise (a tree of depth 5 instead of a chain of up to
+// 32 dependent FP64 additions, which cost ~56 cycles each on this part), then a butterfly over
+// the lanes -- so every CTA gets the same value; valid in thread 0.  Consecutive reductions
 // alternate between two sets of partials (part and part + gridDim.x): a CTA that has summed
 // one set may store into the other while a slower CTA is still summing the first.
 __device__ __forceinline__ double grid_partials(const double* part) {
   double s = 0.0;
   if (threadIdx.x < 32) {
-#pragma unroll 4
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(part + b);
-    s = warp_sum_f64(s);
+    constexpr int kPer = kGridMaxCtas / 32;
+    double v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int b = (int)threadIdx.x + 32 * i;
+      v[i] = b < (int)gridDim.x ? __ldcg(part + b) : 0.0;
+    }
+#pragma unroll
+    for (int w = 1; w < kPer; w <<= 1)
+#pragma unroll
+      for (int i = 0; i + w < kPer; i += 2 * w) v[i] += v[i + w];
+    s = warp_sum_f64(v[0]);
   }
   return s;
 }
@@ -251,6 +262,14 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM, tid = threadIdx.x;
   const int gtid = blockIdx.x * blockDim.x + tid, nthr = gridDim.x * blockDim.x;
   const int items = MN / E;  // (column k, row group j0 / E), k fastest
+  // CG work items are split evenly over the CTAs in contiguous ranges (consecutive columns,
+  // coalesced): every SM then carries the same number of items, so no grid barrier waits for
+  // SMs that hold twice the work of others
+  const int ipc = (items + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int it_beg = min(items, (int)blockIdx.x * ipc), it_end = min(items, it_beg + ipc);
+  // read-off: pilot-grid entries likewise, EQ consecutive q per thread, ranges in CTA order
+  const int qpc = ((MN + (int)gridDim.x - 1) / (int)gridDim.x + EQ - 1) / EQ * EQ;
+  const int q_beg = min(MN, (int)blockIdx.x * qpc), q_end = min(MN, q_beg + qpc);
   const size_t blk = ext_block_elems(M, N, E);
   const bool write_paths = (A.mode & kWritePaths) != 0;
   unsigned gen = 0;  // barriers passed
@@ -285,10 +304,10 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       uint32_t pass = 0;
 #pragma unroll
       for (int i = 0; i < EQ; ++i) {
-        const int q = gtid * EQ + i;
+        const int q = q_beg + tid * EQ + i;
         hv[i] = make_float2(0.f, 0.f);
         mb[i] = 0;
-        if (q < MN) {
+        if (q < q_end) {
           const int l = q >> logM;
           const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
           const C h = cscale(cmul(G.Y[q], tw<R>(A, (size_t)((-A.K0 * dl) & (MN - 1)))), scale);
@@ -393,7 +412,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
 #pragma unroll
       for (int i = 0; i < EQ; ++i) {
         if ((keep >> i) & 1u) {
-          const int q = gtid * EQ + i;
+          const int q = q_beg + tid * EQ + i;
           const int k = q & (M - 1), l = q >> logM;
           const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
           const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
@@ -445,14 +464,14 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
     // ------------------------------------------------ one operator apply
     if (A.mode & kApply) {
       C* src = A.adjoint ? G.extT : G.extP;
-      for (int it = gtid; it < items; it += nthr) {
+      for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
         const int k = it & (M - 1), j0 = (it >> logM) * E;
 #pragma unroll
         for (int i = 0; i < E; ++i) v[i] = reinterpret_cast<const C*>(io.v_in)[(size_t)(j0 + i) * M + k];
         write_ext<R, E, true>(src, A, k, j0, v);
       }
       if (!grid_sync(G.bar, gen)) return fail(io);
-      for (int it = gtid; it < items; it += nthr) {
+      for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
         const int k = it & (M - 1), j0 = (it >> logM) * E;
         if (A.adjoint) gather_adj<R, E, true>(src, blk, paths, runs, nruns, A, 0, k, j0, v);
         else gather_fwd<R, E, true>(src, blk, paths, runs, nruns, A, 0, k, j0, v);
@@ -472,7 +491,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         grid_dzt<E>(io.y_data, A.in_dtype, nullptr, G.extT, A, tile, wn);
       } else {
         const C* Yd = reinterpret_cast<const C*>(io.y_data);
-        for (int it = gtid; it < items; it += nthr) {
+        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
           const int k = it & (M - 1), j0 = (it >> logM) * E;
 #pragma unroll
           for (int i = 0; i < E; ++i) v[i] = Yd[(size_t)(j0 + i) * M + k];
@@ -483,7 +502,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
 
       // b = H^H y;  c = b, p = b, x = 0, c_n = ||c||^2
       R part = 0;
-      for (int it = gtid; it < items; it += nthr) {
+      for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
         const int k = it & (M - 1), j0 = (it >> logM) * E;
         gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
 #pragma unroll
@@ -511,7 +530,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
 
       for (int iter = 0; iter < io.iters && !S->isc[4]; ++iter) {
         // t = H p  (extP -> extT)
-        for (int it = gtid; it < items; it += nthr) {
+        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
           const int k = it & (M - 1), j0 = (it >> logM) * E;
           gather_fwd<R, E, true>(G.extP, blk, paths, runs, nruns, A, 0, k, j0, v);
           write_ext<R, E, true>(G.extT, A, k, j0, v);
@@ -519,7 +538,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         if (!grid_sync(G.bar, gen)) return fail(io);
         // a = H^H t + lambda p;  Re(p^H a)
         part = 0;
-        for (int it = gtid; it < items; it += nthr) {
+        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
           const int k = it & (M - 1), j0 = (it >> logM) * E;
           gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
 #pragma unroll
@@ -541,7 +560,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         const R alpha = (R)S->fsc[0];
         // x += alpha p;  c -= alpha a;  c_n' = ||c||^2
         part = 0;
-        for (int it = gtid; it < items; it += nthr) {
+        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
           const int k = it & (M - 1), j0 = (it >> logM) * E;
 #pragma unroll
           for (int i = 0; i < E; ++i) {
@@ -571,7 +590,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         const R beta = (R)S->fsc[1];
         if (iter + 1 < io.iters) {
           // p = c + beta p, and its extension
-          for (int it = gtid; it < items; it += nthr) {
+          for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
             const int k = it & (M - 1), j0 = (it >> logM) * E;
 #pragma unroll
             for (int i = 0; i < E; ++i) {
@@ -590,7 +609,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       }
       if (S->isc[1]) st |= kStNonFinite;
       if ((A.mode & kWriteX) && io.x_hat)
-        for (int it = gtid; it < items; it += nthr) {
+        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
           const int k = it & (M - 1), j0 = (it >> logM) * E;
 #pragma unroll
           for (int i = 0; i < E; ++i) {

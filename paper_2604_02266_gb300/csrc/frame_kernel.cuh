@@ -22,7 +22,7 @@ __device__ __forceinline__ double block_sum_to_thread0(R v, SharedHdr* S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   v = warp_sum(v);
   if (lane == 0) S->red[warp] = (double)v;
-  __syncthreads();
+  frame_sync();
   double d = 0.0;
   if (threadIdx.x == 0) {
     for (int b = 0; b < nwarps; b += 8) {
@@ -109,11 +109,22 @@ __device__ __forceinline__ FrameIO frame_io(const FrameArgs& A, int f, int csz) 
 // COEF: keep per-(path, column) coefficient tables in shared memory for the frame's lists
 // (forward and adjoint forms), so the CG's gathers read one value per path instead of a path
 // record, a twiddle-table entry and a complex product.
-template <typename R, int E, int NB, int TMAX, int MINB, bool COEF>
+// PACK: the kernel may be launched with a two-dimensional block of blockDim.y frames per CTA;
+// without it the block is one-dimensional, which the compiler is told (the frame-scope barriers
+// and the shared-memory base then reduce to their one-frame forms at no register cost).
+template <typename R, int E, int NB, int TMAX, int MINB, bool COEF, bool PACK>
 __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant__ FrameArgs A, int radix) {
   using C = typename Cx<R>::C;
   using PathRec = PathRecT<R>;
-  extern __shared__ __align__(128) unsigned char smem[];
+  if constexpr (!PACK) {
+    __builtin_assume(blockDim.y == 1);
+    __builtin_assume(threadIdx.y == 0);
+  }
+  extern __shared__ __align__(128) unsigned char smem_all[];
+  // frames packed into one CTA (2D block): row threadIdx.y owns its own slice of shared memory
+  const size_t row_bytes =
+      (frame_smem_bytes(A.M, A.N, E, A.nrx, A.ntx, A.p_max, (int)sizeof(R), COEF) + 127) & ~size_t(127);
+  unsigned char* smem = smem_all + (size_t)threadIdx.y * row_bytes;
   SharedHdr* S = reinterpret_cast<SharedHdr*>(smem);
   const int nlists = A.nrx * A.ntx;
   size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
@@ -159,14 +170,14 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
   const bool write_paths = (A.mode & kWritePaths) != 0;
 
   if (tid == 0) mbar_init(&S->mbar, 1);
-  __syncthreads();
+  frame_sync();
   uint32_t phase = 0;
 
   for (;;) {
     if (tid == 0) S->isc[0] = atomicAdd(A.work_counter, 1);
-    __syncthreads();
+    frame_sync();
     const int f = S->isc[0];
-    __syncthreads();
+    frame_sync();
     if (f >= A.n_frames) break;
     const FrameIO io = frame_io(A, f, (int)sizeof(C));
     const PathIO* gout = (write_paths && io.paths.count) ? &io.paths : nullptr;
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
       }
       have_paths = true;
     }
-    __syncthreads();
+    frame_sync();
     if (st & kStTimeout) {
       if (io.status && tid == 0) *io.status = status_from_bits(st);
       break;  // barrier phases are no longer trustworthy: stop this CTA
@@ -248,7 +259,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           for (int i = 0; i < E; ++i) v[b][i] = reinterpret_cast<const C*>(io.v_in)[(size_t)b * MN + (size_t)(j0 + i) * M + k];
           write_ext<R, E>(ext + b * blk, A, k, j0, v[b]);
         }
-      __syncthreads();
+      frame_sync();
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         if (b < nout) {
@@ -257,7 +268,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
           for (int i = 0; i < E; ++i) reinterpret_cast<C*>(io.u_out)[(size_t)b * MN + (size_t)(j0 + i) * M + k] = v[b][i];
         }
-      __syncthreads();
+      frame_sync();
       if (io.status && tid == 0) *io.status = status_from_bits(st);
       continue;
     }
@@ -297,7 +308,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             const int P = readoff_compact<R, E>(ext, A, (R)io.theta, io.a_pilot, paths, S, gout, 0, trunc);
             if (tid == 0) cnt[0] = P;
             if (trunc) st |= kStTrunc;
-            __syncthreads();
+            frame_sync();
             finalize_lists();
           }
           // remove the pilot's response a_pilot H e_(K0,L0) (grid still scaled by sqrt(N))
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
             C* y = ext + (size_t)bitrev(lr, A.logN) * M + kr;
             *y = csub(*y, val);
           }
-          __syncthreads();
+          frame_sync();
         }
 #pragma unroll
         for (int r = 0; r < NB; ++r)
@@ -320,12 +331,12 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
             for (int i = 0; i < E; ++i)
               v[r][i] = cscale(ext[r * blk + (size_t)bitrev(j0 + i, A.logN) * M + k], (R)A.inv_sqrtN);
-        __syncthreads();
+        frame_sync();
       }
 #pragma unroll
       for (int r = 0; r < NB; ++r)
         if (r < A.nrx) write_ext<R, E>(ext + r * blk, A, k, j0, v[r]);
-      __syncthreads();
+      frame_sync();
 
       // b = H^H y;  c = b, p = b, x = 0, c_n = ||c||^2   (Algorithm 1, initialisation)
       C c[NB][E], p[NB][E];
@@ -346,11 +357,11 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
         S->isc[1] = isfinite(cn) ? 0 : 1;
         S->isc[4] = cn <= stop_at ? 1 : 0;
       }
-      __syncthreads();  // all gathers of y_ext done; flags published
+      frame_sync();  // all gathers of y_ext done; flags published
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (t < A.ntx) write_ext<R, E>(ext + t * blk, A, k, j0, p[t]);
-      __syncthreads();
+      frame_sync();
 
       // the stopping test's flag is read after the barrier that follows the p update
       for (int it = 0; it < io.iters && !S->isc[4]; ++it) {
@@ -358,11 +369,11 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
         for (int r = 0; r < NB; ++r)
           if (r < A.nrx) gather_fwd<R, E, false, COEF>(ext, blk, paths, runs, nruns, A, r, k, j0, v[r], coefF);
-        __syncthreads();
+        frame_sync();
 #pragma unroll
         for (int r = 0; r < NB; ++r)
           if (r < A.nrx) write_ext<R, E>(ext + r * blk, A, k, j0, v[r]);
-        __syncthreads();
+        frame_sync();
         // a = H^H t + lambda p;  Re(p^H a)
         part = 0;
 #pragma unroll
@@ -378,7 +389,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           }
         const double pa = block_sum_to_thread0(part, S);
         if (tid == 0) S->fsc[0] = cg_ratio<R>(cn, pa);  // alpha, FP64
-        __syncthreads();
+        frame_sync();
         const R alpha = (R)S->fsc[0];
         // x += alpha p;  c -= alpha a;  c_n' = ||c||^2
         part = 0;
@@ -400,7 +411,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           if (cn_new <= stop_at) S->isc[4] = 1;
           cn = cn_new;
         }
-        __syncthreads();
+        frame_sync();
         const R beta = (R)S->fsc[1];
         // p = c + beta p
 #pragma unroll
@@ -415,7 +426,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
 #pragma unroll
           for (int t = 0; t < NB; ++t)
             if (t < A.ntx) write_ext<R, E>(ext + t * blk, A, k, j0, p[t]);
-          __syncthreads();
+          frame_sync();
         }
       }
       if (S->isc[1]) st |= kStNonFinite;
@@ -442,13 +453,13 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
       // constellation's unrolled code is live at a time
       uint8_t* lab = reinterpret_cast<uint8_t*>(ext);  // labels, bit j of the symbol at bit j
       C* xs = reinterpret_cast<C*>(ext) + (A.ntx * MN + sizeof(C) - 1) / sizeof(C);
-      __syncthreads();  // ext no longer read by anyone
+      frame_sync();  // ext no longer read by anyone
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (t < A.ntx)
 #pragma unroll
           for (int i = 0; i < E; ++i) xs[(size_t)t * MN + (j0 + i) * M + k] = x[t][i];
-      __syncthreads();
+      frame_sync();
       const R pd = (R)io.pam_d;
       auto demap_all = [&](auto hb) {
         constexpr int HB = decltype(hb)::value;
@@ -468,7 +479,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
       if (bps == 2) demap_all(std::integral_constant<int, 1>{});
       else if (bps == 4) demap_all(std::integral_constant<int, 2>{});
       else demap_all(std::integral_constant<int, 3>{});
-      __syncthreads();
+      frame_sync();
       if (io.bits) {
         // 8 consecutive symbols fill exactly bps bytes (bits LSB first, symbol by symbol)
         const int groups = A.ntx * MN / 8;
@@ -486,7 +497,7 @@ __global__ void __launch_bounds__(TMAX, MINB) frame_kernel(const __grid_constant
           }
         }
       }
-      __syncthreads();
+      frame_sync();
     }
     publish_status(A, io.status, st);
   }

@@ -75,6 +75,12 @@
 #ifndef V_R
 #define V_R float
 #endif
+// the variants small frames run on also get an instantiation that packs several frames per CTA
+#if ZOTFS_VARIANT == 0 || ZOTFS_VARIANT == 2 || ZOTFS_VARIANT == 4 || ZOTFS_VARIANT == 5 || ZOTFS_VARIANT == 8
+#define V_PACK 1
+#else
+#define V_PACK 0
+#endif
 #ifndef V_COEF
 #define V_COEF 0
 #endif
@@ -86,7 +92,15 @@
 namespace zotfs {
 
 using KernT = void (*)(const FrameArgs, int);
-static KernT kern() { return frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB, (V_COEF != 0)>; }
+static KernT kern(bool pack) {
+#if V_PACK
+  if (pack) return frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB, (V_COEF != 0), true>;
+#endif
+  (void)pack;
+  return frame_kernel<V_R, V_E, V_NB, V_TMAX, V_MINB, (V_COEF != 0), false>;
+}
+
+bool VFUN(_packs)() { return V_PACK != 0; }
 
 void VFUN(_info)(int& E, int& NB, int& TMAX, int& real_bytes, int& minb, int& coef) {
   E = V_E;
@@ -100,30 +114,38 @@ void VFUN(_info)(int& E, int& NB, int& TMAX, int& real_bytes, int& minb, int& co
 // Raise the kernel's dynamic shared-memory limit to at least `smem` on the current device.
 // The limit only ever grows (a lower value set later would break launches that rely on the
 // higher one), and the server's scheduler thread launches concurrently with user threads.
-static cudaError_t grant_smem(size_t smem) {
+static cudaError_t grant_smem(size_t smem, bool pack) {
   static std::mutex mu;
-  static int granted[64] = {0};
+  static int granted[2][64] = {{0}};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
-  if (dev < 64 && granted[dev] >= (int)smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(kern(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && dev < 64) granted[dev] = (int)smem;
+  if (dev < 64 && granted[pack][dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern(pack), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev < 64) granted[pack][dev] = (int)smem;
   return e;
 }
 
-cudaError_t VFUN(_launch)(const FrameArgs& A, int radix, int grid, int T, size_t smem, cudaStream_t stream) {
-  cudaError_t e = grant_smem(smem);
+// fpc frames per CTA: a (T, fpc) block, fpc rows of `smem` bytes of shared memory each (rounded
+// to 128 bytes, as the kernel places them).
+static size_t cta_smem(size_t smem, int fpc) { return fpc <= 1 ? smem : ((smem + 127) & ~size_t(127)) * (size_t)fpc; }
+
+cudaError_t VFUN(_launch)(const FrameArgs& A, int radix, int grid, int T, size_t smem, int fpc, cudaStream_t stream) {
+  if (fpc < 1 || !V_PACK) fpc = 1;
+  const bool pack = fpc > 1;
+  cudaError_t e = grant_smem(cta_smem(smem, fpc), pack);
   if (e != cudaSuccess) return e;
-  kern()<<<grid, T, smem, stream>>>(A, radix);
+  kern(pack)<<<grid, dim3((unsigned)T, (unsigned)fpc), cta_smem(smem, fpc), stream>>>(A, radix);
   return cudaGetLastError();
 }
 
-cudaError_t VFUN(_occupancy)(int T, size_t smem, int& blocks) {
-  cudaError_t e = grant_smem(smem);
+cudaError_t VFUN(_occupancy)(int T, size_t smem, int fpc, int& blocks) {
+  if (fpc < 1 || !V_PACK) fpc = 1;
+  const bool pack = fpc > 1;
+  cudaError_t e = grant_smem(cta_smem(smem, fpc), pack);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern(), T, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern(pack), T * fpc, cta_smem(smem, fpc));
 }
 
 }  // namespace zotfs

@@ -96,16 +96,24 @@ struct FrameCfg {
 bool choose_frame_cfg(int M, int N, int nrx, int ntx, int p_max, int threads_override, FrameCfg& cfg,
                       int real_bytes = 4);
 
-// Launch the persistent frame kernel (counter reset included).  n_frames > 0.
+// Launch the persistent frame kernel (counter reset included).  n_frames > 0.  frames_per_cta
+// frames are packed into each CTA (0 or 1: one), reduced to what the variant's thread limit
+// and shared memory allow.
 zotfs_status launch_frame_kernel(zotfs_plan_s* plan, const FrameCfg& cfg, FrameArgs& A, int radix,
-                                 int ctas_per_sm, cudaStream_t stream);
+                                 int ctas_per_sm, cudaStream_t stream, int frames_per_cta = 1);
+// The frames per CTA a launch of `cfg` can take, at most `want`.
+int frames_per_cta_for(const FrameCfg& cfg, int want);
 
-// Variant table implemented in frame_variants.cu
+// Variant table implemented in frame_variants.cu.  fpc: frames packed into one CTA (a (T, fpc)
+// block, `smem` bytes of shared memory per frame; T * fpc <= the variant's TMAX, fpc <= 15).
 int frame_variant_count();
 bool frame_variant_info(int v, int& E, int& NB, int& TMAX, int& real_bytes, int& minb, int& coef);
 cudaError_t frame_variant_launch(int v, const FrameArgs& A, int radix, int grid, int T, size_t smem,
-                                 cudaStream_t stream);
-cudaError_t frame_variant_occupancy(int v, int T, size_t smem, int& blocks);
+                                 cudaStream_t stream, int fpc = 1);
+cudaError_t frame_variant_occupancy(int v, int T, size_t smem, int& blocks, int fpc = 1);
+// Whether variant v has an instantiation that packs frames (the small-frame variants).
+bool frame_variant_packs(int v);
+constexpr int kMaxFramesPerCta = 8;
 
 // Large-frame kernel (big_variant.cu)
 struct BigCfg {

@@ -84,11 +84,11 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
 // Forward unitary DFT along the warp's N elements (element e of lane holds index lane + 32 e):
 // decimation in frequency, natural order in, bit-reversed order out.
 template <int EPL>
-__device__ __forceinline__ void warp_dft(float2 (&a)[EPL], const MrcArgs& A, int lane) {
-  const int N = A.N, M = A.M;
+__device__ __forceinline__ void warp_dft(float2 (&a)[EPL], const MrcArgs& A, const float2* wN, int lane) {
+  const int N = A.N;
   int h = N >> 1;
   if (EPL == 2) {  // N = 64: the span-32 stage pairs the lane's two elements
-    const float2 w = conjf2(__ldg(A.W + (size_t)lane * M));  // exp(-j2pi lane/64)
+    const float2 w = conjf2(wN[lane]);  // exp(-j2pi lane/64)
     const float2 u = a[0], v = a[EPL - 1];
     a[0] = cadd(u, v);
     a[EPL - 1] = cmul(csub(u, v), w);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void warp_dft(float2 (&a)[EPL], const MrcArgs& A, int
   for (; h >= 1; h >>= 1) {
     const bool upper = (lane & h) != 0;
     const int j = lane & (h - 1);
-    const float2 w = conjf2(__ldg(A.W + (size_t)(j * (N / (2 * h))) * M));  // exp(-j2pi j/(2h))
+    const float2 w = conjf2(wN[j * (N / (2 * h))]);  // exp(-j2pi j/(2h))
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
       const float2 p = shfl_xor2(a[e], h);
@@ -110,13 +110,13 @@ __device__ __forceinline__ void warp_dft(float2 (&a)[EPL], const MrcArgs& A, int
 
 // Inverse unitary DFT: decimation in time, bit-reversed order in, natural order out.
 template <int EPL>
-__device__ __forceinline__ void warp_idft(float2 (&a)[EPL], const MrcArgs& A, int lane) {
-  const int N = A.N, M = A.M;
+__device__ __forceinline__ void warp_idft(float2 (&a)[EPL], const MrcArgs& A, const float2* wN, int lane) {
+  const int N = A.N;
   const int hmax = N < 32 ? N : 32;
   for (int h = 1; h < hmax; h <<= 1) {
     const bool upper = (lane & h) != 0;
     const int j = lane & (h - 1);
-    const float2 w = __ldg(A.W + (size_t)(j * (N / (2 * h))) * M);  // exp(+j2pi j/(2h))
+    const float2 w = wN[j * (N / (2 * h))];  // exp(+j2pi j/(2h))
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
       const float2 p = shfl_xor2(a[e], h);
@@ -124,7 +124,7 @@ __device__ __forceinline__ void warp_idft(float2 (&a)[EPL], const MrcArgs& A, in
     }
   }
   if (EPL == 2) {
-    const float2 w = __ldg(A.W + (size_t)lane * M);  // exp(+j2pi lane/64)
+    const float2 w = wN[lane];  // exp(+j2pi lane/64)
     const float2 u = a[0], t = cmul(a[EPL - 1], w);
     a[0] = cadd(u, t);
     a[EPL - 1] = csub(u, t);
@@ -144,17 +144,21 @@ __device__ __forceinline__ int nearest_level(float x, int m, float d) {
   return i < 0 ? 0 : (i > m - 1 ? m - 1 : i);
 }
 
-// Gain of branch b (paths [s, e) of the sorted list) for source delay k at time index n.
-__device__ __forceinline__ float2 branch_gain(const MrcArgs& A, const float2* hs, const int* dls, int s, int e, int k,
-                                              int n) {
-  const int MN = A.M * A.N;
-  const int t0 = k + (n << A.logM);
+// Gain of branch b (paths [s, e) of the sorted list) for source delay k at time index n:
+// sum_p h_p W[dl_p (k + n M)] = sum_p (h_p W[dl_p k]) exp(j2pi dl_p n / N).  The first factor's
+// table index is the same in every lane (one broadcast load); the second comes from the N-entry
+// shared table wN.  (Reading W[dl_p (k + n M)] directly puts the lanes dl_p M entries apart in
+// the MN-entry table: 32 cache lines per load.)
+__device__ __forceinline__ float2 branch_gain(const MrcArgs& A, const float2* wN, const float2* hs, const int* dls,
+                                              int s, int e, int k, int n) {
+  const int MN = A.M * A.N, N = A.N;
   float2 G = make_float2(0.f, 0.f);
   for (int p = s; p < e; ++p) {
-    const float2 w = __ldg(A.W + ((dls[p] * t0) & (MN - 1)));
-    const float2 h = hs[p];
-    G.x = fmaf(h.x, w.x, fmaf(-h.y, w.y, G.x));
-    G.y = fmaf(h.x, w.y, fmaf(h.y, w.x, G.y));
+    const int dl = dls[p];
+    const float2 hk = cmul(hs[p], __ldg(A.W + ((dl * k) & (MN - 1))));
+    const float2 w = wN[(dl * n) & (N - 1)];
+    G.x = fmaf(hk.x, w.x, fmaf(-hk.y, w.y, G.x));
+    G.y = fmaf(hk.x, w.y, fmaf(hk.y, w.x, G.y));
   }
   return G;
 }
@@ -167,6 +171,10 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
   const int m = 1 << A.hb;
   const float d = A.pam_d;
   const MrcSmem L = mrc_smem_layout(MN, A.p_max);
+  // wN[j] = exp(j2pi j / N) = W[j M], shared by the CTA's warps, after their slices
+  float2* wN = reinterpret_cast<float2*>(smem + (size_t)A.warps * L.total);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) wN[j] = __ldg(A.W + (size_t)j * M);
+  __syncthreads();
   unsigned char* base = smem + (size_t)warp * L.total;
   float2* dy = reinterpret_cast<float2*>(base + L.dy);  // residual, DT layout [k][n]
   uint8_t* lab = base + L.lab;                           // decisions [k][bit-reversed l]
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
           const int l = pos < N ? (int)(__brev((unsigned)pos) >> (32 - logN)) : 0;
           a[e] = pos < N ? yd[(size_t)l * M + k] : make_float2(0.f, 0.f);
         }
-        warp_idft<EPL>(a, A, lane);
+        warp_idft<EPL>(a, A, wN, lane);
 #pragma unroll
         for (int e = 0; e < EPL; ++e)
           if (lane + 32 * e < N) dy[k * N + lane + 32 * e] = a[e];
@@ -290,14 +298,14 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
           g[e] = make_float2(0.f, 0.f);
           D[e] = 0.f;
         }
-        if (it > 0) warp_idft<EPL>(old, A, lane);  // current estimate of vector k, DT
+        if (it > 0) warp_idft<EPL>(old, A, wN, lane);  // current estimate of vector k, DT
         for (int b = 0; b < nb; ++b) {
           const int dd = brd[b], kt = (k + dd) & (M - 1), fsh = (k + dd) >> A.logM;
 #pragma unroll
           for (int e = 0; e < EPL; ++e) {
             const int n = lane + 32 * e;
             if (n < N) {
-              const float2 G = branch_gain(A, hs, dls, brs[b], brs[b + 1], k, n);
+              const float2 G = branch_gain(A, wN, hs, dls, brs[b], brs[b + 1], k, n);
               const float2 r = dy[kt * N + ((n + fsh) & (N - 1))];
               g[e].x = fmaf(G.x, r.x, fmaf(G.y, r.y, g[e].x));  // conj(G) r
               g[e].y = fmaf(G.x, r.y, fmaf(-G.y, r.x, g[e].y));
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
             c[e].y = fmaf(g[e].y, inv, c[e].y);
           }
         }
-        warp_dft<EPL>(c, A, lane);  // c: DD values at bit-reversed positions
+        warp_dft<EPL>(c, A, wN, lane);  // c: DD values at bit-reversed positions
         float2 s[EPL];
         uint8_t nl[EPL];
 #pragma unroll
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
             }
           }
         }
-        warp_idft<EPL>(s, A, lane);  // new estimate of vector k, DT
+        warp_idft<EPL>(s, A, wN, lane);  // new estimate of vector k, DT
         float2 delta[EPL];
 #pragma unroll
         for (int e = 0; e < EPL; ++e) delta[e] = csub(s[e], old[e]);
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
           for (int e = 0; e < EPL; ++e) {
             const int n = lane + 32 * e;
             if (n < N) {
-              const float2 G = branch_gain(A, hs, dls, brs[b], brs[b + 1], k, n);
+              const float2 G = branch_gain(A, wN, hs, dls, brs[b], brs[b + 1], k, n);
               float2* r = dy + kt * N + ((n + fsh) & (N - 1));
               *r = csub(*r, cmul(G, delta[e]));
             }
@@ -422,13 +430,13 @@ extern "C" zotfs_status zotfs_equalize_mrc(zotfs_plan plan, const void* y, int y
   A.status = status;
   const size_t per_warp = mrc_smem_layout(plan->M * plan->N, A.p_max).total;
   const size_t kSmemCap = 227 * 1024;
-  int warps = (int)std::min<size_t>(12, kSmemCap / per_warp);
+  int warps = (int)std::min<size_t>(12, (kSmemCap - (size_t)plan->N * sizeof(float2)) / per_warp);
   if (warps < 1) {
     set_error("zotfs_equalize_mrc: frame does not fit one SM's shared memory");
     return ZOTFS_EUNSUPPORTED;
   }
   A.warps = warps;
-  const size_t smem = per_warp * warps;
+  const size_t smem = per_warp * warps + (size_t)plan->N * sizeof(float2);
   int* counter = plan->d_counters + (plan->counter_next++ & 63);
   A.work_counter = counter;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);

@@ -499,6 +499,11 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
   s->split = o.light_work > 0 && o.waves_in_flight >= 2;
   if (s->split)  // the first half of the slots serve light frames
     for (int i = 0; i < o.waves_in_flight; ++i) s->waves[i].cls = i < o.waves_in_flight / 2 ? 0 : 1;
+  // Light waves run on the device's highest-priority streams: when an SM frees up, their
+  // waiting CTAs are placed before the heavy waves' (heavy CTAs run to the end of their frame;
+  // nothing is preempted).
+  int prio_least = 0, prio_greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   for (Wave& w : s->waves) {
     if (st) break;
     const int n = o.max_wave_frames;
@@ -511,9 +516,10 @@ zotfs_status zotfs_server_create(const zotfs_server_opts* opts, zotfs_server* ou
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&w.d_status), w.h_status, 0);
     if (e == cudaSuccess && s->big_slots)
       e = dev_alloc(&w.d_big, s->big_slot_bytes * (size_t)s->big_slots);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.main, cudaStreamNonBlocking);
+    const int prio = w.cls == 0 ? prio_greatest : prio_least;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&w.main, cudaStreamNonBlocking, prio);
     for (int i = 0; i < kWorkers && e == cudaSuccess; ++i) {
-      e = cudaStreamCreateWithFlags(&w.work[i], cudaStreamNonBlocking);
+      e = cudaStreamCreateWithPriority(&w.work[i], cudaStreamNonBlocking, prio);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.wdone[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.start, cudaEventDisableTiming);

@@ -27,7 +27,7 @@ zotfs_status tinval(const std::string& m) {
 constexpr int kTuneFramesPerSm = 4;
 
 struct Candidate {
-  int threads, radix, ctas, cluster;
+  int threads, radix, ctas, cluster, fpc;
 };
 
 // Launch shapes worth timing for one (M, N, n_rx, n_tx, p_max) group.
@@ -38,20 +38,24 @@ std::vector<Candidate> candidates(int M, int N, int nrx, int ntx, int p_max) {
   for (int T = 32; T <= 1024 && T <= MN; T += 32) {
     FrameCfg cfg;
     if (!choose_frame_cfg(M, N, nrx, ntx, p_max, T, cfg) || cfg.T != T) continue;
-    int occ = 0;
-    if (frame_variant_occupancy(cfg.variant, cfg.T, cfg.smem, occ) != cudaSuccess || occ < 1) continue;
-    any = true;
-    for (int radix : {2, 4})
-      for (int c = 1; c <= occ; ++c) out.push_back({T, radix, c, 0});
+    // frames per CTA: one, and packings of 2 and 4 small frames where the kernel takes them
+    for (int fpc : {1, 2, 4}) {
+      if (frames_per_cta_for(cfg, fpc) != fpc) continue;
+      int occ = 0;
+      if (frame_variant_occupancy(cfg.variant, cfg.T, cfg.smem, occ, fpc) != cudaSuccess || occ < 1) continue;
+      any = true;
+      for (int radix : {2, 4})
+        for (int c = 1; c <= occ; ++c) out.push_back({T, radix, c, 0, fpc});
+    }
   }
   if (!any) {  // the large-frame kernels: fixed threads and occupancy; radix, CTAs per frame
     BigCfg big;
     if (choose_big_cfg(M, N, nrx, ntx, p_max, big))
-      for (int radix : {2, 4}) out.push_back({0, radix, 0, 1});
+      for (int radix : {2, 4}) out.push_back({0, radix, 0, 1, 1});
     for (int cl : {2, 4}) {
       BigClusterCfg bc;
       if (choose_big_cluster_cfg(M, N, nrx, ntx, p_max, cl, bc))
-        for (int radix : {2, 4}) out.push_back({0, radix, 0, cl});
+        for (int radix : {2, 4}) out.push_back({0, radix, 0, cl, 1});
     }
   }
   return out;
@@ -67,6 +71,17 @@ float time_shape(const std::vector<zotfs_frame_desc>& D, const Candidate& c, int
   o.ctas_per_sm = c.ctas;
   o.max_sms = max_sms;
   o.cluster = c.cluster;
+  // frames per CTA travel in a tuning entry of the group's shape (the timing set is one shape)
+  zotfs_tuning_entry te{};
+  if (!D.empty()) {
+    te.M = D[0].M;
+    te.N = D[0].N;
+    te.n_rx = D[0].n_rx;
+    te.n_tx = D[0].n_tx;
+    te.tuning.frames_per_cta = c.fpc;
+    o.n_tuning = 1;
+    o.tuning = &te;
+  }
   zotfs_batch b = nullptr;
   if (zotfs_batch_create(D.data(), (int)D.size(), &o, &b) != ZOTFS_OK) return -1.f;
   float ms = -1.f;
@@ -216,7 +231,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
     R.best.n_rx = d0.n_rx;
     R.best.n_tx = d0.n_tx;
     R.n_frames = target;
-    R.ms_default = time_shape(T, Candidate{0, 0, 0, 0}, 0, warmup, reps, d_status, stream, e0, e1);
+    R.ms_default = time_shape(T, Candidate{0, 0, 0, 0, 0}, 0, warmup, reps, d_status, stream, e0, e1);
     if (R.ms_default < 0.f) {
       st = ZOTFS_EINVAL;
       set_error(std::string("autotune: default launch shape failed: ") + zotfs_last_error());
@@ -232,6 +247,7 @@ zotfs_status zotfs_autotune(const zotfs_frame_desc* descs, int n_frames, const z
         R.best.tuning.fft_radix = c.radix;
         R.best.tuning.ctas_per_sm = c.ctas;
         R.best.tuning.cluster = c.cluster;
+        R.best.tuning.frames_per_cta = c.fpc;
       }
     }
     R.sm_ms_per_frame = R.ms_best * (float)sm_count / (float)target;

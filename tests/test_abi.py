@@ -54,13 +54,13 @@ def test_struct_layouts_match_header_sizes(libpath):
     # all fields are 4-byte ints/floats or 8-byte pointers in declaration order
     assert ctypes.sizeof(Z.zotfs_options) == 40
     assert ctypes.sizeof(Z.zotfs_paths) == 5 * 8 + 8
-    assert ctypes.sizeof(Z.zotfs_tuning) == 16
+    assert ctypes.sizeof(Z.zotfs_tuning) == 20
     assert ctypes.sizeof(Z.zotfs_frame_desc) == 16 * 4 + 9 * 8  # 16 scalars, 9 pointers
     assert ctypes.sizeof(Z.zotfs_request) == 10 * 4 + 3 * 8  # 10 scalars, 2 pointers, the tag
     assert ctypes.sizeof(Z.zotfs_batch_opts) == 4 * 4 + 8 + 4 + 4  # ..., max_sms, cluster
     assert ctypes.sizeof(Z.zotfs_autotune_opts) == 12
-    assert ctypes.sizeof(Z.zotfs_tuning_entry) == 4 * 4 + 16
-    assert ctypes.sizeof(Z.zotfs_tuning_result) == 4 * 4 + 16 + 5 * 4
+    assert ctypes.sizeof(Z.zotfs_tuning_entry) == 4 * 4 + 20
+    assert ctypes.sizeof(Z.zotfs_tuning_result) == 4 * 4 + 20 + 5 * 4
 
 
 def test_argument_errors_without_gpu(libpath):
@@ -148,8 +148,8 @@ def test_tuning_file_round_trip(tmp_path, libpath):
     import json
     from paper_2604_02266_gb300 import load_tuning, save_tuning
     res = [{"M": 64, "N": 32, "n_rx": 1, "n_tx": 1, "threads_per_frame": 256, "fft_radix": 4, "ctas_per_sm": 2,
-            "cluster": 0, "sm_ms_per_frame": 0.08, "ms_best": 0.5, "ms_default": 0.6, "n_candidates": 9,
-            "n_frames": 1024},
+            "cluster": 0, "frames_per_cta": 2, "sm_ms_per_frame": 0.08, "ms_best": 0.5, "ms_default": 0.6,
+            "n_candidates": 9, "n_frames": 1024},
            {"M": 128, "N": 64, "n_rx": 4, "n_tx": 4, "threads_per_frame": 512, "fft_radix": 2, "ctas_per_sm": 1,
             "cluster": 4, "sm_ms_per_frame": 9.5, "ms_best": 17.0, "ms_default": 17.7, "n_candidates": 6,
             "n_frames": 256}]
@@ -158,8 +158,9 @@ def test_tuning_file_round_trip(tmp_path, libpath):
     doc = json.loads(path.read_text())
     assert doc["format"] == "zotfs-tuning-1" and doc["device"] == "GB300" and len(doc["entries"]) == 2
     assert load_tuning(str(path)) == [
-        ((64, 32, 1, 1), {"threads_per_frame": 256, "fft_radix": 4, "ctas_per_sm": 2, "cluster": 0}),
-        ((128, 64, 4, 4), {"threads_per_frame": 512, "fft_radix": 2, "ctas_per_sm": 1, "cluster": 4})]
+        ((64, 32, 1, 1), {"threads_per_frame": 256, "fft_radix": 4, "ctas_per_sm": 2, "cluster": 0, "frames_per_cta": 2}),
+        ((128, 64, 4, 4), {"threads_per_frame": 512, "fft_radix": 2, "ctas_per_sm": 1, "cluster": 4,
+                           "frames_per_cta": 0})]  # files written before the field existed read as 0
     other = tmp_path / "other.json"
     other.write_text(json.dumps({"format": "something-else", "entries": []}))
     with pytest.raises(ValueError):
