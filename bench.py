@@ -326,6 +326,22 @@ def impl_zotfs(args):
     P = probe["paths"].count.cpu().numpy()
     status = probe["status"].cpu().numpy()
     total_flops = float(sum(flops_per_frame(int(p)) for p in P))
+    # decoding quality of the batch (untimed): BER of the hard bits against the transmitted
+    # bits, with the benchmark's p_max = 64 and with p_max = 256 (no list of this batch is cut)
+    errs64 = bit_errors(probe["bits"].cpu().numpy(), batch["bits"], FRAMES)
+    wide = Plan(M, N, 1, 1, Q, p_max=256)
+    probe256 = wide.rx(yp[0], yd[0], nv, th, ITERS, FRAMES, want_paths=True)
+    errs256 = bit_errors(probe256["bits"].cpu().numpy(), batch["bits"], FRAMES)
+    P256 = probe256["paths"].count.cpu().numpy()
+    nbits = FRAMES * M * N * int(np.log2(Q))
+    quality = {"ber_p_max_64": float(errs64.sum()) / nbits, "ber_p_max_256": float(errs256.sum()) / nbits,
+               "paths_p_max_256": {"mean": float(P256.mean()), "max": int(P256.max())},
+               "ber_by_snr_db": {int(snr): {"p_max_64": float(errs64[batch["snr_db"] == snr].sum()) /
+                                            max(1, int((batch["snr_db"] == snr).sum()) * M * N * int(np.log2(Q))),
+                                            "p_max_256": float(errs256[batch["snr_db"] == snr].sum()) /
+                                            max(1, int((batch["snr_db"] == snr).sum()) * M * N * int(np.log2(Q)))}
+                                 for snr in (0, 10, 20, 30)}}
+    del wide, probe256
 
     def step(i):
         plan.rx(yp[i % copies], yd[i % copies], nv, th, ITERS, FRAMES, out=outs)
@@ -503,6 +519,7 @@ def impl_zotfs(args):
                       # P_est histogram: [0, 8), [8, 16), ..., [56, 64), and exactly 64 (= p_max)
                       "hist_edges": PATH_HIST_EDGES,
                       "hist_counts": np.histogram(P, bins=PATH_HIST_EDGES)[0].tolist()},
+            "decoding": quality,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
