@@ -373,14 +373,42 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
 // registers, mac_run accumulates.  Kernels whose extensions live in global memory issue two
 // runs' loads before either accumulates (two L2 round trips in flight per thread instead of
 // one after the other).
+// Where a gather's runs read: RS, the distance between rows of a row-major extension; the
+// coefficients formed from the path records and the frame's twiddle table, or with ct from a
+// table of the adjoint factors of a CTA's own delay columns, ct[p ct_rs + k - ct_c0] =
+// h_p W[dl_p k] (path p in list order), whose forward factor is ct[..] phi[p] with
+// phi[p] = W[-dl_p dk_p] (so that hf_p W[dl_p k] = h_p W[dl_p k] phi[p]).
+template <typename R>
+struct GatherAt {
+  size_t RS;
+  const typename Cx<R>::C* ct;
+  const typename Cx<R>::C* phi;
+  int ct_rs, ct_c0;
+};
+
+// Coefficient D of path p (list order, delay-Doppler (dk, dl0 + m) of run rr) at column k.
+template <typename R, bool kFwd>
+__device__ __forceinline__ typename Cx<R>::C path_coef(const FrameArgs& A, const GatherAt<R>& at,
+                                                       const PathRecT<R>* pl, const RunRec& rr, int m, int k) {
+  const int p = rr.start + m;
+  if (at.ct) {  // adjoint entries unconjugated: the caller's final combine conjugates them
+    const typename Cx<R>::C c = at.ct[(size_t)p * at.ct_rs + (k - at.ct_c0)];
+    return kFwd ? cmul(c, at.phi[p]) : c;
+  }
+  const PathRecT<R> rec = pl[p];
+  const typename Cx<R>::C t = tab<R>(A, (rr.dl0 + m + (A.N >> 1)) * A.M + k);
+  return kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+}
+
 template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
 __device__ __forceinline__ void load_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
                                          const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
-                                         int j0, typename Cx<R>::C (&W)[L + E - 1], typename Cx<R>::C (&D)[L]) {
+                                         int j0, const GatherAt<R>& at, typename Cx<R>::C (&W)[L + E - 1],
+                                         typename Cx<R>::C (&D)[L]) {
   using C = typename Cx<R>::C;
   const int M = A.M, N = A.N;
   const int CS = kRowMajor ? 1 : N + E + 3;
-  const size_t RS = kRowMajor ? (size_t)(2 * M) : 1;
+  const size_t RS = at.RS;
   const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
   const C* a = src + (size_t)row0 * RS + (kFwd ? -rr.dk : rr.dk) * CS;
 #pragma unroll
@@ -391,9 +419,7 @@ __device__ __forceinline__ void load_run(const typename Cx<R>::C* src, const Pat
     if constexpr (kCoef) {
       D[m] = cr[(size_t)m * M];
     } else {
-      const PathRecT<R> rec = pl[rr.start + m];
-      const C t = tab<R>(A, (rr.dl0 + m + (N >> 1)) * M + k);
-      D[m] = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+      D[m] = path_coef<R, kFwd>(A, at, pl, rr, m, k);
     }
   }
 }
@@ -410,24 +436,26 @@ __device__ __forceinline__ void mac_run(const typename Cx<R>::C (&W)[L + E - 1],
   }
 }
 
-template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef, bool kPair = kRowMajor>
 __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
                                           const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
-                                          int j0, typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
+                                          int j0, const GatherAt<R>& at, typename Cx<R>::C (&accA)[E],
+                                          typename Cx<R>::C (&accB)[E]) {
   using C = typename Cx<R>::C;
-  if constexpr (kRowMajor) {
+  if constexpr (kRowMajor && kPair) {
     C W[L + E - 1], D[L];
-    load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, W, D);
+    load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rr, A, k, j0, at, W, D);
     mac_run<R, E, L, kFwd>(W, D, accA, accB);
   } else {
-    // shared-memory extension: each coefficient is loaded right before its MACs (fewer live
-    // registers in the kernels that keep the CG vectors in registers)
-    const int M = A.M, N = A.N, CS = N + E + 3;
+    // shared-memory extension (column-major, or a row-major window): each coefficient is
+    // loaded right before its MACs (fewer live registers)
+    const int M = A.M, N = A.N, CS = kRowMajor ? 1 : N + E + 3;
+    const size_t RS = kRowMajor ? at.RS : 1;
     const int row0 = kFwd ? ((j0 - rr.dl0 - (L - 1)) & (N - 1)) : ((j0 + rr.dl0) & (N - 1));
-    const C* a = src + (size_t)row0 + (kFwd ? -rr.dk : rr.dk) * CS;
+    const C* a = src + (size_t)row0 * RS + (kFwd ? -rr.dk : rr.dk) * CS;
     C W[L + E - 1];
 #pragma unroll
-    for (int w = 0; w < L + E - 1; ++w) W[w] = a[w];
+    for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
     const C* cr = kCoef ? ct + (size_t)rr.start * M : nullptr;
 #pragma unroll
     for (int m = 0; m < L; ++m) {
@@ -435,9 +463,7 @@ __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const Pa
       if constexpr (kCoef) {
         D = cr[(size_t)m * M];
       } else {
-        const PathRecT<R> rec = pl[rr.start + m];
-        const C t = tab<R>(A, (rr.dl0 + m + (N >> 1)) * M + k);
-        D = kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
+        D = path_coef<R, kFwd>(A, at, pl, rr, m, k);
       }
       const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
 #pragma unroll
@@ -446,41 +472,52 @@ __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const Pa
   }
 }
 
-// Runs [q, end) of one length class, two at a time when the extension is in global memory.
-template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
+// Runs [q, end) of one length class, two at a time when the extension is in global memory
+// (kPair: two runs' loads in flight before either accumulates).
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef, bool kPair = kRowMajor>
 __device__ __forceinline__ int apply_runs(const typename Cx<R>::C* src, const PathRecT<R>* pl,
                                           const typename Cx<R>::C* ct, const RunRec* rl, int q, int end,
-                                          const FrameArgs& A, int k, int j0, typename Cx<R>::C (&accA)[E],
-                                          typename Cx<R>::C (&accB)[E]) {
+                                          const FrameArgs& A, int k, int j0, const GatherAt<R>& at,
+                                          typename Cx<R>::C (&accA)[E], typename Cx<R>::C (&accB)[E]) {
   using C = typename Cx<R>::C;
-  if constexpr (kRowMajor) {
+  if constexpr (kRowMajor && kPair) {
     for (; q + 1 < end; q += 2) {
       C W0[L + E - 1], D0[L], W1[L + E - 1], D1[L];
-      load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, W0, D0);
-      load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q + 1], A, k, j0, W1, D1);
+      load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, at, W0, D0);
+      load_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q + 1], A, k, j0, at, W1, D1);
       mac_run<R, E, L, kFwd>(W0, D0, accA, accB);
       mac_run<R, E, L, kFwd>(W1, D1, accA, accB);
     }
   }
-  for (; q < end; ++q) apply_run<R, E, L, kFwd, kRowMajor, kCoef>(src, pl, ct, rl[q], A, k, j0, accA, accB);
+  for (; q < end; ++q) apply_run<R, E, L, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, rl[q], A, k, j0, at, accA, accB);
   return q;
 }
 
+constexpr int kColHalf = -0x40000000;  // gather column offset: the extension's own (M / 2)
+
 // Forward rows (kFwd) of output block b: out[i] = (H p)_b[k, j0 + i], summed over the tx blocks
 // and the runs of each (b, t) list; adjoint: out[i] = (H^H u)_b[k, j0 + i] over the rx blocks.
-template <typename R, int E, bool kFwd, bool kRowMajor, bool kCoef>
+// Column k of the extension is column k + col0 of `ext` (col0 = M / 2 by default); a row-major
+// extension's rows are `rs` elements apart (2 M by default) -- a shared-memory window of
+// a row-major extension passes its own offset and stride; ct / phi / ct_rs / ct_c0: a CTA's
+// coefficient table (see GatherAt), else the coefficients are formed per path.
+template <typename R, int E, bool kFwd, bool kRowMajor, bool kCoef, bool kPair = kRowMajor>
 __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                             const RunRec* runs, const int* nruns, const typename Cx<R>::C* coef,
-                                            const FrameArgs& A, int b, int k, int j0, typename Cx<R>::C (&out)[E]) {
+                                            const FrameArgs& A, int b, int k, int j0, typename Cx<R>::C (&out)[E],
+                                            size_t rs = 0, int col0 = kColHalf,
+                                            const typename Cx<R>::C* ct_tab = nullptr,
+                                            const typename Cx<R>::C* phi = nullptr, int ct_rs = 0, int ct_c0 = 0) {
   using C = typename Cx<R>::C;
   // register budget: the window holds L + E - 1 complex values beside 2E accumulators
   constexpr int kLMax = E >= 32 ? 1 : (E >= 16 ? 2 : kMaxRun);
-  const int Hk = A.M >> 1;
+  const int c0 = col0 == kColHalf ? (A.M >> 1) : col0;
   const int CS = kRowMajor ? 1 : A.N + E + 3;
+  const GatherAt<R> at{kRowMajor ? (rs ? rs : (size_t)(2 * A.M)) : 1, ct_tab, phi, ct_rs, ct_c0};
   C accA[E], accB[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) accA[i] = accB[i] = Cx<R>::make(0, 0);
-  const C* colk = ext + (size_t)(k + Hk) * CS;
+  const C* colk = ext + (size_t)(k + c0) * CS;
   const int nother = kFwd ? A.ntx : A.nrx;
   for (int o = 0; o < nother; ++o) {
     const C* src = colk + (size_t)o * blk;
@@ -493,8 +530,8 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
     const int n4 = packed & 127, n3 = (packed >> 7) & 127, n2 = (packed >> 14) & 255, n1 = (packed >> 22) & 511;
     int q = 0;
     if constexpr (kLMax == 4) {
-      q = apply_runs<R, E, 4, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4, A, k, j0, accA, accB);
-      q = apply_runs<R, E, 3, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4 + n3, A, k, j0, accA, accB);
+      q = apply_runs<R, E, 4, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, rl, q, n4, A, k, j0, at, accA, accB);
+      q = apply_runs<R, E, 3, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, rl, q, n4 + n3, A, k, j0, at, accA, accB);
     } else {
       for (const int e3 = n4 + n3; q < e3; ++q) {  // split into runs of at most kLMax paths
         const RunRec rr = rl[q];
@@ -502,46 +539,53 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
           RunRec sub = rr;
           sub.start = (short)(rr.start + m);
           sub.dl0 = (short)(rr.dl0 + m);
-          if (kLMax == 2 && rr.len - m >= 2) apply_run<R, E, (kLMax == 2 ? 2 : 1), kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
-          else apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
+          if (kLMax == 2 && rr.len - m >= 2) apply_run<R, E, (kLMax == 2 ? 2 : 1), kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, sub, A, k, j0, at, accA, accB);
+          else apply_run<R, E, 1, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, sub, A, k, j0, at, accA, accB);
         }
       }
     }
     if constexpr (kLMax >= 2) {
-      q = apply_runs<R, E, 2, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4 + n3 + n2, A, k, j0, accA, accB);
+      q = apply_runs<R, E, 2, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, rl, q, n4 + n3 + n2, A, k, j0, at, accA, accB);
     } else {
       for (const int e2 = n4 + n3 + n2; q < e2; ++q) {
         RunRec sub = rl[q];
-        apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
+        apply_run<R, E, 1, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, sub, A, k, j0, at, accA, accB);
         sub.start = (short)(sub.start + 1);
         sub.dl0 = (short)(sub.dl0 + 1);
-        apply_run<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, sub, A, k, j0, accA, accB);
+        apply_run<R, E, 1, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, sub, A, k, j0, at, accA, accB);
       }
     }
-    apply_runs<R, E, 1, kFwd, kRowMajor, kCoef>(src, pl, ct, rl, q, n4 + n3 + n2 + n1, A, k, j0, accA, accB);
+    apply_runs<R, E, 1, kFwd, kRowMajor, kCoef, kPair>(src, pl, ct, rl, q, n4 + n3 + n2 + n1, A, k, j0, at, accA, accB);
   }
   // accA = sum D.x W, accB = sum D.y W: D W = (A.x - B.y, A.y + B.x); for the adjoint's table
   // entries c (D = conj(c)): (A.x + B.y, A.y - B.x)
+  const bool conj_tab = !kFwd && (kCoef || ct_tab != nullptr);
 #pragma unroll
   for (int i = 0; i < E; ++i)
-    out[i] = (kCoef && !kFwd) ? Cx<R>::make(accA[i].x + accB[i].y, accA[i].y - accB[i].x)
-                              : Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
+    out[i] = conj_tab ? Cx<R>::make(accA[i].x + accB[i].y, accA[i].y - accB[i].x)
+                      : Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
 }
 
 // coefF / coefA: the frame's coefficient tables (kCoef), else unused.
-template <typename R, int E, bool kRowMajor = false, bool kCoef = false>
+template <typename R, int E, bool kRowMajor = false, bool kCoef = false, bool kPair = kRowMajor>
 __device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int r, int k,
                                            int j0, typename Cx<R>::C (&out)[E],
-                                           const typename Cx<R>::C* coefF = nullptr) {
-  gather_runs<R, E, true, kRowMajor, kCoef>(ext, blk, paths, runs, nruns, coefF, A, r, k, j0, out);
+                                           const typename Cx<R>::C* coefF = nullptr, size_t rs = 0,
+                                           int col0 = kColHalf, const typename Cx<R>::C* ct_tab = nullptr,
+                                           const typename Cx<R>::C* phi = nullptr, int ct_rs = 0, int ct_c0 = 0) {
+  gather_runs<R, E, true, kRowMajor, kCoef, kPair>(ext, blk, paths, runs, nruns, coefF, A, r, k, j0, out, rs, col0,
+                                                   ct_tab, phi, ct_rs, ct_c0);
 }
-template <typename R, int E, bool kRowMajor = false, bool kCoef = false>
+template <typename R, int E, bool kRowMajor = false, bool kCoef = false, bool kPair = kRowMajor>
 __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int t, int k,
                                            int j0, typename Cx<R>::C (&out)[E],
-                                           const typename Cx<R>::C* coefA = nullptr) {
-  gather_runs<R, E, false, kRowMajor, kCoef>(ext, blk, paths, runs, nruns, coefA, A, t, k, j0, out);
+                                           const typename Cx<R>::C* coefA = nullptr, size_t rs = 0,
+                                           int col0 = kColHalf, const typename Cx<R>::C* ct_tab = nullptr,
+                                           const typename Cx<R>::C* phi = nullptr, int ct_rs = 0, int ct_c0 = 0) {
+  gather_runs<R, E, false, kRowMajor, kCoef, kPair>(ext, blk, paths, runs, nruns, coefA, A, t, k, j0, out, rs, col0,
+                                                    ct_tab, phi, ct_rs, ct_c0);
 }
 
 // The coefficient tables of one list (after build_runs: sorted order), all threads:

@@ -1,14 +1,18 @@
 // The receiver for paper-scale frames (M up to 16384, M N up to 524288: 4 MB per FP32
 // vector), one frame at a time on the whole GPU.  A cooperative persistent kernel: its CTAs
 // split every stage by delay columns (Zak transform tiles, operator gathers, CG updates,
-// demapping) or by contiguous index ranges (read-off, bit packing) and meet at grid barriers;
-// the frame's grid, the quasi-periodic extensions of p and t (row-major, as in the
-// large-frame kernel) and the CG vectors live in global scratch that stays in L2 (about
-// 45 MB at 16384 x 32).  The read-off is the threshold / stable-compaction / exact top-P_max
-// of the shared-memory kernel, with its scans and radix-select histograms taken over the grid.
-// Algorithm 1's scalars are FP64 sums of per-CTA partials taken in CTA order, so every CTA
-// derives the same alpha, beta and stopping decision.  SISO, separate pilot frames (or
-// loaded lists), FP32.
+// demapping) or by contiguous index ranges (read-off, bit packing) and meet at grid barriers.
+// The frame's grid, the quasi-periodic extensions of p, t and c (row-major, as in the
+// large-frame kernel) and the CG vectors live in global scratch that stays in L2 (about 58 MB
+// at 16384 x 32).  In the CG each CTA owns a slab of delay columns over all rows; when every
+// path's delay offset is within the launch's cap it gathers from shared-memory windows of the
+// extensions (its columns and the offsets' reach on either side) with a per-CTA table of the
+// paths' coefficients, and keeps p's window in shared memory across the iterations: three grid
+// barriers per iteration.  The read-off is the threshold / stable-compaction / exact
+// top-P_max of the shared-memory kernel, with its scans and radix-select histograms taken over
+// the grid.  Algorithm 1's scalars are FP64 sums of per-CTA partials taken in CTA order, so
+// every CTA derives the same alpha, beta and stopping decision.  SISO, separate pilot frames
+// (or loaded lists), FP32.
 #pragma once
 
 #include "frame_kernel.cuh"
@@ -22,6 +26,10 @@ constexpr uint32_t kGridMaxPolls = 1u << 22;
 
 constexpr int kGridMaxCtas = 512;  // two CTAs per SM on up to 256 SMs
 
+// Delay columns per CTA in the CG stages (the last CTAs may hold fewer, or none).
+// Even, so that the CTAs' column ranges start on 16-byte boundaries of the extensions' rows.
+__host__ __device__ __forceinline__ int grid_cols_per_cta(int M, int grid) { return ((M + grid - 1) / grid + 1) & ~1; }
+
 struct GridBarrier {
   unsigned long long count;  // CTA arrivals since the launch began (zeroed before each launch)
   int err;                   // a wait gave up: every CTA leaves at its next barrier
@@ -31,15 +39,20 @@ struct GridBarrier {
 // Global scratch of one grid receiver (one frame at a time).
 struct GridScratch {
   float2* Y;                     // [MN] Zak-transformed grid (pilot, then data), q = l M + k
-  float2* extP;                  // extensions of p and t (row-major, ext_block_elems(M, N, 8))
-  float2* extT;
-  float2 *X, *Cv, *Pv, *Vv;      // [MN] the CG vectors x, c, p and a
+  float2* extP[2];               // extensions of p (row-major, ext_block_elems(M, N, 8)): the
+                                 // iterations alternate, the previous p stays readable
+  float2* extT;                  // extension of y, then of t = H p
+  float2* extC;                  // extension of the residual c
+  float2 *X, *Vv;                // [MN] the CG vectors x and a
   uint8_t* lab;                  // [MN] hard labels, bit j of the label = bit j of the symbol
   PathRecT<float>* list;         // [p_max] the frame's path list
   double* part;                  // [2 grid] per-CTA partial sums, two alternating sets
   int* icnt;                     // [2 grid] per-CTA counts of the read-off compaction
   int* hist;                     // [5 x 128] radix-select histograms (zeroed per frame)
   GridBarrier* bar;
+  // shared-memory windows of the CG gathers (set by the launch): columns per window row (0: no
+  // windows) and the largest |dk| a window covers
+  int win_cols, win_dcap;
 };
 
 // Rows of the extension and bytes of the scratch for one (M, N, p_max) at a given grid.
@@ -48,9 +61,8 @@ __host__ __device__ __forceinline__ size_t grid_scratch_bytes(int M, int N, int 
   size_t b = 0;
   auto take = [&](size_t n) { b += (n + 255) & ~size_t(255); };
   take(MN * 8);       // Y
-  take(ext * 8);      // extP
-  take(ext * 8);      // extT
-  for (int i = 0; i < 4; ++i) take(MN * 8);
+  for (int i = 0; i < 4; ++i) take(ext * 8);  // extP[0], extP[1], extT, extC
+  for (int i = 0; i < 2; ++i) take(MN * 8);   // X, Vv
   take(MN);           // lab
   take((size_t)p_max * sizeof(PathRecT<float>));
   take((size_t)grid * 16);
@@ -70,11 +82,11 @@ __host__ __device__ __forceinline__ GridScratch grid_scratch_carve(char* base, i
     return p;
   };
   G.Y = reinterpret_cast<float2*>(take(MN * 8));
-  G.extP = reinterpret_cast<float2*>(take(ext * 8));
+  G.extP[0] = reinterpret_cast<float2*>(take(ext * 8));
+  G.extP[1] = reinterpret_cast<float2*>(take(ext * 8));
   G.extT = reinterpret_cast<float2*>(take(ext * 8));
+  G.extC = reinterpret_cast<float2*>(take(ext * 8));
   G.X = reinterpret_cast<float2*>(take(MN * 8));
-  G.Cv = reinterpret_cast<float2*>(take(MN * 8));
-  G.Pv = reinterpret_cast<float2*>(take(MN * 8));
   G.Vv = reinterpret_cast<float2*>(take(MN * 8));
   G.lab = reinterpret_cast<uint8_t*>(take(MN));
   G.list = reinterpret_cast<PathRecT<float>*>(take((size_t)p_max * sizeof(PathRecT<float>)));
@@ -82,6 +94,8 @@ __host__ __device__ __forceinline__ GridScratch grid_scratch_carve(char* base, i
   G.icnt = reinterpret_cast<int*>(take((size_t)grid * 8));
   G.hist = reinterpret_cast<int*>(take(5 * 128 * 4));
   G.bar = reinterpret_cast<GridBarrier*>(take(sizeof(GridBarrier)));
+  G.win_cols = 0;
+  G.win_dcap = -1;
   return G;
 }
 
@@ -141,6 +155,73 @@ __device__ __forceinline__ void ext_store_rm(float2* ext, const FrameArgs& A, in
     ext[(size_t)r * 2 * M + mc] = v;
     ext[(size_t)r * 2 * M + hc] = hv;
   }
+}
+
+// Store the E values of item (column k, rows j0 .. j0 + E - 1) into a row-major quasi-periodic
+// extension: the main column and the periodic halo rows always, the halo column (with its
+// quasi-periodic phase W_N^{+-l}, from wn[l] = W_N^{-l} in shared memory) when `halo` -- the
+// windowed gathers read halo columns only within a few delays of the wrap, the global gathers
+// anywhere.
+template <int E>
+__device__ __forceinline__ void grid_ext_store(float2* ext, const FrameArgs& A, int k, int j0, const float2 (&v)[E],
+                                               bool halo, const float2* wn) {
+  const int M = A.M, N = A.N, Hk = M >> 1, R = N + E + 3;
+  const size_t RS = (size_t)(2 * M);
+  const bool low = k < Hk;
+  float2* mcol = ext + (k + Hk);
+  float2* hcol = ext + ((low ? k + M : k - M) + Hk);
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int l = j0 + i;
+    for (int r = l; r < R; r += N) mcol[r * RS] = v[i];
+    if (halo) {
+      const float2 w = wn[l];
+      const float2 hv = cmul(v[i], low ? conjf2(w) : w);
+      for (int r = l; r < R; r += N) hcol[r * RS] = hv;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// A bulk copy that completes on `bar` without arriving on it (the expected bytes were armed once).
+__device__ __forceinline__ void bulk_g2s_tx(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Copy the columns [A0, A1) of rows [0, R) of a row-major extension into the shared-memory
+// window dst (rows Wp elements apart) by bulk async copies, one per row, issued by warp 0 after
+// one arm of the barrier with all the bytes.  A0 and A1 are even, so every copy starts 16-byte
+// aligned with a multiple of 16 bytes, as the bulk copy requires; nothing is copied when
+// A0 == A1.  The extension was written by other CTAs before the grid barrier this CTA passed
+// (generic stores): the issuing threads order them before the async reads with a proxy fence.
+// All threads call; false, uniformly, if the bounded wait gave up.
+__device__ __forceinline__ bool grid_window_load(float2* dst, const float2* src, int M, int R, int A0, int A1, int Wp,
+                                                 uint64_t* bar, uint32_t& phase) {
+  __syncthreads();  // earlier generic accesses to the window are complete
+  const uint32_t row_bytes = (uint32_t)(A1 - A0) * 8u;
+  bool ok = true;
+  if (row_bytes) {
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, row_bytes * (uint32_t)R);
+      }
+      __syncwarp();
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      const size_t off = (size_t)(A0 + (M >> 1));
+      for (int r = threadIdx.x; r < R; r += 32)
+        bulk_g2s_tx(dst + (size_t)r * Wp, src + (size_t)r * (size_t)(2 * M) + off, row_bytes, bar);
+    }
+    ok = mbar_wait_bounded(bar, phase, kMaxPolls);
+    if (!ok) ok = mbar_wait_bounded(bar, phase, kMaxPolls);  // let an in-flight copy land
+    phase ^= 1u;
+  }
+  return __syncthreads_and(ok) != 0;
 }
 
 // Y[l M + k] = N^-1/2 sum_n y[k + n M] W_N^{-n l} (Eq. zak) for all columns: tiles of
@@ -258,6 +339,15 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
   C* tile = reinterpret_cast<C*>(smem + off);
   off += (size_t)A.N * kGridDftCols * sizeof(C);
   C* wn = reinterpret_cast<C*>(smem + off);
+  off += ((size_t)A.N * sizeof(C) + 127) & ~size_t(127);
+  // the CG's coefficient table (p_max rows of the CTA's columns) with the paths' forward
+  // phases, and windows (p and c / t: N + E + 3 rows of G.win_cols columns each)
+  C* ctab = reinterpret_cast<C*>(smem + off);
+  off += ((size_t)A.p_max * grid_cols_per_cta(A.M, (int)gridDim.x) * sizeof(C) + 127) & ~size_t(127);
+  C* phi = reinterpret_cast<C*>(smem + off);
+  off += ((size_t)A.p_max * sizeof(C) + 127) & ~size_t(127);
+  C* bufP = reinterpret_cast<C*>(smem + off);
+  C* bufX = bufP + (size_t)(A.N + E + 3) * G.win_cols;
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM, tid = threadIdx.x;
   const int gtid = blockIdx.x * blockDim.x + tid, nthr = gridDim.x * blockDim.x;
@@ -273,9 +363,12 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
   const size_t blk = ext_block_elems(M, N, E);
   const bool write_paths = (A.mode & kWritePaths) != 0;
   unsigned gen = 0;  // barriers passed
+  uint32_t mph = 0;  // phase of the window barrier
   auto fail = [&](const FrameIO& io) {
     if (tid == 0 && io.status) *io.status = ZOTFS_ETIMEOUT;
   };
+  if (tid == 0) mbar_init(&S->mbar, 1);
+  __syncthreads();
 
   for (int f = 0; f < A.n_frames; ++f) {
     const FrameIO io = frame_io(A, f, (int)sizeof(C));
@@ -463,7 +556,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
     C v[E];
     // ------------------------------------------------ one operator apply
     if (A.mode & kApply) {
-      C* src = A.adjoint ? G.extT : G.extP;
+      C* src = A.adjoint ? G.extT : G.extP[0];
       for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
         const int k = it & (M - 1), j0 = (it >> logM) * E;
 #pragma unroll
@@ -486,34 +579,84 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
     // ------------------------------------------------ equalisation (Algorithm 1)
     if (A.mode & kCG) {
       const R lam = (R)io.lam;
+      // Work items (column k, rows j0 .. j0 + E - 1): this CTA owns the delay columns [k0, k1)
+      // over all rows, column fastest.
+      const int cpc = grid_cols_per_cta(M, (int)gridDim.x);
+      const int k0 = min(M, (int)blockIdx.x * cpc), k1 = min(M, k0 + cpc), ncol = k1 - k0;
+      // a row group's items on lanes of their own warps (gstride a power of two >= 32), so no warp
+      // mixes two row groups in its shared-memory reads
+      int gshift = 5;
+      while ((1 << gshift) < ncol) ++gshift;
+      const int nslots = (N / E) << gshift;
+      // The per-(path, column) factors of Eq. sparse_mvm / Eq. sparse_herm_mvm on the CTA's
+      // columns, h_p W[dl_p k] (the adjoint's, conjugated at use), and each path's phase
+      // W[-dl_p dk_p] that turns one into the forward factor hf_p W[dl_p k] (paths in the
+      // sorted order of the runs).
+      for (int e = tid; e < P * ncol; e += blockDim.x) {
+        const int p = e / ncol, c = e - p * ncol;
+        const PathRec& rec = paths[p];
+        ctab[p * cpc + c] = cmul(rec.h, tab<R>(A, (size_t)(rec.dl + (N >> 1)) * M + k0 + c));
+      }
+      for (int p = tid; p < P; p += blockDim.x)
+        phi[p] = tw<R>(A, (size_t)((-paths[p].dl * paths[p].dk) & (MN - 1)));
+      for (int i = tid; i < N; i += blockDim.x) wn[i] = conjf2(tw<R>(A, (size_t)i << logM));  // W_N^{-l}
+      // Window mode, when every path's |dk| is within the launch's cap: the CTA keeps p over the
+      // columns [A0, A1) -- its own and dmax more on either side -- in shared memory, forming it
+      // there from a window of c each iteration (so no grid barrier separates the p update from
+      // the forward gather), and gathers t from a window of t.  Otherwise the gathers read the
+      // global extensions, p included.
+      if (tid < 32) {
+        int m = 0;
+        for (int p = tid; p < P; p += 32) m = max(m, abs(paths[p].dk));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (tid == 0) S->isc[5] = m;
+      }
+      __syncthreads();
+      const int dmax = S->isc[5];
+      const bool win = G.win_cols > 0 && dmax <= G.win_dcap;
+      const int A0 = (k0 - dmax) & ~1, Wc = ((k1 + dmax + 1) & ~1) - A0, Wp = G.win_cols;
+      const int A1 = ncol > 0 ? A0 + Wc : A0;  // no window when the CTA has no columns
+      const int Rw = N + E + 3, colw = -A0;
+
+      const int hw = win ? dmax + 2 : M;  // halo columns stored: k < hw or k >= M - hw
+      const size_t RS = (size_t)(2 * M);
+      auto main_at = [&](const C* ext, int k, int l) { return ext[(size_t)l * RS + (k + (M >> 1))]; };
+      auto wfail = [&](const FrameIO& io) {
+        if (tid == 0) atomicExch(&G.bar->err, 1);  // the other CTAs leave at their next barrier
+        fail(io);
+      };
+
       if (!A.y_is_dd) {
         // the data frame's Zak transform writes the extension of y directly
         grid_dzt<E>(io.y_data, A.in_dtype, nullptr, G.extT, A, tile, wn);
       } else {
         const C* Yd = reinterpret_cast<const C*>(io.y_data);
-        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
-          const int k = it & (M - 1), j0 = (it >> logM) * E;
+        for (int s = tid; s < nslots; s += blockDim.x) {
+          const int g = s >> gshift, kk = s - (g << gshift);
+          if (kk >= ncol) continue;
+          const int k = k0 + kk, j0 = g * E;
 #pragma unroll
           for (int i = 0; i < E; ++i) v[i] = Yd[(size_t)(j0 + i) * M + k];
-          write_ext<R, E, true>(G.extT, A, k, j0, v);
+          grid_ext_store<E>(G.extT, A, k, j0, v, k < hw || k >= M - hw, wn);
         }
       }
       if (!grid_sync(G.bar, gen)) return fail(io);
 
-      // b = H^H y;  c = b, p = b, x = 0, c_n = ||c||^2
+      // b = H^H y;  c = b, x = 0, c_n = ||c||^2  (p = c is formed by the first iteration)
+      if (win && !grid_window_load(bufX, G.extT, M, Rw, A0, A1, Wp, &S->mbar, mph)) return wfail(io);
       R part = 0;
-      for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
-        const int k = it & (M - 1), j0 = (it >> logM) * E;
-        gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
+      for (int s = tid; s < nslots; s += blockDim.x) {
+        const int g = s >> gshift, kk = s - (g << gshift);
+        if (kk >= ncol) continue;
+        const int k = k0 + kk, j0 = g * E;
+        if (win) gather_adj<R, E, true, false, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
+        else gather_adj<R, E, true, false, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-          const size_t o = (size_t)(j0 + i) * M + k;
-          G.Cv[o] = v[i];
-          G.Pv[o] = v[i];
-          G.X[o] = make_float2(0.f, 0.f);
+          G.X[(size_t)(j0 + i) * M + k] = make_float2(0.f, 0.f);
           part = fma(v[i].x, v[i].x, fma(v[i].y, v[i].y, part));
         }
-        write_ext<R, E, true>(G.extP, A, k, j0, v);
+        grid_ext_store<E>(G.extC, A, k, j0, v, k < hw || k >= M - hw, wn);
       }
       double* const partA = G.part;               // Re(p^H a)
       double* const partC = G.part + gridDim.x;   // ||c||^2
@@ -529,26 +672,81 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       __syncthreads();
 
       for (int iter = 0; iter < io.iters && !S->isc[4]; ++iter) {
-        // t = H p  (extP -> extT)
-        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
-          const int k = it & (M - 1), j0 = (it >> logM) * E;
-          gather_fwd<R, E, true>(G.extP, blk, paths, runs, nruns, A, 0, k, j0, v);
-          write_ext<R, E, true>(G.extT, A, k, j0, v);
+        C* const extPc = G.extP[iter & 1];
+        const C* const extPo = G.extP[(iter & 1) ^ 1];
+        const R beta = iter ? (R)S->fsc[1] : (R)0;
+        // p = c + beta p (p = c in the first iteration), then t = H p
+        if (win) {
+          if (!grid_window_load(bufX, G.extC, M, Rw, A0, A1, Wp, &S->mbar, mph)) return wfail(io);
+          for (int e = tid; e < (ncol > 0 ? Rw * Wc : 0); e += blockDim.x) {
+            const int r = e / Wc, c = e - r * Wc;
+            const C cv = bufX[r * Wp + c];
+            C& pv = bufP[r * Wp + c];
+            pv = iter ? make_float2(fma(beta, pv.x, cv.x), fma(beta, pv.y, cv.y)) : cv;
+          }
+          __syncthreads();
+          for (int s = tid; s < nslots; s += blockDim.x) {
+            const int g = s >> gshift, kk = s - (g << gshift);
+            if (kk >= ncol) continue;
+            const int k = k0 + kk, j0 = g * E;
+            gather_fwd<R, E, true, false, false>(bufP, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
+            grid_ext_store<E>(G.extT, A, k, j0, v, k < hw || k >= M - hw, wn);
+          }
+        } else {
+          // the main column of p from those of c and the previous p; the halo column likewise
+          // from the stored halo columns (as a window forms it)
+          for (int s = tid; s < nslots; s += blockDim.x) {
+            const int g = s >> gshift, kk = s - (g << gshift);
+            if (kk >= ncol) continue;
+            const int k = k0 + kk, j0 = g * E;
+            const int mc = k + (M >> 1), hc = (k < (M >> 1) ? k + M : k - M) + (M >> 1);
+            C ph[E];
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+              const size_t o = (size_t)(j0 + i) * RS;
+              v[i] = G.extC[o + mc];
+              ph[i] = G.extC[o + hc];
+              if (iter) {
+                const C po = extPo[o + mc], qo = extPo[o + hc];
+                v[i] = make_float2(fma(beta, po.x, v[i].x), fma(beta, po.y, v[i].y));
+                ph[i] = make_float2(fma(beta, qo.x, ph[i].x), fma(beta, qo.y, ph[i].y));
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < E; ++i)
+              for (int r = j0 + i; r < Rw; r += N) {
+                extPc[(size_t)r * RS + mc] = v[i];
+                extPc[(size_t)r * RS + hc] = ph[i];
+              }
+          }
+          if (!grid_sync(G.bar, gen)) return fail(io);
+          for (int s = tid; s < nslots; s += blockDim.x) {
+            const int g = s >> gshift, kk = s - (g << gshift);
+            if (kk >= ncol) continue;
+            const int k = k0 + kk, j0 = g * E;
+            gather_fwd<R, E, true, false, false>(extPc, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
+            grid_ext_store<E>(G.extT, A, k, j0, v, true, wn);
+          }
         }
         if (!grid_sync(G.bar, gen)) return fail(io);
+        // p of item (k, l): the window, else the global extension (written this iteration)
+        auto p_at = [&](int k, int l) { return win ? bufP[l * Wp + (k - A0)] : main_at(extPc, k, l); };
         // a = H^H t + lambda p;  Re(p^H a)
+        if (win && !grid_window_load(bufX, G.extT, M, Rw, A0, A1, Wp, &S->mbar, mph)) return wfail(io);
         part = 0;
-        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
-          const int k = it & (M - 1), j0 = (it >> logM) * E;
-          gather_adj<R, E, true>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v);
+        for (int s = tid; s < nslots; s += blockDim.x) {
+          const int g = s >> gshift, kk = s - (g << gshift);
+          if (kk >= ncol) continue;
+          const int k = k0 + kk, j0 = g * E;
+          if (win) gather_adj<R, E, true, false, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
+          else gather_adj<R, E, true, false, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
 #pragma unroll
           for (int i = 0; i < E; ++i) {
-            const size_t o = (size_t)(j0 + i) * M + k;
-            const C pv = G.Pv[o];
+            const C pv = p_at(k, j0 + i);
             v[i].x = fma(lam, pv.x, v[i].x);
             v[i].y = fma(lam, pv.y, v[i].y);
             part = fma(pv.x, v[i].x, fma(pv.y, v[i].y, part));
-            G.Vv[o] = v[i];
+            G.Vv[(size_t)(j0 + i) * M + k] = v[i];
           }
         }
         d = block_sum_to_thread0(part, S);
@@ -560,21 +758,29 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         const R alpha = (R)S->fsc[0];
         // x += alpha p;  c -= alpha a;  c_n' = ||c||^2
         part = 0;
-        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
-          const int k = it & (M - 1), j0 = (it >> logM) * E;
+        for (int s = tid; s < nslots; s += blockDim.x) {
+          const int g = s >> gshift, kk = s - (g << gshift);
+          if (kk >= ncol) continue;
+          const int k = k0 + kk, j0 = g * E;
+          C xv[E], av[E];  // the global loads before the first store
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const size_t o = (size_t)(j0 + i) * M + k;
-            const C pv = G.Pv[o], av = G.Vv[o];
-            C xv = G.X[o], cv = G.Cv[o];
-            xv.x = fma(alpha, pv.x, xv.x);
-            xv.y = fma(alpha, pv.y, xv.y);
-            cv.x = fma(-alpha, av.x, cv.x);
-            cv.y = fma(-alpha, av.y, cv.y);
-            G.X[o] = xv;
-            G.Cv[o] = cv;
-            part = fma(cv.x, cv.x, fma(cv.y, cv.y, part));
+            av[i] = G.Vv[o];
+            xv[i] = G.X[o];
+            v[i] = main_at(G.extC, k, j0 + i);
           }
+#pragma unroll
+          for (int i = 0; i < E; ++i) {
+            const C pv = p_at(k, j0 + i);
+            xv[i].x = fma(alpha, pv.x, xv[i].x);
+            xv[i].y = fma(alpha, pv.y, xv[i].y);
+            v[i].x = fma(-alpha, av[i].x, v[i].x);
+            v[i].y = fma(-alpha, av[i].y, v[i].y);
+            G.X[(size_t)(j0 + i) * M + k] = xv[i];
+            part = fma(v[i].x, v[i].x, fma(v[i].y, v[i].y, part));
+          }
+          grid_ext_store<E>(G.extC, A, k, j0, v, k < hw || k >= M - hw, wn);
         }
         d = block_sum_to_thread0(part, S);
         if (tid == 0) partC[blockIdx.x] = d;
@@ -587,30 +793,13 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
           cn = cn_new;
         }
         __syncthreads();
-        const R beta = (R)S->fsc[1];
-        if (iter + 1 < io.iters) {
-          // p = c + beta p, and its extension
-          for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
-            const int k = it & (M - 1), j0 = (it >> logM) * E;
-#pragma unroll
-            for (int i = 0; i < E; ++i) {
-              const size_t o = (size_t)(j0 + i) * M + k;
-              const C cv = G.Cv[o];
-              C pv = G.Pv[o];
-              pv.x = fma(beta, pv.x, cv.x);
-              pv.y = fma(beta, pv.y, cv.y);
-              G.Pv[o] = pv;
-              v[i] = pv;
-            }
-            write_ext<R, E, true>(G.extP, A, k, j0, v);
-          }
-          if (!grid_sync(G.bar, gen)) return fail(io);
-        }
       }
       if (S->isc[1]) st |= kStNonFinite;
       if ((A.mode & kWriteX) && io.x_hat)
-        for (int it = it_beg + tid; it < it_end; it += blockDim.x) {
-          const int k = it & (M - 1), j0 = (it >> logM) * E;
+        for (int s = tid; s < nslots; s += blockDim.x) {
+          const int g = s >> gshift, kk = s - (g << gshift);
+          if (kk >= ncol) continue;
+          const int k = k0 + kk, j0 = g * E;
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const size_t o = (size_t)(j0 + i) * M + k;
@@ -653,14 +842,18 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
   }
 }
 
-__host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max) {
+// win_cols: columns per row of the two CG windows (0: none); cpc: delay columns per CTA.
+__host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max, int win_cols, int cpc) {
   size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
   off += ((size_t)p_max * sizeof(PathRecT<float>) + sizeof(int) * 2 + 127) & ~size_t(127);
   off += ((size_t)p_max * sizeof(RunRec) + 127) & ~size_t(127);
   off += ((size_t)p_max * sizeof(PathRecT<float>) + 127) & ~size_t(127);
   off += ((size_t)((p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);
   off += (size_t)N * kGridDftCols * sizeof(float2);
-  off += (size_t)N * sizeof(float2);
+  off += ((size_t)N * sizeof(float2) + 127) & ~size_t(127);
+  off += ((size_t)p_max * cpc * sizeof(float2) + 127) & ~size_t(127);
+  off += ((size_t)p_max * sizeof(float2) + 127) & ~size_t(127);
+  off += 2 * (size_t)(N + kGridE + 3) * (size_t)win_cols * sizeof(float2);
   return off;
 }
 

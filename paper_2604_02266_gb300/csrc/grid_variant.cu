@@ -1,4 +1,5 @@
 // Instantiations and cooperative launch of the paper-scale grid receiver (frame_grid.cuh).
+#include <algorithm>
 #include <mutex>
 
 #include "frame_grid.cuh"
@@ -75,28 +76,59 @@ bool grid_shape(int M, int N, int nrx, int ntx) {
          N <= 64 && (size_t)M * N <= kGridMaxElems;
 }
 
+// The CG windows of one CTA at a given grid: its ceil(M / grid) columns plus dcap on either
+// side (and one for the even start), as much as the shared memory left at `occ` CTAs per SM
+// holds, dcap at most M / 2 - 2 (the windows stay inside the extensions' halo) and 128.
+void grid_window(int M, int N, int p_max, int grid, int occ, int smem_per_sm, int smem_reserved, int& cols,
+                 int& dcap) {
+  cols = 0;
+  dcap = -1;
+  const int cpc = grid_cols_per_cta(M, grid);
+  const long long base = (long long)grid_smem_bytes(N, p_max, 0, cpc);
+  const long long avail = (long long)smem_per_sm / occ - smem_reserved - base;
+  const long long row_bytes = 2LL * (N + kGridE + 3) * (long long)sizeof(float2);  // both windows, one column
+  if (avail <= 0) return;
+  const long long wmax = avail / row_bytes;
+  int d = (int)std::min<long long>((wmax - cpc - 3) / 2, 128);  // cols below stays <= wmax
+  d = std::min(d, M / 2 - 2);
+  if (d < 1) return;
+  dcap = d;
+  cols = (cpc + 2 * d + 2 + 1) & ~1;
+}
+
 cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, int ctas_per_sm, GridCfg& cfg) {
-  cfg.smem = grid_smem_bytes(N, p_max);
+  int dev = 0, smem_sm = 0, smem_res = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
   cfg.T = kGridThreads;
   cfg.EQ = 0;
   for (int v = 0; v < kNumGridVariants; ++v) {
     const GridVariant& gv = kGridVariants[v];
-    cudaError_t e = grant(v, cfg.smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gv.k, kGridThreads, cfg.smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) continue;
-    if (occ > gv.minb) occ = gv.minb;
-    if (ctas_per_sm > 0 && occ > ctas_per_sm) occ = ctas_per_sm;
-    if (occ > kGridMaxCtasPerSm) occ = kGridMaxCtasPerSm;  // the plan's scratch holds partials for that many
-    const int grid = occ * sm_count;
-    if (grid > kGridMaxCtas) return cudaErrorInvalidConfiguration;
-    if ((long long)grid * kGridThreads * gv.EQ >= (long long)M * N) {
+    int want = gv.minb;
+    if (ctas_per_sm > 0 && want > ctas_per_sm) want = ctas_per_sm;
+    if (want > kGridMaxCtasPerSm) want = kGridMaxCtasPerSm;  // the plan's scratch holds partials for that many
+    for (int occ_t = want; occ_t >= 1; --occ_t) {
+      const int grid = occ_t * sm_count;
+      if (grid > kGridMaxCtas) return cudaErrorInvalidConfiguration;
+      if ((long long)grid * kGridThreads * gv.EQ < (long long)M * N) break;  // the read-off needs more threads
+      int cols = 0, dcap = -1;
+      grid_window(M, N, p_max, grid, occ_t, smem_sm, smem_res, cols, dcap);
+      const size_t smem = grid_smem_bytes(N, p_max, cols, grid_cols_per_cta(M, grid));
+      e = grant(v, smem);
+      if (e != cudaSuccess) return e;
+      int occ = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gv.k, kGridThreads, smem);
+      if (e != cudaSuccess) return e;
+      if (occ < occ_t) continue;
       cfg.EQ = gv.EQ;
       cfg.E = gv.E;
       cfg.variant = v;
       cfg.grid = grid;
+      cfg.smem = smem;
+      cfg.win_cols = cols;
+      cfg.win_dcap = dcap;
       return cudaSuccess;
     }
   }
@@ -111,6 +143,8 @@ cudaError_t grid_launch(const GridCfg& cfg, const FrameArgs& A, char* scratch, c
   cudaError_t e = grant(cfg.variant, cfg.smem);
   if (e != cudaSuccess) return e;
   GridScratch G = grid_scratch_carve(scratch, A.M, A.N, A.p_max, cfg.grid);
+  G.win_cols = cfg.win_cols;
+  G.win_dcap = cfg.win_dcap;
   e = cudaMemsetAsync(G.bar, 0, sizeof(GridBarrier), stream);
   if (e != cudaSuccess) return e;
   FrameArgs args = A;

@@ -145,6 +145,7 @@ constexpr size_t kGridMaxElems = (size_t)1 << 19;  // M N up to 524288 (16384 x 
 struct GridCfg {
   int T, EQ, E, grid, variant;
   size_t smem;
+  int win_cols, win_dcap;  // the CG windows: columns per row (0: none), largest |dk| covered
 };
 bool grid_shape(int M, int N, int nrx, int ntx);
 // ctas_per_sm: the plan's tuning, CTAs per SM of the cooperative launch (0: as many as fit, at

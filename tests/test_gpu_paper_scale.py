@@ -180,3 +180,45 @@ def test_grid_embedded_pilot_is_unsupported():
     yd = to_dev(b["y_data_td"])
     with pytest.raises(ZotfsError):
         plan.rx(yd, yd, to_dev(b["noise_var"]), to_dev(b["theta"]), 10, 1)
+
+
+@pytest.mark.parametrize("M,N,ctas", [(1024, 32, 2), (4096, 16, 2), (2048, 32, 1)])
+def test_grid_windowed_and_global_gathers_agree(M, N, ctas):
+    """The CG gathers read shared-memory windows of the extensions when every path's |dk| is
+    within the launch's cap, else the global extensions.  Adding a zero-gain tap at the far
+    delay M/2 - 1 changes no value but sends the frame down the global route: x is bitwise
+    the same, and both match the oracle.  A second list adds a real tap 20 delays out (a wide
+    window, read across the delay wrap by the first and last CTAs)."""
+    F, iters = 2, 10
+    b, grids = _cg_case_grid(M, N, F, seed=9960 + M + ctas)
+    plan = Plan(M, N, 1, 1, 16, p_max=128)  # room for the estimated 64 taps and one more
+    plan.set_tuning(ctas_per_sm=ctas)
+    y = to_dev(b["y_data_td"])
+    nv = to_dev(b["noise_var"])
+    near = [g[0][0] for g in grids]
+    far = []
+    wide = []
+    for pl in near:
+        dk = np.append(pl.dk, M // 2 - 1)
+        dl = np.append(pl.dl, 0)
+        far.append(dc.PathList.from_offsets(M, N, M // 2, N // 2, np.append(pl.h, 0j), dk, dl))
+        rng = np.random.default_rng(int(abs(pl.h[0]) * 1e6) % 1000)
+        k_new = -20 if (-20, 3) not in set(zip(pl.dk.tolist(), pl.dl.tolist())) else 20
+        wide.append(dc.PathList.from_offsets(M, N, M // 2, N // 2,
+                                             np.append(pl.h, 0.05 * (rng.standard_normal() + 1j)).astype(np.complex64)
+                                             .astype(complex), np.append(pl.dk, k_new), np.append(pl.dl, 3)))
+    xs = {}
+    for name, lists in (("near", near), ("far", far), ("wide", wide)):
+        paths = fill_paths(plan.new_paths(F), lists, plan.p_max)
+        xs[name] = plan.equalize(y, paths, nv, iters, F).cpu().numpy()
+    assert np.array_equal(xs["near"], xs["far"])
+    y_dd = [zak.vec(zak.dzt(b["y_data_td"][f, 0].astype(complex), M, N)) for f in range(F)]
+    for name, lists in (("near", near), ("wide", wide)):
+        for f in range(F):
+            ref = eq.cga([[lists[f]]], y_dd[f], float(b["noise_var"][f]), iters)
+            assert rel_l2(xs[name][f].reshape(-1), ref) < TOL_X, (name, f)
+
+
+def _cg_case_grid(M, N, F, seed):
+    from tests.test_gpu_stages import _cg_case
+    return _cg_case(M, N, F, 20, seed=seed)
