@@ -25,6 +25,15 @@ constexpr int kGridDftCols = 32;  // delay columns per Zak-transform tile
 constexpr uint32_t kGridMaxPolls = 1u << 22;
 
 constexpr int kGridMaxCtas = 512;  // two CTAs per SM on up to 256 SMs
+constexpr int kGridCandMax = 4096;  // passing taps the CTAs select among in shared memory
+
+// A tap that passed the read-off threshold: its grid index, |h|^2 as an ordered bit pattern,
+// and h.
+struct GridCand {
+  int q;
+  uint32_t key;
+  float2 h;
+};
 
 // Delay columns per CTA in the CG stages (the last CTAs may hold fewer, or none).
 // Even, so that the CTAs' column ranges start on 16-byte boundaries of the extensions' rows.
@@ -45,7 +54,8 @@ struct GridScratch {
   float2* extC;                  // extension of the residual c
   float2 *X, *Vv;                // [MN] the CG vectors x and a
   uint8_t* lab;                  // [MN] hard labels, bit j of the label = bit j of the symbol
-  PathRecT<float>* list;         // [p_max] the frame's path list
+  PathRecT<float>* list;         // [p_max] the frame's path list (read-offs with many taps)
+  GridCand* cand;                // [kGridCandMax] the passing taps of a read-off, ascending q
   double* part;                  // [2 grid] per-CTA partial sums, two alternating sets
   int* icnt;                     // [2 grid] per-CTA counts of the read-off compaction
   int* hist;                     // [5 x 128] radix-select histograms (zeroed per frame)
@@ -65,6 +75,7 @@ __host__ __device__ __forceinline__ size_t grid_scratch_bytes(int M, int N, int 
   for (int i = 0; i < 2; ++i) take(MN * 8);   // X, Vv
   take(MN);           // lab
   take((size_t)p_max * sizeof(PathRecT<float>));
+  take((size_t)kGridCandMax * sizeof(GridCand));
   take((size_t)grid * 16);
   take((size_t)grid * 8);
   take(5 * 128 * 4);
@@ -90,6 +101,7 @@ __host__ __device__ __forceinline__ GridScratch grid_scratch_carve(char* base, i
   G.Vv = reinterpret_cast<float2*>(take(MN * 8));
   G.lab = reinterpret_cast<uint8_t*>(take(MN));
   G.list = reinterpret_cast<PathRecT<float>*>(take((size_t)p_max * sizeof(PathRecT<float>)));
+  G.cand = reinterpret_cast<GridCand*>(take((size_t)kGridCandMax * sizeof(GridCand)));
   G.part = reinterpret_cast<double*>(take((size_t)grid * 16));
   G.icnt = reinterpret_cast<int*>(take((size_t)grid * 8));
   G.hist = reinterpret_cast<int*>(take(5 * 128 * 4));
@@ -315,6 +327,132 @@ __device__ __forceinline__ void grid_prefix(const int* counts, SharedHdr* S) {
   __syncthreads();
 }
 
+// The path list from the n <= kGridCandMax passing taps in cand (ascending q): all of them, or
+// when n > K the exact K largest |h|^2, ties to the lower q (the same list the grid-wide
+// selection gives), into out[0, P) in ascending q (Eq. heff_thres with the p_max cap).  Every
+// CTA computes it alike from the same candidates: thread t holds candidates [t CPT, t CPT + CPT),
+// a radix select of 7 bits per pass finds the K-th largest key from block histograms, and one
+// block scan places the kept taps.  With gout (one CTA) the list is also stored there.
+// All threads call; returns P and sets trunc.
+template <int CPT>
+__device__ __forceinline__ int grid_select(const GridCand* cand, int n, const FrameArgs& A, PathRecT<float>* out,
+                                           SharedHdr* S, const PathIO* gout, int& trunc) {
+  const int tid = threadIdx.x, K = A.p_max;
+  const int M = A.M, N = A.N, MN = M * N;
+  const int b0 = tid * CPT;
+  uint32_t key[CPT];
+  uint32_t have = 0;
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    key[j] = 0;
+    if (b0 + j < n) {
+      key[j] = __ldcg(&cand[b0 + j].key);
+      have |= 1u << j;
+    }
+  }
+  uint32_t keep = have;
+  int total = n, base = b0;
+  trunc = 0;
+  if (n > K) {
+    trunc = 1;
+    uint32_t prefix = 0, fixed = 0;
+    int kleft = K;  // rank of the wanted key among the candidates that match `prefix`
+    const int lane = tid & 31;
+    for (int b = tid; b < 128; b += blockDim.x) S->hist[b] = 0;
+    __syncthreads();
+    for (int hb = 31; hb > 0; hb -= 7) {
+      const int w = hb < 7 ? hb : 7, sh = hb - w;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j)
+        if (((have >> j) & 1u) && ((key[j] ^ prefix) & fixed) == 0) atomicAdd(&S->hist[(key[j] >> sh) & 127u], 1);
+      __syncthreads();
+      if (tid < 32) {  // the bin holding the kleft-th largest, from the top (lane: 4 bins)
+        int c[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          c[j] = S->hist[4 * lane + j];
+          S->hist[4 * lane + j] = 0;
+          sum += c[j];
+        }
+        int suf = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_down_sync(0xffffffffu, suf, o);
+          if (lane + o < 32) suf += v;
+        }
+        int acc = suf - sum;
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+          if (acc < kleft && acc + c[j] >= kleft) {
+            S->isc[2] = 4 * lane + j;
+            S->isc[3] = kleft - acc;
+          }
+          acc += c[j];
+        }
+      }
+      __syncthreads();
+      prefix |= (uint32_t)S->isc[2] << sh;
+      kleft = S->isc[3];
+      fixed |= ((1u << w) - 1u) << sh;
+      __syncthreads();
+    }
+    const uint32_t vK = prefix;  // the K-th largest key
+    const int need = kleft;      // keys equal to vK that are kept: the first `need` in ascending q
+    uint32_t gt = 0, eq = 0;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j)
+      if ((have >> j) & 1u) {
+        if (key[j] > vK) gt |= 1u << j;
+        else if (key[j] == vK) eq |= 1u << j;
+      }
+    int both_total;
+    const int both = block_exclusive_scan((__popc(gt) << 16) | __popc(eq), S->scan, both_total);
+    (void)both_total;
+    int eq_before = both & 0xffff;
+    base = (both >> 16) + min(eq_before, need);
+    keep = 0;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      if ((gt >> j) & 1u) {
+        keep |= 1u << j;
+      } else if ((eq >> j) & 1u) {
+        if (eq_before < need) keep |= 1u << j;
+        ++eq_before;
+      }
+    }
+    total = K;
+  }
+  int pos = base;
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    if ((keep >> j) & 1u) {
+      const GridCand c = cand[b0 + j];
+      const int k = c.q & (M - 1), l = c.q >> A.logM;
+      const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
+      const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+      PathRecT<float> rec;
+      rec.h = c.h;
+      rec.dk = dk;
+      rec.dl = dl;
+      rec.hf = cmul(c.h, tw<float>(A, (size_t)((-dl * dk) & (MN - 1))));
+      rec.pad0 = rec.pad1 = 0;
+      out[pos] = rec;
+      if (gout) {
+        gout->dk[pos] = (int16_t)dk;
+        gout->dl[pos] = (int16_t)dl;
+        store_complex(gout->h, (size_t)pos, gout->tap_dtype, c.h);
+      }
+      ++pos;
+    }
+  }
+  if (gout && tid == 0) {
+    gout->count[0] = total;
+    if (gout->status) gout->status[0] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
+  }
+  __syncthreads();
+  return total;
+}
+
 // EQ: pilot-grid entries per thread in the read-off; E: rows per CG work item (column k, rows
 // j0 .. j0 + E - 1); MINB: CTAs per SM the launch bounds are set for.
 template <int EQ, int E, int MINB>
@@ -417,129 +555,150 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       grid_prefix(G.icnt, S);
       int total = S->isc[3];
       int base = S->isc[2] + in_blk;
-      uint32_t keep = pass;
-      int trunc = 0;
-      if (total > A.p_max) {
-        // the K-th largest |h|^2 among the passing taps, exactly: radix select on the bit
-        // patterns, 7 bits per pass, histograms over the whole grid
-        trunc = 1;
-        const int K = A.p_max;
-        uint32_t prefix = 0, fixed = 0;
-        int kleft = K;
-        int hp = 0;
-        for (int hb = 31; hb > 0; hb -= 7, ++hp) {
-          const int w = hb < 7 ? hb : 7, sh = hb - w;
-          int* H = G.hist + hp * 128;
-#pragma unroll
-          for (int i = 0; i < EQ; ++i)
-            if (((pass >> i) & 1u) && ((mb[i] ^ prefix) & fixed) == 0) atomicAdd(&H[(mb[i] >> sh) & 127u], 1);
-          if (!grid_sync(G.bar, gen)) return fail(io);
-          if (tid < 32) {  // the bin holding the kleft-th largest, from the top (lane: 4 bins)
-            const int lane = tid;
-            int c[4], sum = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              c[j] = __ldcg(H + 4 * lane + j);
-              sum += c[j];
-            }
-            int suf = sum;  // inclusive suffix sum over lanes >= lane
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int n = __shfl_down_sync(0xffffffffu, suf, o);
-              if (lane + o < 32) suf += n;
-            }
-            int acc = suf - sum;  // taps in the bins above this lane's four
-#pragma unroll
-            for (int j = 3; j >= 0; --j) {
-              if (acc < kleft && acc + c[j] >= kleft) {
-                S->isc[2] = 4 * lane + j;
-                S->isc[3] = kleft - acc;
-              }
-              acc += c[j];
-            }
-          }
-          __syncthreads();
-          prefix |= (uint32_t)S->isc[2] << sh;
-          kleft = S->isc[3];
-          fixed |= ((1u << w) - 1u) << sh;
-          __syncthreads();
-        }
-        const uint32_t vK = prefix;  // the K-th largest value; `kleft` ties to it are kept
-        const int need = kleft;
-        uint32_t gt = 0, eq = 0;
+      if (total <= kGridCandMax) {
+        // The passing taps as candidates at their places in ascending q; then every CTA selects
+        // the list from them alike in shared memory: one grid barrier instead of the grid-wide
+        // radix select's and the list's.
+        int pos = base;
 #pragma unroll
         for (int i = 0; i < EQ; ++i)
           if ((pass >> i) & 1u) {
-            if (mb[i] > vK) gt |= 1u << i;
-            else if (mb[i] == vK) eq |= 1u << i;
+            GridCand c;
+            c.q = q_beg + tid * EQ + i;
+            c.key = mb[i];
+            c.h = hv[i];
+            G.cand[pos++] = c;
           }
-        int tg, te;
-        const int gt_in = block_exclusive_scan(__popc(gt), S->scan, tg);
-        const int eq_in = block_exclusive_scan(__popc(eq), S->scan, te);
-        if (tid == 0) {
-          G.icnt[blockIdx.x] = tg;
-          G.icnt[gridDim.x + blockIdx.x] = te;
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        const PathIO* gout = (write_paths && io.paths.count && blockIdx.x == 0) ? &io.paths : nullptr;
+        int trunc = 0;
+        P = grid_select<kGridCandMax / kGridThreads>(G.cand, total, A, paths, S, gout, trunc);
+        if (trunc) st |= kStTrunc;
+      } else {
+        uint32_t keep = pass;
+        int trunc = 0;
+        if (total > A.p_max) {
+          // the K-th largest |h|^2 among the passing taps, exactly: radix select on the bit
+          // patterns, 7 bits per pass, histograms over the whole grid
+          trunc = 1;
+          const int K = A.p_max;
+          uint32_t prefix = 0, fixed = 0;
+          int kleft = K;
+          int hp = 0;
+          for (int hb = 31; hb > 0; hb -= 7, ++hp) {
+            const int w = hb < 7 ? hb : 7, sh = hb - w;
+            int* H = G.hist + hp * 128;
+  #pragma unroll
+            for (int i = 0; i < EQ; ++i)
+              if (((pass >> i) & 1u) && ((mb[i] ^ prefix) & fixed) == 0) atomicAdd(&H[(mb[i] >> sh) & 127u], 1);
+            if (!grid_sync(G.bar, gen)) return fail(io);
+            if (tid < 32) {  // the bin holding the kleft-th largest, from the top (lane: 4 bins)
+              const int lane = tid;
+              int c[4], sum = 0;
+  #pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                c[j] = __ldcg(H + 4 * lane + j);
+                sum += c[j];
+              }
+              int suf = sum;  // inclusive suffix sum over lanes >= lane
+  #pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_down_sync(0xffffffffu, suf, o);
+                if (lane + o < 32) suf += n;
+              }
+              int acc = suf - sum;  // taps in the bins above this lane's four
+  #pragma unroll
+              for (int j = 3; j >= 0; --j) {
+                if (acc < kleft && acc + c[j] >= kleft) {
+                  S->isc[2] = 4 * lane + j;
+                  S->isc[3] = kleft - acc;
+                }
+                acc += c[j];
+              }
+            }
+            __syncthreads();
+            prefix |= (uint32_t)S->isc[2] << sh;
+            kleft = S->isc[3];
+            fixed |= ((1u << w) - 1u) << sh;
+            __syncthreads();
+          }
+          const uint32_t vK = prefix;  // the K-th largest value; `kleft` ties to it are kept
+          const int need = kleft;
+          uint32_t gt = 0, eq = 0;
+  #pragma unroll
+          for (int i = 0; i < EQ; ++i)
+            if ((pass >> i) & 1u) {
+              if (mb[i] > vK) gt |= 1u << i;
+              else if (mb[i] == vK) eq |= 1u << i;
+            }
+          int tg, te;
+          const int gt_in = block_exclusive_scan(__popc(gt), S->scan, tg);
+          const int eq_in = block_exclusive_scan(__popc(eq), S->scan, te);
+          if (tid == 0) {
+            G.icnt[blockIdx.x] = tg;
+            G.icnt[gridDim.x + blockIdx.x] = te;
+          }
+          if (!grid_sync(G.bar, gen)) return fail(io);
+          grid_prefix(G.icnt, S);
+          const int gt_pre = S->isc[2];
+          __syncthreads();
+          grid_prefix(G.icnt + gridDim.x, S);
+          int eq_before = S->isc[2] + eq_in;
+          base = gt_pre + gt_in + min(eq_before, need);
+          keep = 0;
+  #pragma unroll
+          for (int i = 0; i < EQ; ++i) {
+            if ((gt >> i) & 1u) {
+              keep |= 1u << i;
+            } else if ((eq >> i) & 1u) {
+              if (eq_before < need) keep |= 1u << i;
+              ++eq_before;
+            }
+          }
+          total = K;
+        }
+        if (trunc) st |= kStTrunc;
+        const PathIO* gout = (write_paths && io.paths.count) ? &io.paths : nullptr;
+        int pos = base;
+  #pragma unroll
+        for (int i = 0; i < EQ; ++i) {
+          if ((keep >> i) & 1u) {
+            const int q = q_beg + tid * EQ + i;
+            const int k = q & (M - 1), l = q >> logM;
+            const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
+            const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+            PathRec rec;
+            rec.h = hv[i];
+            rec.dk = dk;
+            rec.dl = dl;
+            rec.hf = cmul(hv[i], tw<R>(A, (size_t)((-dl * dk) & (MN - 1))));
+            rec.pad0 = rec.pad1 = 0;
+            G.list[pos] = rec;
+            if (gout) {
+              gout->dk[pos] = (int16_t)dk;
+              gout->dl[pos] = (int16_t)dl;
+              store_complex(gout->h, (size_t)pos, gout->tap_dtype, hv[i]);
+            }
+            ++pos;
+          }
+        }
+        if (gout && blockIdx.x == 0 && tid == 0) {
+          gout->count[0] = total;
+          if (gout->status) gout->status[0] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
         }
         if (!grid_sync(G.bar, gen)) return fail(io);
-        grid_prefix(G.icnt, S);
-        const int gt_pre = S->isc[2];
-        __syncthreads();
-        grid_prefix(G.icnt + gridDim.x, S);
-        int eq_before = S->isc[2] + eq_in;
-        base = gt_pre + gt_in + min(eq_before, need);
-        keep = 0;
-#pragma unroll
-        for (int i = 0; i < EQ; ++i) {
-          if ((gt >> i) & 1u) {
-            keep |= 1u << i;
-          } else if ((eq >> i) & 1u) {
-            if (eq_before < need) keep |= 1u << i;
-            ++eq_before;
-          }
-        }
-        total = K;
-      }
-      if (trunc) st |= kStTrunc;
-      const PathIO* gout = (write_paths && io.paths.count) ? &io.paths : nullptr;
-      int pos = base;
-#pragma unroll
-      for (int i = 0; i < EQ; ++i) {
-        if ((keep >> i) & 1u) {
-          const int q = q_beg + tid * EQ + i;
-          const int k = q & (M - 1), l = q >> logM;
-          const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
-          const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+        P = total;
+        for (int p = tid; p < P; p += blockDim.x) {
           PathRec rec;
-          rec.h = hv[i];
-          rec.dk = dk;
-          rec.dl = dl;
-          rec.hf = cmul(hv[i], tw<R>(A, (size_t)((-dl * dk) & (MN - 1))));
+          const float4* s4 = reinterpret_cast<const float4*>(G.list + p);
+          const float4 a = __ldcg(s4), b = __ldcg(s4 + 1);
+          rec.h = make_float2(a.x, a.y);
+          rec.hf = make_float2(a.z, a.w);
+          rec.dk = __float_as_int(b.x);
+          rec.dl = __float_as_int(b.y);
           rec.pad0 = rec.pad1 = 0;
-          G.list[pos] = rec;
-          if (gout) {
-            gout->dk[pos] = (int16_t)dk;
-            gout->dl[pos] = (int16_t)dl;
-            store_complex(gout->h, (size_t)pos, gout->tap_dtype, hv[i]);
-          }
-          ++pos;
+          paths[p] = rec;
         }
-      }
-      if (gout && blockIdx.x == 0 && tid == 0) {
-        gout->count[0] = total;
-        if (gout->status) gout->status[0] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
-      }
-      if (!grid_sync(G.bar, gen)) return fail(io);
-      P = total;
-      for (int p = tid; p < P; p += blockDim.x) {
-        PathRec rec;
-        const float4* s4 = reinterpret_cast<const float4*>(G.list + p);
-        const float4 a = __ldcg(s4), b = __ldcg(s4 + 1);
-        rec.h = make_float2(a.x, a.y);
-        rec.hf = make_float2(a.z, a.w);
-        rec.dk = __float_as_int(b.x);
-        rec.dl = __float_as_int(b.y);
-        rec.pad0 = rec.pad1 = 0;
-        paths[p] = rec;
       }
       if (tid == 0) cnt[0] = P;
       __syncthreads();

@@ -91,6 +91,27 @@ def test_grid_estimate_truncation(p_max):
             assert st[f] == 6 and len(lists[f][0]) == p_max
 
 
+@pytest.mark.parametrize("theta_scale", [1e-3, 0.05])
+def test_grid_estimate_many_passing_taps(theta_scale):
+    """A threshold so low that more taps pass than the CTAs select among in shared memory
+    (every tap at 1e-3; thousands at 0.05): the grid-wide radix select and compaction take
+    over and still give the exact p_max largest in ascending q."""
+    M, N, F, p_max = 1024, 32, 2, 64
+    b = synth.fractional_batch(F, seed=9910, M=M, N=N, Q=16, snr_db=(10, 30))
+    theta = (b["theta"] * theta_scale).astype(np.float32)
+    plan = Plan(M, N, 1, 1, 16, p_max=p_max)
+    paths = plan.estimate(to_dev(b["y_pilot_td"]), to_dev(theta), F)
+    lists = paths.to_host()
+    st = paths.status.cpu().numpy()
+    for f in range(F):
+        heff = dc.heff_readoff(zak.dzt(b["y_pilot_td"][f, 0, 0].astype(complex), M, N), M // 2, N // 2,
+                               b["a_pilot"])
+        n_pass = int((np.abs(heff) > float(theta[f])).sum())
+        assert n_pass > p_max
+        check_path_list(M, N, lists[f], heff, float(theta[f]), p_max)
+        assert st[f] == 6 and len(lists[f][0]) == p_max
+
+
 def test_grid_dzt():
     M, N, n = 2048, 16, 3
     g = np.random.default_rng(9901)
