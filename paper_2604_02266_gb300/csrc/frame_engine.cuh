@@ -364,10 +364,10 @@ __device__ __forceinline__ void write_ext(typename Cx<R>::C* ext, const FrameArg
 // of column k - dk and path m reads window[L - 1 - m + i]; adjoint: rows start at
 // (j0 + dl0) mod N of column k + dk and path m reads window[m + i].
 //
-// Coefficients: with kCoef they come from the frame's table `ct` (this list's column-k entry
-// of path 0; path p at ct[p M]) -- hf W[dl k] for kFwd, h W[dl k] for the adjoint, whose
-// conjugate the caller's final combine applies -- else they are formed here from the path
-// record and the twiddle table.
+// Coefficients: with kCoef == 1 they come from the frame's table `ct` (this list's column-k
+// entry of path 0; path p at ct[p M]) -- hf W[dl k] for kFwd, h W[dl k] for the adjoint, whose
+// conjugate the caller's final combine applies; with kCoef == 2 from a CTA's table (see
+// GatherAt); else they are formed here from the path record and the twiddle table.
 //
 // A run is applied in two phases: load_run gathers its window and its L coefficients into
 // registers, mac_run accumulates.  Kernels whose extensions live in global memory issue two
@@ -387,20 +387,21 @@ struct GatherAt {
 };
 
 // Coefficient D of path p (list order, delay-Doppler (dk, dl0 + m) of run rr) at column k.
-template <typename R, bool kFwd>
+template <typename R, bool kFwd, bool kTab>
 __device__ __forceinline__ typename Cx<R>::C path_coef(const FrameArgs& A, const GatherAt<R>& at,
                                                        const PathRecT<R>* pl, const RunRec& rr, int m, int k) {
   const int p = rr.start + m;
-  if (at.ct) {  // adjoint entries unconjugated: the caller's final combine conjugates them
+  if constexpr (kTab) {  // adjoint entries unconjugated: the caller's final combine conjugates them
     const typename Cx<R>::C c = at.ct[(size_t)p * at.ct_rs + (k - at.ct_c0)];
     return kFwd ? cmul(c, at.phi[p]) : c;
+  } else {
+    const PathRecT<R> rec = pl[p];
+    const typename Cx<R>::C t = tab<R>(A, (rr.dl0 + m + (A.N >> 1)) * A.M + k);
+    return kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
   }
-  const PathRecT<R> rec = pl[p];
-  const typename Cx<R>::C t = tab<R>(A, (rr.dl0 + m + (A.N >> 1)) * A.M + k);
-  return kFwd ? cmul(rec.hf, t) : conjf2(cmul(rec.h, t));
 }
 
-template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef>
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, int kCoef>
 __device__ __forceinline__ void load_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
                                          const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
                                          int j0, const GatherAt<R>& at, typename Cx<R>::C (&W)[L + E - 1],
@@ -413,13 +414,13 @@ __device__ __forceinline__ void load_run(const typename Cx<R>::C* src, const Pat
   const C* a = src + (size_t)row0 * RS + (kFwd ? -rr.dk : rr.dk) * CS;
 #pragma unroll
   for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
-  const C* cr = kCoef ? ct + (size_t)rr.start * M : nullptr;
+  const C* cr = kCoef == 1 ? ct + (size_t)rr.start * M : nullptr;
 #pragma unroll
   for (int m = 0; m < L; ++m) {
-    if constexpr (kCoef) {
+    if constexpr (kCoef == 1) {
       D[m] = cr[(size_t)m * M];
     } else {
-      D[m] = path_coef<R, kFwd>(A, at, pl, rr, m, k);
+      D[m] = path_coef<R, kFwd, kCoef == 2>(A, at, pl, rr, m, k);
     }
   }
 }
@@ -436,7 +437,7 @@ __device__ __forceinline__ void mac_run(const typename Cx<R>::C (&W)[L + E - 1],
   }
 }
 
-template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef, bool kPair = kRowMajor>
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, int kCoef, bool kPair = kRowMajor>
 __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const PathRecT<R>* pl,
                                           const typename Cx<R>::C* ct, const RunRec& rr, const FrameArgs& A, int k,
                                           int j0, const GatherAt<R>& at, typename Cx<R>::C (&accA)[E],
@@ -456,14 +457,14 @@ __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const Pa
     C W[L + E - 1];
 #pragma unroll
     for (int w = 0; w < L + E - 1; ++w) W[w] = a[w * RS];
-    const C* cr = kCoef ? ct + (size_t)rr.start * M : nullptr;
+    const C* cr = kCoef == 1 ? ct + (size_t)rr.start * M : nullptr;
 #pragma unroll
     for (int m = 0; m < L; ++m) {
       C D;
-      if constexpr (kCoef) {
+      if constexpr (kCoef == 1) {
         D = cr[(size_t)m * M];
       } else {
-        D = path_coef<R, kFwd>(A, at, pl, rr, m, k);
+        D = path_coef<R, kFwd, kCoef == 2>(A, at, pl, rr, m, k);
       }
       const C DX = Cx<R>::make(D.x, D.x), DY = Cx<R>::make(D.y, D.y);
 #pragma unroll
@@ -474,7 +475,7 @@ __device__ __forceinline__ void apply_run(const typename Cx<R>::C* src, const Pa
 
 // Runs [q, end) of one length class, two at a time when the extension is in global memory
 // (kPair: two runs' loads in flight before either accumulates).
-template <typename R, int E, int L, bool kFwd, bool kRowMajor, bool kCoef, bool kPair = kRowMajor>
+template <typename R, int E, int L, bool kFwd, bool kRowMajor, int kCoef, bool kPair = kRowMajor>
 __device__ __forceinline__ int apply_runs(const typename Cx<R>::C* src, const PathRecT<R>* pl,
                                           const typename Cx<R>::C* ct, const RunRec* rl, int q, int end,
                                           const FrameArgs& A, int k, int j0, const GatherAt<R>& at,
@@ -501,7 +502,7 @@ constexpr int kColHalf = -0x40000000;  // gather column offset: the extension's 
 // extension's rows are `rs` elements apart (2 M by default) -- a shared-memory window of
 // a row-major extension passes its own offset and stride; ct / phi / ct_rs / ct_c0: a CTA's
 // coefficient table (see GatherAt), else the coefficients are formed per path.
-template <typename R, int E, bool kFwd, bool kRowMajor, bool kCoef, bool kPair = kRowMajor>
+template <typename R, int E, bool kFwd, bool kRowMajor, int kCoef, bool kPair = kRowMajor>
 __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                             const RunRec* runs, const int* nruns, const typename Cx<R>::C* coef,
                                             const FrameArgs& A, int b, int k, int j0, typename Cx<R>::C (&out)[E],
@@ -524,7 +525,7 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
     const int li = kFwd ? b * A.ntx + o : o * A.ntx + b;
     const PathRecT<R>* pl = paths + (size_t)li * A.p_max;
     const RunRec* rl = runs + (size_t)li * A.p_max;
-    const C* ct = kCoef ? coef + (size_t)li * A.p_max * A.M + k : nullptr;
+    const C* ct = kCoef == 1 ? coef + (size_t)li * A.p_max * A.M + k : nullptr;
     // runs are stored longest first: n4 of length 4, then n3, n2 and n1 (packed counts)
     const int packed = nruns[li];
     const int n4 = packed & 127, n3 = (packed >> 7) & 127, n2 = (packed >> 14) & 255, n1 = (packed >> 22) & 511;
@@ -559,15 +560,16 @@ __device__ __forceinline__ void gather_runs(const typename Cx<R>::C* ext, size_t
   }
   // accA = sum D.x W, accB = sum D.y W: D W = (A.x - B.y, A.y + B.x); for the adjoint's table
   // entries c (D = conj(c)): (A.x + B.y, A.y - B.x)
-  const bool conj_tab = !kFwd && (kCoef || ct_tab != nullptr);
+  constexpr bool conj_tab = !kFwd && kCoef != 0;
 #pragma unroll
   for (int i = 0; i < E; ++i)
     out[i] = conj_tab ? Cx<R>::make(accA[i].x + accB[i].y, accA[i].y - accB[i].x)
                       : Cx<R>::make(accA[i].x - accB[i].y, accA[i].y + accB[i].x);
 }
 
-// coefF / coefA: the frame's coefficient tables (kCoef), else unused.
-template <typename R, int E, bool kRowMajor = false, bool kCoef = false, bool kPair = kRowMajor>
+// kCoef: 0 coefficients formed per path, 1 the frame's tables coefF / coefA, 2 a CTA's table
+// ct_tab with the forward phases phi (see GatherAt).
+template <typename R, int E, bool kRowMajor = false, int kCoef = 0, bool kPair = kRowMajor>
 __device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int r, int k,
                                            int j0, typename Cx<R>::C (&out)[E],
@@ -577,7 +579,7 @@ __device__ __forceinline__ void gather_fwd(const typename Cx<R>::C* ext, size_t 
   gather_runs<R, E, true, kRowMajor, kCoef, kPair>(ext, blk, paths, runs, nruns, coefF, A, r, k, j0, out, rs, col0,
                                                    ct_tab, phi, ct_rs, ct_c0);
 }
-template <typename R, int E, bool kRowMajor = false, bool kCoef = false, bool kPair = kRowMajor>
+template <typename R, int E, bool kRowMajor = false, int kCoef = 0, bool kPair = kRowMajor>
 __device__ __forceinline__ void gather_adj(const typename Cx<R>::C* ext, size_t blk, const PathRecT<R>* paths,
                                            const RunRec* runs, const int* nruns, const FrameArgs& A, int t, int k,
                                            int j0, typename Cx<R>::C (&out)[E],

@@ -808,8 +808,8 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         const int g = s >> gshift, kk = s - (g << gshift);
         if (kk >= ncol) continue;
         const int k = k0 + kk, j0 = g * E;
-        if (win) gather_adj<R, E, true, false, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
-        else gather_adj<R, E, true, false, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
+        if (win) gather_adj<R, E, true, 2, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
+        else gather_adj<R, E, true, 2, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           G.X[(size_t)(j0 + i) * M + k] = make_float2(0.f, 0.f);
@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
             const int g = s >> gshift, kk = s - (g << gshift);
             if (kk >= ncol) continue;
             const int k = k0 + kk, j0 = g * E;
-            gather_fwd<R, E, true, false, false>(bufP, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
+            gather_fwd<R, E, true, 2, false>(bufP, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
             grid_ext_store<E>(G.extT, A, k, j0, v, k < hw || k >= M - hw, wn);
           }
         } else {
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
             const int g = s >> gshift, kk = s - (g << gshift);
             if (kk >= ncol) continue;
             const int k = k0 + kk, j0 = g * E;
-            gather_fwd<R, E, true, false, false>(extPc, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
+            gather_fwd<R, E, true, 2, false>(extPc, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
             grid_ext_store<E>(G.extT, A, k, j0, v, true, wn);
           }
         }
@@ -897,8 +897,8 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
           const int g = s >> gshift, kk = s - (g << gshift);
           if (kk >= ncol) continue;
           const int k = k0 + kk, j0 = g * E;
-          if (win) gather_adj<R, E, true, false, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
-          else gather_adj<R, E, true, false, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
+          if (win) gather_adj<R, E, true, 2, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
+          else gather_adj<R, E, true, 2, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const C pv = p_at(k, j0 + i);
