@@ -15,6 +15,8 @@
 // (or loaded lists), FP32.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoding is done through the runtime's driver entry point)
+
 #include "frame_kernel.cuh"
 
 namespace zotfs {
@@ -26,6 +28,11 @@ constexpr uint32_t kGridMaxPolls = 1u << 22;
 
 constexpr int kGridMaxCtas = 512;  // two CTAs per SM on up to 256 SMs
 constexpr int kGridCandMax = 4096;  // passing taps the CTAs select among in shared memory
+
+// Elements of one CG window (N + E + 3 rows of win_cols), rounded to 128 bytes.
+__host__ __device__ __forceinline__ size_t grid_window_elems(int N, int win_cols) {
+  return (((size_t)(N + kGridE + 3) * (size_t)win_cols * sizeof(float2) + 127) & ~size_t(127)) / sizeof(float2);
+}
 
 // A tap that passed the read-off threshold: its grid index, |h|^2 as an ordered bit pattern,
 // and h.
@@ -63,6 +70,12 @@ struct GridScratch {
   // shared-memory windows of the CG gathers (set by the launch): columns per window row (0: no
   // windows) and the largest |dk| a window covers
   int win_cols, win_dcap;
+};
+
+// TMA descriptors of the extensions of c and t (row-major, rows N + E + 3 of 2 M 8-byte
+// elements), with a box of the CG windows' size: win_cols columns by all rows.
+struct GridMaps {
+  CUtensorMap c, t;
 };
 
 // Rows of the extension and bytes of the scratch for one (M, N, p_max) at a given grid.
@@ -205,29 +218,29 @@ __device__ __forceinline__ void bulk_g2s_tx(void* dst, const void* src, uint32_t
       : "memory");
 }
 
-// Copy the columns [A0, A1) of rows [0, R) of a row-major extension into the shared-memory
-// window dst (rows Wp elements apart) by bulk async copies, one per row, issued by warp 0 after
-// one arm of the barrier with all the bytes.  A0 and A1 are even, so every copy starts 16-byte
-// aligned with a multiple of 16 bytes, as the bulk copy requires; nothing is copied when
-// A0 == A1.  The extension was written by other CTAs before the grid barrier this CTA passed
-// (generic stores): the issuing threads order them before the async reads with a proxy fence.
-// All threads call; false, uniformly, if the bounded wait gave up.
-__device__ __forceinline__ bool grid_window_load(float2* dst, const float2* src, int M, int R, int A0, int A1, int Wp,
-                                                 uint64_t* bar, uint32_t& phase) {
+// Copy the box of the CG windows -- columns [A0, A0 + win_cols) of all rows of a row-major
+// extension -- into the shared-memory window dst (row-major, rows win_cols elements apart) by
+// one tiled bulk tensor copy, issued by thread 0 after arming the barrier with the box's bytes.
+// A0 is even, so the copy's inner coordinate A0 + M/2 is a multiple of 16 bytes; columns past
+// the extension read as zeros.  The extension was written by other CTAs before the grid barrier
+// this CTA passed (generic stores): the issuing thread orders them before the async read with a
+// proxy fence.  All threads call (`active` false: no copy); false, uniformly, if the bounded
+// wait gave up.
+__device__ __forceinline__ bool grid_window_load(float2* dst, const CUtensorMap* map, int M, int A0,
+                                                 uint32_t box_bytes, bool active, uint64_t* bar, uint32_t& phase) {
   __syncthreads();  // earlier generic accesses to the window are complete
-  const uint32_t row_bytes = (uint32_t)(A1 - A0) * 8u;
   bool ok = true;
-  if (row_bytes) {
-    if (threadIdx.x < 32) {
-      if (threadIdx.x == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, row_bytes * (uint32_t)R);
-      }
-      __syncwarp();
+  if (active) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
       asm volatile("fence.proxy.async.global;" ::: "memory");
-      const size_t off = (size_t)(A0 + (M >> 1));
-      for (int r = threadIdx.x; r < R; r += 32)
-        bulk_g2s_tx(dst + (size_t)r * Wp, src + (size_t)r * (size_t)(2 * M) + off, row_bytes, bar);
+      mbar_arrive_expect_tx(bar, box_bytes);
+      const int x = A0 + (M >> 1), y = 0;
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              smem_u32(dst)),
+          "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+          : "memory");
     }
     ok = mbar_wait_bounded(bar, phase, kMaxPolls);
     if (!ok) ok = mbar_wait_bounded(bar, phase, kMaxPolls);  // let an in-flight copy land
@@ -457,7 +470,7 @@ __device__ __forceinline__ int grid_select(const GridCand* cand, int n, const Fr
 // j0 .. j0 + E - 1); MINB: CTAs per SM the launch bounds are set for.
 template <int EQ, int E, int MINB>
 __global__ void __launch_bounds__(kGridThreads, MINB)
-    grid_kernel(const __grid_constant__ FrameArgs A, GridScratch G) {
+    grid_kernel(const __grid_constant__ FrameArgs A, GridScratch G, const __grid_constant__ GridMaps maps) {
   using R = float;
   using C = float2;
   using PathRec = PathRecT<R>;
@@ -485,7 +498,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
   C* phi = reinterpret_cast<C*>(smem + off);
   off += ((size_t)A.p_max * sizeof(C) + 127) & ~size_t(127);
   C* bufP = reinterpret_cast<C*>(smem + off);
-  C* bufX = bufP + (size_t)(A.N + E + 3) * G.win_cols;
+  C* bufX = bufP + grid_window_elems(A.N, G.win_cols);  // both 128-byte aligned, as the tensor copy needs
 
   const int M = A.M, N = A.N, MN = M * N, logM = A.logM, tid = threadIdx.x;
   const int gtid = blockIdx.x * blockDim.x + tid, nthr = gridDim.x * blockDim.x;
@@ -775,6 +788,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       const bool win = G.win_cols > 0 && dmax <= G.win_dcap;
       const int A0 = (k0 - dmax) & ~1, Wc = ((k1 + dmax + 1) & ~1) - A0, Wp = G.win_cols;
       const int A1 = ncol > 0 ? A0 + Wc : A0;  // no window when the CTA has no columns
+      const uint32_t box_bytes = (uint32_t)(N + E + 3) * (uint32_t)Wp * 8u;
       const int Rw = N + E + 3, colw = -A0;
 
       const int hw = win ? dmax + 2 : M;  // halo columns stored: k < hw or k >= M - hw
@@ -802,7 +816,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       if (!grid_sync(G.bar, gen)) return fail(io);
 
       // b = H^H y;  c = b, x = 0, c_n = ||c||^2  (p = c is formed by the first iteration)
-      if (win && !grid_window_load(bufX, G.extT, M, Rw, A0, A1, Wp, &S->mbar, mph)) return wfail(io);
+      if (win && !grid_window_load(bufX, &maps.t, M, A0, box_bytes, ncol > 0, &S->mbar, mph)) return wfail(io);
       R part = 0;
       for (int s = tid; s < nslots; s += blockDim.x) {
         const int g = s >> gshift, kk = s - (g << gshift);
@@ -836,7 +850,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         const R beta = iter ? (R)S->fsc[1] : (R)0;
         // p = c + beta p (p = c in the first iteration), then t = H p
         if (win) {
-          if (!grid_window_load(bufX, G.extC, M, Rw, A0, A1, Wp, &S->mbar, mph)) return wfail(io);
+          if (!grid_window_load(bufX, &maps.c, M, A0, box_bytes, ncol > 0, &S->mbar, mph)) return wfail(io);
           for (int e = tid; e < (ncol > 0 ? Rw * Wc : 0); e += blockDim.x) {
             const int r = e / Wc, c = e - r * Wc;
             const C cv = bufX[r * Wp + c];
@@ -891,7 +905,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         // p of item (k, l): the window, else the global extension (written this iteration)
         auto p_at = [&](int k, int l) { return win ? bufP[l * Wp + (k - A0)] : main_at(extPc, k, l); };
         // a = H^H t + lambda p;  Re(p^H a)
-        if (win && !grid_window_load(bufX, G.extT, M, Rw, A0, A1, Wp, &S->mbar, mph)) return wfail(io);
+        if (win && !grid_window_load(bufX, &maps.t, M, A0, box_bytes, ncol > 0, &S->mbar, mph)) return wfail(io);
         part = 0;
         for (int s = tid; s < nslots; s += blockDim.x) {
           const int g = s >> gshift, kk = s - (g << gshift);
@@ -1012,7 +1026,7 @@ __host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max, int
   off += ((size_t)N * sizeof(float2) + 127) & ~size_t(127);
   off += ((size_t)p_max * cpc * sizeof(float2) + 127) & ~size_t(127);
   off += ((size_t)p_max * sizeof(float2) + 127) & ~size_t(127);
-  off += 2 * (size_t)(N + kGridE + 3) * (size_t)win_cols * sizeof(float2);
+  off += 2 * grid_window_elems(N, win_cols) * sizeof(float2);
   return off;
 }
 

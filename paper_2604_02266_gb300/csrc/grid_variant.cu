@@ -1,5 +1,6 @@
 // Instantiations and cooperative launch of the paper-scale grid receiver (frame_grid.cuh).
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "frame_grid.cuh"
@@ -9,7 +10,7 @@ namespace zotfs {
 
 namespace {
 
-using GridKern = void (*)(const FrameArgs, GridScratch);
+using GridKern = void (*)(const FrameArgs, GridScratch, const GridMaps);
 
 // Instantiations: (read-off entries per thread EQ, CG rows per item E, CTAs per SM MINB).
 // Items of 4 rows at three CTAs per SM were measured slower than 8 rows at two (0.86 against
@@ -55,6 +56,37 @@ __global__ void check_grid_wait_kernel(uint32_t max_polls, int32_t* status) {
   if (threadIdx.x == 0) *status = ok ? ZOTFS_OK : ZOTFS_ETIMEOUT;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver
+// library); null when the driver does not provide it.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiled>(f);
+  }();
+  return fn;
+}
+
+// The descriptor of one row-major CG extension (rows N + E + 3 of 2 M float2, 8-byte
+// elements) with a box of win_cols columns by all rows.
+bool encode_ext_map(CUtensorMap* map, float2* ext, int M, int N, int win_cols) {
+  EncodeTiled fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * M), (cuuint64_t)(N + kGridE + 3)};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * M) * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)win_cols, (cuuint32_t)(N + kGridE + 3)};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, ext, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 }  // namespace
 
 cudaError_t check_bounded_wait(int which, uint32_t max_polls, int32_t* status, cudaStream_t stream) {
@@ -76,21 +108,23 @@ bool grid_shape(int M, int N, int nrx, int ntx) {
          N <= 64 && (size_t)M * N <= kGridMaxElems;
 }
 
-// The CG windows of one CTA at a given grid: its ceil(M / grid) columns plus dcap on either
+// The CG windows of one CTA at a given grid: its grid_cols_per_cta columns plus dcap on either
 // side (and one for the even start), as much as the shared memory left at `occ` CTAs per SM
-// holds, dcap at most M / 2 - 2 (the windows stay inside the extensions' halo) and 128.
+// holds, dcap at most M / 2 - 2 (the windows stay inside the extensions' halo) and 128, and the
+// window at most 256 columns (the tensor copy's box).
 void grid_window(int M, int N, int p_max, int grid, int occ, int smem_per_sm, int smem_reserved, int& cols,
                  int& dcap) {
   cols = 0;
   dcap = -1;
   const int cpc = grid_cols_per_cta(M, grid);
   const long long base = (long long)grid_smem_bytes(N, p_max, 0, cpc);
-  const long long avail = (long long)smem_per_sm / occ - smem_reserved - base;
+  const long long avail = (long long)smem_per_sm / occ - smem_reserved - base - 256;  // windows rounded to 128 B
   const long long row_bytes = 2LL * (N + kGridE + 3) * (long long)sizeof(float2);  // both windows, one column
   if (avail <= 0) return;
   const long long wmax = avail / row_bytes;
   int d = (int)std::min<long long>((wmax - cpc - 3) / 2, 128);  // cols below stays <= wmax
   d = std::min(d, M / 2 - 2);
+  d = std::min(d, (256 - cpc - 3) / 2);  // a tensor copy's box spans at most 256 columns
   if (d < 1) return;
   dcap = d;
   cols = (cpc + 2 * d + 2 + 1) & ~1;
@@ -145,10 +179,18 @@ cudaError_t grid_launch(const GridCfg& cfg, const FrameArgs& A, char* scratch, c
   GridScratch G = grid_scratch_carve(scratch, A.M, A.N, A.p_max, cfg.grid);
   G.win_cols = cfg.win_cols;
   G.win_dcap = cfg.win_dcap;
+  // the windows' tensor copies; without the descriptors the gathers read global memory
+  GridMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  if (G.win_cols > 0 && !(encode_ext_map(&maps.c, G.extC, A.M, A.N, G.win_cols) &&
+                          encode_ext_map(&maps.t, G.extT, A.M, A.N, G.win_cols))) {
+    G.win_cols = 0;
+    G.win_dcap = -1;
+  }
   e = cudaMemsetAsync(G.bar, 0, sizeof(GridBarrier), stream);
   if (e != cudaSuccess) return e;
   FrameArgs args = A;
-  void* params[] = {&args, &G};
+  void* params[] = {&args, &G, &maps};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3((unsigned)cfg.grid),
                                      dim3((unsigned)cfg.T), params, cfg.smem, stream);
 }
