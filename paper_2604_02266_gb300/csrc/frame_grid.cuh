@@ -60,7 +60,6 @@ struct GridScratch {
   float2* extT;                  // extension of y, then of t = H p
   float2* extC;                  // extension of the residual c
   float2 *X, *Vv;                // [MN] the CG vectors x and a
-  uint8_t* lab;                  // [MN] hard labels, bit j of the label = bit j of the symbol
   PathRecT<float>* list;         // [p_max] the frame's path list (read-offs with many taps)
   GridCand* cand;                // [kGridCandMax] the passing taps of a read-off, ascending q
   double* part;                  // [2 grid] per-CTA partial sums, two alternating sets
@@ -86,7 +85,6 @@ __host__ __device__ __forceinline__ size_t grid_scratch_bytes(int M, int N, int 
   take(MN * 8);       // Y
   for (int i = 0; i < 4; ++i) take(ext * 8);  // extP[0], extP[1], extT, extC
   for (int i = 0; i < 2; ++i) take(MN * 8);   // X, Vv
-  take(MN);           // lab
   take((size_t)p_max * sizeof(PathRecT<float>));
   take((size_t)kGridCandMax * sizeof(GridCand));
   take((size_t)grid * 16);
@@ -112,7 +110,6 @@ __host__ __device__ __forceinline__ GridScratch grid_scratch_carve(char* base, i
   G.extC = reinterpret_cast<float2*>(take(ext * 8));
   G.X = reinterpret_cast<float2*>(take(MN * 8));
   G.Vv = reinterpret_cast<float2*>(take(MN * 8));
-  G.lab = reinterpret_cast<uint8_t*>(take(MN));
   G.list = reinterpret_cast<PathRecT<float>*>(take((size_t)p_max * sizeof(PathRecT<float>)));
   G.cand = reinterpret_cast<GridCand*>(take((size_t)kGridCandMax * sizeof(GridCand)));
   G.part = reinterpret_cast<double*>(take((size_t)grid * 16));
@@ -167,15 +164,15 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned& gen, uint32_
 
 // Store DD value v of (delay k, Doppler l) into a row-major quasi-periodic extension (element
 // (A, r) at r 2M + A + M/2, rows N + E + 3): the main column, the halo column with its
-// quasi-periodic phase, and the periodic halo rows -- what write_ext<R, E, true> stores for one
-// element.
+// quasi-periodic phase W_N^{+-l} (from wn[l] = W_N^{-l} in shared memory), and the periodic
+// halo rows.
 template <int E>
-__device__ __forceinline__ void ext_store_rm(float2* ext, const FrameArgs& A, int k, int l, float2 v) {
-  const int M = A.M, N = A.N, Hk = M >> 1, MN = M * N;
+__device__ __forceinline__ void ext_store_rm(float2* ext, const FrameArgs& A, int k, int l, float2 v, const float2* wn) {
+  const int M = A.M, N = A.N, Hk = M >> 1;
   const bool low = k < Hk;
   const int mc = k + Hk, hc = (low ? k + M : k - M) + Hk;
-  const int widx = low ? (l << A.logM) : ((MN - (l << A.logM)) & (MN - 1));
-  const float2 hv = cmul(v, tw<float>(A, widx));
+  const float2 w = wn[l];
+  const float2 hv = cmul(v, low ? conjf2(w) : w);
   for (int r = l; r < N + E + 3; r += N) {
     ext[(size_t)r * 2 * M + mc] = v;
     ext[(size_t)r * 2 * M + hc] = hv;
@@ -287,7 +284,7 @@ __device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, 
       const int l = e / kGridDftCols, kk = e - l * kGridDftCols;
       const float2 v = cscale(tile[bitrev(l, logN) * kGridDftCols + kk], s);
       if (Y) Y[(size_t)l * M + k0 + kk] = v;
-      if (ext) ext_store_rm<E>(ext, A, k0 + kk, l, v);
+      if (ext) ext_store_rm<E>(ext, A, k0 + kk, l, v, wn);
     }
     __syncthreads();
   }
@@ -351,7 +348,7 @@ template <int CPT>
 __device__ __forceinline__ int grid_select(const GridCand* cand, int n, const FrameArgs& A, PathRecT<float>* out,
                                            SharedHdr* S, const PathIO* gout, int& trunc) {
   const int tid = threadIdx.x, K = A.p_max;
-  const int M = A.M, N = A.N, MN = M * N;
+  const int M = A.M, N = A.N;
   const int b0 = tid * CPT;
   uint32_t key[CPT];
   uint32_t have = 0;
@@ -443,11 +440,11 @@ __device__ __forceinline__ int grid_select(const GridCand* cand, int n, const Fr
       const int k = c.q & (M - 1), l = c.q >> A.logM;
       const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
       const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
-      PathRecT<float> rec;
+      PathRecT<float> rec;  // hf unused: the grid CG forms its factors from a table and phases
       rec.h = c.h;
       rec.dk = dk;
       rec.dl = dl;
-      rec.hf = cmul(c.h, tw<float>(A, (size_t)((-dl * dk) & (MN - 1))));
+      rec.hf = make_float2(0.f, 0.f);
       rec.pad0 = rec.pad1 = 0;
       out[pos] = rec;
       if (gout) {
@@ -851,12 +848,20 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         // p = c + beta p (p = c in the first iteration), then t = H p
         if (win) {
           if (!grid_window_load(bufX, &maps.c, M, A0, box_bytes, ncol > 0, &S->mbar, mph)) return wfail(io);
-          for (int e = tid; e < (ncol > 0 ? Rw * Wc : 0); e += blockDim.x) {
-            const int r = e / Wc, c = e - r * Wc;
-            const C cv = bufX[r * Wp + c];
-            C& pv = bufP[r * Wp + c];
-            pv = iter ? make_float2(fma(beta, pv.x, cv.x), fma(beta, pv.y, cv.y)) : cv;
-          }
+          // two columns per thread and step (rows are 16-byte aligned: Wp and A0 even); rows
+          // split over blockDim / 64 thread groups
+          for (int r = tid >> 6; r < (ncol > 0 ? Rw : 0); r += blockDim.x >> 6)
+            for (int c = 2 * (tid & 63); c < Wc; c += 128) {
+              const float4 cv = *reinterpret_cast<const float4*>(bufX + r * Wp + c);
+              float4* pp = reinterpret_cast<float4*>(bufP + r * Wp + c);
+              if (iter) {
+                const float4 pv = *pp;
+                *pp = make_float4(fma(beta, pv.x, cv.x), fma(beta, pv.y, cv.y), fma(beta, pv.z, cv.z),
+                                  fma(beta, pv.w, cv.w));
+              } else {
+                *pp = cv;
+              }
+            }
           __syncthreads();
           for (int s = tid; s < nslots; s += blockDim.x) {
             const int g = s >> gshift, kk = s - (g << gshift);
@@ -986,24 +991,24 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       const C* xs = (A.mode & kLoadX) ? reinterpret_cast<const C*>(io.x_in) : G.X;
       const R inv_lam = (R)1 / (R)io.lam;
       const int bps = io.bps;
-      for (int q = gtid; q < MN; q += nthr) {
-        float2 l01, l23, l45;
-        const int hard = qam_llr_regs<R>(xs[q], bps, (R)io.pam_d, inv_lam, l01, l23, l45);
-        G.lab[q] = (uint8_t)(__brev((unsigned)hard) >> (32 - bps));
-        if (io.llr) {
-          float2* ol = reinterpret_cast<float2*>(io.llr + (size_t)q * bps);
-          ol[0] = l01;
-          if (bps > 2) ol[1] = l23;
-          if (bps > 4) ol[2] = l45;
-        }
-      }
-      if (io.bits) {
-        if (!grid_sync(G.bar, gen)) return fail(io);
-        for (int g = gtid; g < MN / 8; g += nthr) {
-          const unsigned long long l8 = __ldcg(reinterpret_cast<const unsigned long long*>(G.lab) + g);
-          unsigned long long w = 0;
+      // eight consecutive symbols per thread: their LLRs, and their hard bits packed into bps
+      // bytes right away (bit j of a symbol's label = its bit j)
+      for (int g = gtid; g < MN / 8; g += nthr) {
+        unsigned long long w = 0;
 #pragma unroll
-          for (int s8 = 0; s8 < 8; ++s8) w |= ((l8 >> (8 * s8)) & 0xffull) << (bps * s8);
+        for (int s8 = 0; s8 < 8; ++s8) {
+          const int q = 8 * g + s8;
+          float2 l01, l23, l45;
+          const int hard = qam_llr_regs<R>(xs[q], bps, (R)io.pam_d, inv_lam, l01, l23, l45);
+          w |= (unsigned long long)(__brev((unsigned)hard) >> (32 - bps)) << (bps * s8);
+          if (io.llr) {
+            float2* ol = reinterpret_cast<float2*>(io.llr + (size_t)q * bps);
+            ol[0] = l01;
+            if (bps > 2) ol[1] = l23;
+            if (bps > 4) ol[2] = l45;
+          }
+        }
+        if (io.bits) {
           uint8_t* o = io.bits + (size_t)g * bps;
           for (int h = 0; h < bps; ++h) o[h] = (uint8_t)(w >> (8 * h));
         }
