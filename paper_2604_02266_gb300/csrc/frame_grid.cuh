@@ -534,8 +534,12 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
 
     // ------------------------------------------------ path list
     int P = 0;
+    // the data frame's Zak transform goes with the pilot's when both run (no barrier of its own;
+    // the read-off's barriers publish it): it writes the extension of y directly
+    const bool y_early = (A.mode & kEstimate) && (A.mode & kCG) && !A.y_is_dd;
     if (A.mode & kEstimate) {
       grid_dzt<E>(io.y_pilot, A.in_dtype, G.Y, nullptr, A, tile, wn);
+      if (y_early) grid_dzt<E>(io.y_data, A.in_dtype, nullptr, G.extT, A, tile, wn);
       if (!grid_sync(G.bar, gen)) return fail(io);
       // read-off: thread g owns q in [g EQ, g EQ + EQ) (Eq. heff_hadamard over the pilot grid)
       const R scale = (R)(1.0 / io.a_pilot);
@@ -796,7 +800,9 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         fail(io);
       };
 
-      if (!A.y_is_dd) {
+      if (y_early) {
+        // done with the pilot's
+      } else if (!A.y_is_dd) {
         // the data frame's Zak transform writes the extension of y directly
         grid_dzt<E>(io.y_data, A.in_dtype, nullptr, G.extT, A, tile, wn);
       } else {
@@ -810,7 +816,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
           grid_ext_store<E>(G.extT, A, k, j0, v, k < hw || k >= M - hw, wn);
         }
       }
-      if (!grid_sync(G.bar, gen)) return fail(io);
+      if (!y_early && !grid_sync(G.bar, gen)) return fail(io);
 
       // b = H^H y;  c = b, x = 0, c_n = ||c||^2  (p = c is formed by the first iteration)
       if (win && !grid_window_load(bufX, &maps.t, M, A0, box_bytes, ncol > 0, &S->mbar, mph)) return wfail(io);
