@@ -75,6 +75,7 @@ __host__ __device__ inline MrcSmem mrc_smem_layout(int MN, int p_max) {
 }
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGainRegs = 16;  // branch gains (times elements per lane) kept in registers per step
 constexpr uint8_t kNoDecision = 0xff;  // x_hat = 0 before the first decision
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
@@ -145,17 +146,17 @@ __device__ __forceinline__ int nearest_level(float x, int m, float d) {
 }
 
 // Gain of branch b (paths [s, e) of the sorted list) for source delay k at time index n:
-// sum_p h_p W[dl_p (k + n M)] = sum_p (h_p W[dl_p k]) exp(j2pi dl_p n / N).  The first factor's
-// table index is the same in every lane (one broadcast load); the second comes from the N-entry
-// shared table wN.  (Reading W[dl_p (k + n M)] directly puts the lanes dl_p M entries apart in
-// the MN-entry table: 32 cache lines per load.)
-__device__ __forceinline__ float2 branch_gain(const MrcArgs& A, const float2* wN, const float2* hs, const int* dls,
-                                              int s, int e, int k, int n) {
-  const int MN = A.M * A.N, N = A.N;
+// sum_p h_p W[dl_p (k + n M)] = sum_p (h_p W[dl_p k]) exp(j2pi dl_p n / N).  The first factor,
+// the same in every lane, is formed once per delay bin for all paths (hk, shared memory); the
+// second comes from the N-entry shared table wN.  (Reading W[dl_p (k + n M)] directly puts the
+// lanes dl_p M entries apart in the MN-entry table: 32 cache lines per load.)
+__device__ __forceinline__ float2 branch_gain(const MrcArgs& A, const float2* wN, const float2* hk_all, const int* dls,
+                                              int s, int e, int n) {
+  const int N = A.N;
   float2 G = make_float2(0.f, 0.f);
   for (int p = s; p < e; ++p) {
     const int dl = dls[p];
-    const float2 hk = cmul(hs[p], __ldg(A.W + ((dl * k) & (MN - 1))));
+    const float2 hk = hk_all[p];
     const float2 w = wN[(dl * n) & (N - 1)];
     G.x = fmaf(hk.x, w.x, fmaf(-hk.y, w.y, G.x));
     G.y = fmaf(hk.x, w.y, fmaf(hk.y, w.x, G.y));
@@ -255,6 +256,9 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
       nb += __popc(hm);
     }
     if (lane == 0) brs[nb] = P;
+    // h_p W[dl_p k] of every path for the delay bin being processed, in the space of the sort's
+    // keys and ranks (dks and tmp, free once the branches are cut: together >= 8 p_max bytes)
+    float2* hk = reinterpret_cast<float2*>(dks);
 
     // ---- received DT grid into the residual (dy = y - H 0)
     if (!A.y_is_dd) {
@@ -299,19 +303,33 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
           D[e] = 0.f;
         }
         if (it > 0) warp_idft<EPL>(old, A, wN, lane);  // current estimate of vector k, DT
-        for (int b = 0; b < nb; ++b) {
+        for (int p = lane; p < P; p += 32) hk[p] = cmul(hs[p], __ldg(A.W + ((dls[p] * k) & (MN - 1))));
+        __syncwarp();
+        // combining over the branches; the first kGainRegs / EPL branches' gains stay in
+        // registers for the feedback below (the rest are formed again there)
+        auto combine = [&](int b, float2 (&Gb)[EPL]) {
           const int dd = brd[b], kt = (k + dd) & (M - 1), fsh = (k + dd) >> A.logM;
 #pragma unroll
           for (int e = 0; e < EPL; ++e) {
             const int n = lane + 32 * e;
             if (n < N) {
-              const float2 G = branch_gain(A, wN, hs, dls, brs[b], brs[b + 1], k, n);
+              const float2 G = branch_gain(A, wN, hk, dls, brs[b], brs[b + 1], n);
+              Gb[e] = G;
               const float2 r = dy[kt * N + ((n + fsh) & (N - 1))];
               g[e].x = fmaf(G.x, r.x, fmaf(G.y, r.y, g[e].x));  // conj(G) r
               g[e].y = fmaf(G.x, r.y, fmaf(-G.y, r.x, g[e].y));
               D[e] = fmaf(G.x, G.x, fmaf(G.y, G.y, D[e]));
             }
           }
+        };
+        constexpr int kB = kGainRegs / EPL;
+        float2 Gc[kB][EPL];
+#pragma unroll
+        for (int b = 0; b < kB; ++b)
+          if (b < nb) combine(b, Gc[b]);
+        for (int b = kB; b < nb; ++b) {
+          float2 Gt[EPL];
+          combine(b, Gt);
         }
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
@@ -344,18 +362,22 @@ __global__ void __launch_bounds__(384) mrc_kernel(const __grid_constant__ MrcArg
 #pragma unroll
         for (int e = 0; e < EPL; ++e) delta[e] = csub(s[e], old[e]);
         __syncwarp();  // every lane's reads of dy for this step are done
-        for (int b = 0; b < nb; ++b) {
+        auto feed_back = [&](int b, const float2* Gb) {
           const int dd = brd[b], kt = (k + dd) & (M - 1), fsh = (k + dd) >> A.logM;
 #pragma unroll
           for (int e = 0; e < EPL; ++e) {
             const int n = lane + 32 * e;
             if (n < N) {
-              const float2 G = branch_gain(A, wN, hs, dls, brs[b], brs[b + 1], k, n);
+              const float2 G = Gb ? Gb[e] : branch_gain(A, wN, hk, dls, brs[b], brs[b + 1], n);
               float2* r = dy + kt * N + ((n + fsh) & (N - 1));
               *r = csub(*r, cmul(G, delta[e]));
             }
           }
-        }
+        };
+#pragma unroll
+        for (int b = 0; b < kB; ++b)
+          if (b < nb) feed_back(b, Gc[b]);
+        for (int b = kB; b < nb; ++b) feed_back(b, nullptr);
 #pragma unroll
         for (int e = 0; e < EPL; ++e)
           if (lane + 32 * e < N) lab[k * N + lane + 32 * e] = nl[e];
