@@ -41,6 +41,7 @@ struct GridCand {
   uint32_t key;
   float2 h;
 };
+static_assert(sizeof(GridCand) == 16, "a candidate is read as one 16-byte vector");
 
 // Delay columns per CTA in the CG stages (the last CTAs may hold fewer, or none).
 // Even, so that the CTAs' column ranges start on 16-byte boundaries of the extensions' rows.
@@ -50,6 +51,18 @@ struct GridBarrier {
   unsigned long long count;  // CTA arrivals since the launch began (zeroed before each launch)
   int err;                   // a wait gave up: every CTA leaves at its next barrier
   int pad;
+  int cand[2];               // read-off candidates appended, frames alternating (zeroed likewise)
+  int pad2[2];
+};
+
+// The pilot read-off done inside the pilot's Zak transform: each output's h_eff (Eq.
+// heff_hadamard) against the threshold, passing taps appended to cand (unordered) through the
+// counter; beyond cap they are only counted.
+struct GridReadoff {
+  float scale, th2;
+  GridCand* cand;
+  int* counter;
+  int cap;
 };
 
 // Global scratch of one grid receiver (one frame at a time).
@@ -254,8 +267,8 @@ __device__ __forceinline__ bool grid_window_load(float2* dst, const CUtensorMap*
 // item), either may be NULL.  `tile` holds N kGridDftCols values, `wn` N twiddles.
 template <int E>
 __device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, float2* ext, const FrameArgs& A,
-                                         float2* tile, float2* wn) {
-  const int M = A.M, N = A.N, logM = A.logM, logN = A.logN;
+                                         float2* tile, float2* wn, const GridReadoff* ro = nullptr) {
+  const int M = A.M, N = A.N, logM = A.logM, logN = A.logN, MN = M * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) wn[i] = conjf2(tw<float>(A, (size_t)i << logM));
   const float s = (float)A.inv_sqrtN;
   const int ntiles = M / kGridDftCols;
@@ -285,6 +298,27 @@ __device__ __forceinline__ void grid_dzt(const char* src, int dtype, float2* Y, 
       const float2 v = cscale(tile[bitrev(l, logN) * kGridDftCols + kk], s);
       if (Y) Y[(size_t)l * M + k0 + kk] = v;
       if (ext) ext_store_rm<E>(ext, A, k0 + kk, l, v, wn);
+      if (ro) {  // every lane of a warp runs the same number of elements
+        const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+        const float2 h = cscale(cmul(v, tw<float>(A, (size_t)((-A.K0 * dl) & (MN - 1)))), ro->scale);
+        const float m2 = h.x * h.x + h.y * h.y;
+        const bool pass = m2 > ro->th2;
+        const unsigned mask = __ballot_sync(0xffffffffu, pass);
+        if (mask) {
+          const int lane = threadIdx.x & 31, first = __ffs(mask) - 1;
+          int base = 0;
+          if (lane == first) base = atomicAdd(ro->counter, __popc(mask));
+          base = __shfl_sync(0xffffffffu, base, first);
+          const int pos = base + __popc(mask & ((1u << lane) - 1u));
+          if (pass && pos < ro->cap) {
+            GridCand c;
+            c.q = l * M + k0 + kk;
+            c.key = __float_as_uint(m2);
+            c.h = h;
+            ro->cand[pos] = c;
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -337,6 +371,20 @@ __device__ __forceinline__ void grid_prefix(const int* counts, SharedHdr* S) {
   __syncthreads();
 }
 
+// hist[bin] += 1 for every lane with `active`, one atomic per distinct counter of the warp (the
+// read-off's magnitudes crowd into a few bins, where one atomic per tap serialises).  Every
+// thread of the block calls (a warp may hold threads of two rows of a 2D block, each row with
+// its own histogram: lanes group by the counter's address).
+__device__ __forceinline__ void warp_hist_add(int* hist, unsigned bin, bool active) {
+  const unsigned lin = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+  const unsigned base = lin & ~31u, lanes = nthr - base < 32u ? nthr - base : 32u;
+  const unsigned mask = lanes == 32u ? 0xffffffffu : (1u << lanes) - 1u;
+  const unsigned lane = lin & 31u;
+  const unsigned key = active ? (unsigned)reinterpret_cast<uintptr_t>(hist + bin) : 0xffffffffu;
+  const unsigned peers = __match_any_sync(mask, key);
+  if (active && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&hist[bin], __popc(peers));
+}
+
 // The path list from the n <= kGridCandMax passing taps in cand (ascending q): all of them, or
 // when n > K the exact K largest |h|^2, ties to the lower q (the same list the grid-wide
 // selection gives), into out[0, P) in ascending q (Eq. heff_thres with the p_max cap).  Every
@@ -374,7 +422,7 @@ __device__ __forceinline__ int grid_select(const GridCand* cand, int n, const Fr
       const int w = hb < 7 ? hb : 7, sh = hb - w;
 #pragma unroll
       for (int j = 0; j < CPT; ++j)
-        if (((have >> j) & 1u) && ((key[j] ^ prefix) & fixed) == 0) atomicAdd(&S->hist[(key[j] >> sh) & 127u], 1);
+        warp_hist_add(S->hist, (key[j] >> sh) & 127u, ((have >> j) & 1u) && ((key[j] ^ prefix) & fixed) == 0);
       __syncthreads();
       if (tid < 32) {  // the bin holding the kleft-th largest, from the top (lane: 4 bins)
         int c[4], sum = 0;
@@ -463,6 +511,152 @@ __device__ __forceinline__ int grid_select(const GridCand* cand, int n, const Fr
   return total;
 }
 
+// As grid_select, for candidates in any order (appended by the pilot's transform): the same
+// radix select gives the K-th largest key; the ties to it that are kept are those of the lowest
+// q (each tie ranked by q among all ties, through tq: room for tie_cap indices), and the kept
+// taps are placed in ascending q by ranking each against the others (kq, kh: room for K).
+// Returns P, or -1 (uniformly) when more than tie_cap taps tie with the K-th largest -- the
+// caller then takes the ordered route.
+template <int CPT>
+__device__ __forceinline__ int grid_select_q(const GridCand* cand, int n, const FrameArgs& A, PathRecT<float>* out,
+                                             SharedHdr* S, const PathIO* gout, int* tq, int tie_cap, int* kq,
+                                             float2* kh, int* whist, int nh, int& trunc) {
+  const int tid = threadIdx.x, K = A.p_max;
+  const int M = A.M, N = A.N;
+  const int nw = nh, warp = (tid >> 5) % nh;  // nh histograms, warps sharing them round-robin
+  // thread t holds candidates t + j blockDim (whole records, coalesced)
+  uint32_t key[CPT];
+  int qv[CPT];
+  uint32_t have = 0;
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int i = tid + j * kGridThreads;
+    key[j] = 0;
+    qv[j] = 0;
+    if (i < n) {
+      const int2 qk = __ldcg(reinterpret_cast<const int2*>(cand + i));  // q and key
+      qv[j] = qk.x;
+      key[j] = (uint32_t)qk.y;
+      have |= 1u << j;
+    }
+  }
+  uint32_t keep = have;
+  int total = n;
+  trunc = 0;
+  if (n > K) {
+    trunc = 1;
+    uint32_t prefix = 0, fixed = 0;
+    int kleft = K;
+    const int lane = tid & 31;
+    // 128-bin histograms, one per warp when nh covers the warps, so their increments do not contend
+    for (int b = tid; b < 128 * nw; b += blockDim.x) whist[b] = 0;
+    __syncthreads();
+    for (int hb = 31; hb > 0; hb -= 7) {
+      const int w = hb < 7 ? hb : 7, sh = hb - w;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j)
+        warp_hist_add(whist + 128 * warp, (key[j] >> sh) & 127u,
+                      ((have >> j) & 1u) && ((key[j] ^ prefix) & fixed) == 0);
+      __syncthreads();
+      if (tid < 32) {
+        int c[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          c[j] = 0;
+          for (int u = 0; u < nw; ++u) {
+            c[j] += whist[128 * u + 4 * lane + j];
+            whist[128 * u + 4 * lane + j] = 0;
+          }
+          sum += c[j];
+        }
+        int suf = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_down_sync(0xffffffffu, suf, o);
+          if (lane + o < 32) suf += v;
+        }
+        int acc = suf - sum;
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+          if (acc < kleft && acc + c[j] >= kleft) {
+            S->isc[2] = 4 * lane + j;
+            S->isc[3] = kleft - acc;
+          }
+          acc += c[j];
+        }
+      }
+      __syncthreads();
+      prefix |= (uint32_t)S->isc[2] << sh;
+      kleft = S->isc[3];
+      fixed |= ((1u << w) - 1u) << sh;
+      __syncthreads();
+    }
+    const uint32_t vK = prefix;
+    const int need = kleft;
+    uint32_t gt = 0, eq = 0;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j)
+      if ((have >> j) & 1u) {
+        if (key[j] > vK) gt |= 1u << j;
+        else if (key[j] == vK) eq |= 1u << j;
+      }
+    // the ties' indices, compacted, then each tie kept when fewer than `need` ties have a lower q
+    int nties;
+    int tpos = block_exclusive_scan(__popc(eq), S->scan, nties);
+    if (nties > tie_cap) return -1;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j)
+      if ((eq >> j) & 1u) tq[tpos++] = qv[j];
+    __syncthreads();
+    keep = gt;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j)
+      if ((eq >> j) & 1u) {
+        int r = 0;
+        for (int t = 0; t < nties; ++t) r += tq[t] < qv[j];
+        if (r < need) keep |= 1u << j;
+      }
+    total = K;
+  }
+  // the kept taps, compacted in any order, then each placed at its rank in q
+  int nk;
+  int kpos = block_exclusive_scan(__popc(keep), S->scan, nk);
+#pragma unroll
+  for (int j = 0; j < CPT; ++j)
+    if ((keep >> j) & 1u) {
+      kq[kpos] = qv[j];
+      kh[kpos] = __ldcg(&cand[tid + j * kGridThreads].h);
+      ++kpos;
+    }
+  __syncthreads();
+  for (int i = tid; i < nk; i += blockDim.x) {
+    const int q = kq[i];
+    int r = 0;
+    for (int t = 0; t < nk; ++t) r += kq[t] < q;
+    const int k = q & (M - 1), l = q >> A.logM;
+    const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
+    const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+    PathRecT<float> rec;  // hf unused: the grid CG forms its factors from a table and phases
+    rec.h = kh[i];
+    rec.dk = dk;
+    rec.dl = dl;
+    rec.hf = make_float2(0.f, 0.f);
+    rec.pad0 = rec.pad1 = 0;
+    out[r] = rec;
+    if (gout) {
+      gout->dk[r] = (int16_t)dk;
+      gout->dl[r] = (int16_t)dl;
+      store_complex(gout->h, (size_t)r, gout->tap_dtype, rec.h);
+    }
+  }
+  if (gout && tid == 0) {
+    gout->count[0] = total;
+    if (gout->status) gout->status[0] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
+  }
+  __syncthreads();
+  return total;
+}
+
 // EQ: pilot-grid entries per thread in the read-off; E: rows per CG work item (column k, rows
 // j0 .. j0 + E - 1); MINB: CTAs per SM the launch bounds are set for.
 template <int EQ, int E, int MINB>
@@ -538,180 +732,204 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
     // the read-off's barriers publish it): it writes the extension of y directly
     const bool y_early = (A.mode & kEstimate) && (A.mode & kCG) && !A.y_is_dd;
     if (A.mode & kEstimate) {
-      grid_dzt<E>(io.y_pilot, A.in_dtype, G.Y, nullptr, A, tile, wn);
-      if (y_early) grid_dzt<E>(io.y_data, A.in_dtype, nullptr, G.extT, A, tile, wn);
-      if (!grid_sync(G.bar, gen)) return fail(io);
-      // read-off: thread g owns q in [g EQ, g EQ + EQ) (Eq. heff_hadamard over the pilot grid)
+      // The pilot's transform reads the taps off as it writes them (Eq. heff_hadamard against the
+      // threshold) and appends those that pass as candidates; after the one barrier every CTA
+      // selects the list from them in shared memory.  When more taps pass than the candidates
+      // hold, or too many tie with the p_max-th largest, the ordered route below runs from the
+      // transformed grid Y.
       const R scale = (R)(1.0 / io.a_pilot);
       const R th2 = (R)io.theta * (R)io.theta;
-      C hv[EQ];
-      uint32_t mb[EQ];
-      uint32_t pass = 0;
-#pragma unroll
-      for (int i = 0; i < EQ; ++i) {
-        const int q = q_beg + tid * EQ + i;
-        hv[i] = make_float2(0.f, 0.f);
-        mb[i] = 0;
-        if (q < q_end) {
-          const int l = q >> logM;
-          const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
-          const C h = cscale(cmul(G.Y[q], tw<R>(A, (size_t)((-A.K0 * dl) & (MN - 1)))), scale);
-          const R m2 = h.x * h.x + h.y * h.y;
-          hv[i] = h;
-          mb[i] = __float_as_uint(m2);
-          if (m2 > th2) pass |= 1u << i;
-        }
-      }
-      int blk_total;
-      const int in_blk = block_exclusive_scan(__popc(pass), S->scan, blk_total);
-      if (tid == 0) G.icnt[blockIdx.x] = blk_total;
+      const GridReadoff ro{scale, th2, G.cand, &G.bar->cand[f & 1], kGridCandMax};
+      grid_dzt<E>(io.y_pilot, A.in_dtype, G.Y, nullptr, A, tile, wn, &ro);
+      if (y_early) grid_dzt<E>(io.y_data, A.in_dtype, nullptr, G.extT, A, tile, wn);
       if (!grid_sync(G.bar, gen)) return fail(io);
-      grid_prefix(G.icnt, S);
-      int total = S->isc[3];
-      int base = S->isc[2] + in_blk;
-      if (total <= kGridCandMax) {
-        // The passing taps as candidates at their places in ascending q; then every CTA selects
-        // the list from them alike in shared memory: one grid barrier instead of the grid-wide
-        // radix select's and the list's.
-        int pos = base;
-#pragma unroll
-        for (int i = 0; i < EQ; ++i)
-          if ((pass >> i) & 1u) {
-            GridCand c;
-            c.q = q_beg + tid * EQ + i;
-            c.key = mb[i];
-            c.h = hv[i];
-            G.cand[pos++] = c;
-          }
-        if (!grid_sync(G.bar, gen)) return fail(io);
+      if (blockIdx.x == 0 && tid == 0) G.bar->cand[(f + 1) & 1] = 0;  // the next frame's count
+      const int ncand = *reinterpret_cast<volatile int*>(&G.bar->cand[f & 1]);
+      P = -1;
+      if (ncand <= kGridCandMax) {
         const PathIO* gout = (write_paths && io.paths.count && blockIdx.x == 0) ? &io.paths : nullptr;
         int trunc = 0;
-        P = grid_select<kGridCandMax / kGridThreads>(G.cand, total, A, paths, S, gout, trunc);
-        if (trunc) st |= kStTrunc;
-      } else {
-        uint32_t keep = pass;
-        int trunc = 0;
-        if (total > A.p_max) {
-          // the K-th largest |h|^2 among the passing taps, exactly: radix select on the bit
-          // patterns, 7 bits per pass, histograms over the whole grid
-          trunc = 1;
-          const int K = A.p_max;
-          uint32_t prefix = 0, fixed = 0;
-          int kleft = K;
-          int hp = 0;
-          for (int hb = 31; hb > 0; hb -= 7, ++hp) {
-            const int w = hb < 7 ? hb : 7, sh = hb - w;
-            int* H = G.hist + hp * 128;
+        // scratch: the transform's tile for the ties' indices, the sort buffer for the kept taps
+        float2* kh = reinterpret_cast<float2*>(sort_tmp);
+        int* kq = reinterpret_cast<int*>(kh + A.p_max);
+        // per-warp histograms in the (still unused) p window when it has room, else the header's
+        const bool wh = (size_t)G.win_cols * (N + E + 3) * sizeof(C) >= (size_t)kGridThreads / 32 * 128 * sizeof(int);
+        P = grid_select_q<kGridCandMax / kGridThreads>(G.cand, ncand, A, paths, S, gout,
+                                                        reinterpret_cast<int*>(tile), 64 * N, kq, kh,
+                                                        wh ? reinterpret_cast<int*>(bufP) : S->hist,
+                                                        wh ? kGridThreads / 32 : 1, trunc);
+        if (P >= 0 && trunc) st |= kStTrunc;
+      }
+      if (P < 0) {
+        C hv[EQ];
+        uint32_t mb[EQ];
+        uint32_t pass = 0;
   #pragma unroll
-            for (int i = 0; i < EQ; ++i)
-              if (((pass >> i) & 1u) && ((mb[i] ^ prefix) & fixed) == 0) atomicAdd(&H[(mb[i] >> sh) & 127u], 1);
-            if (!grid_sync(G.bar, gen)) return fail(io);
-            if (tid < 32) {  // the bin holding the kleft-th largest, from the top (lane: 4 bins)
-              const int lane = tid;
-              int c[4], sum = 0;
-  #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                c[j] = __ldcg(H + 4 * lane + j);
-                sum += c[j];
-              }
-              int suf = sum;  // inclusive suffix sum over lanes >= lane
-  #pragma unroll
-              for (int o = 1; o < 32; o <<= 1) {
-                const int n = __shfl_down_sync(0xffffffffu, suf, o);
-                if (lane + o < 32) suf += n;
-              }
-              int acc = suf - sum;  // taps in the bins above this lane's four
-  #pragma unroll
-              for (int j = 3; j >= 0; --j) {
-                if (acc < kleft && acc + c[j] >= kleft) {
-                  S->isc[2] = 4 * lane + j;
-                  S->isc[3] = kleft - acc;
-                }
-                acc += c[j];
-              }
-            }
-            __syncthreads();
-            prefix |= (uint32_t)S->isc[2] << sh;
-            kleft = S->isc[3];
-            fixed |= ((1u << w) - 1u) << sh;
-            __syncthreads();
+        for (int i = 0; i < EQ; ++i) {
+          const int q = q_beg + tid * EQ + i;
+          hv[i] = make_float2(0.f, 0.f);
+          mb[i] = 0;
+          if (q < q_end) {
+            const int l = q >> logM;
+            const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+            const C h = cscale(cmul(G.Y[q], tw<R>(A, (size_t)((-A.K0 * dl) & (MN - 1)))), scale);
+            const R m2 = h.x * h.x + h.y * h.y;
+            hv[i] = h;
+            mb[i] = __float_as_uint(m2);
+            if (m2 > th2) pass |= 1u << i;
           }
-          const uint32_t vK = prefix;  // the K-th largest value; `kleft` ties to it are kept
-          const int need = kleft;
-          uint32_t gt = 0, eq = 0;
+        }
+        int blk_total;
+        const int in_blk = block_exclusive_scan(__popc(pass), S->scan, blk_total);
+        if (tid == 0) G.icnt[blockIdx.x] = blk_total;
+        if (!grid_sync(G.bar, gen)) return fail(io);
+        grid_prefix(G.icnt, S);
+        int total = S->isc[3];
+        int base = S->isc[2] + in_blk;
+        if (total <= kGridCandMax) {
+          // The passing taps as candidates at their places in ascending q; then every CTA selects
+          // the list from them alike in shared memory: one grid barrier instead of the grid-wide
+          // radix select's and the list's.
+          int pos = base;
   #pragma unroll
           for (int i = 0; i < EQ; ++i)
             if ((pass >> i) & 1u) {
-              if (mb[i] > vK) gt |= 1u << i;
-              else if (mb[i] == vK) eq |= 1u << i;
+              GridCand c;
+              c.q = q_beg + tid * EQ + i;
+              c.key = mb[i];
+              c.h = hv[i];
+              G.cand[pos++] = c;
             }
-          int tg, te;
-          const int gt_in = block_exclusive_scan(__popc(gt), S->scan, tg);
-          const int eq_in = block_exclusive_scan(__popc(eq), S->scan, te);
-          if (tid == 0) {
-            G.icnt[blockIdx.x] = tg;
-            G.icnt[gridDim.x + blockIdx.x] = te;
+          if (!grid_sync(G.bar, gen)) return fail(io);
+          const PathIO* gout = (write_paths && io.paths.count && blockIdx.x == 0) ? &io.paths : nullptr;
+          int trunc = 0;
+          P = grid_select<kGridCandMax / kGridThreads>(G.cand, total, A, paths, S, gout, trunc);
+          if (trunc) st |= kStTrunc;
+        } else {
+          uint32_t keep = pass;
+          int trunc = 0;
+          if (total > A.p_max) {
+            // the K-th largest |h|^2 among the passing taps, exactly: radix select on the bit
+            // patterns, 7 bits per pass, histograms over the whole grid
+            trunc = 1;
+            const int K = A.p_max;
+            uint32_t prefix = 0, fixed = 0;
+            int kleft = K;
+            int hp = 0;
+            for (int hb = 31; hb > 0; hb -= 7, ++hp) {
+              const int w = hb < 7 ? hb : 7, sh = hb - w;
+              int* H = G.hist + hp * 128;
+#pragma unroll
+              for (int i = 0; i < EQ; ++i)
+                warp_hist_add(H, (mb[i] >> sh) & 127u, ((pass >> i) & 1u) && ((mb[i] ^ prefix) & fixed) == 0);
+              if (!grid_sync(G.bar, gen)) return fail(io);
+              if (tid < 32) {  // the bin holding the kleft-th largest, from the top (lane: 4 bins)
+                const int lane = tid;
+                int c[4], sum = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  c[j] = __ldcg(H + 4 * lane + j);
+                  sum += c[j];
+                }
+                int suf = sum;  // inclusive suffix sum over lanes >= lane
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                  const int n = __shfl_down_sync(0xffffffffu, suf, o);
+                  if (lane + o < 32) suf += n;
+                }
+                int acc = suf - sum;  // taps in the bins above this lane's four
+#pragma unroll
+                for (int j = 3; j >= 0; --j) {
+                  if (acc < kleft && acc + c[j] >= kleft) {
+                    S->isc[2] = 4 * lane + j;
+                    S->isc[3] = kleft - acc;
+                  }
+                  acc += c[j];
+                }
+              }
+              __syncthreads();
+              prefix |= (uint32_t)S->isc[2] << sh;
+              kleft = S->isc[3];
+              fixed |= ((1u << w) - 1u) << sh;
+              __syncthreads();
+            }
+            const uint32_t vK = prefix;  // the K-th largest value; `kleft` ties to it are kept
+            const int need = kleft;
+            uint32_t gt = 0, eq = 0;
+#pragma unroll
+            for (int i = 0; i < EQ; ++i)
+              if ((pass >> i) & 1u) {
+                if (mb[i] > vK) gt |= 1u << i;
+                else if (mb[i] == vK) eq |= 1u << i;
+              }
+            int tg, te;
+            const int gt_in = block_exclusive_scan(__popc(gt), S->scan, tg);
+            const int eq_in = block_exclusive_scan(__popc(eq), S->scan, te);
+            if (tid == 0) {
+              G.icnt[blockIdx.x] = tg;
+              G.icnt[gridDim.x + blockIdx.x] = te;
+            }
+            if (!grid_sync(G.bar, gen)) return fail(io);
+            grid_prefix(G.icnt, S);
+            const int gt_pre = S->isc[2];
+            __syncthreads();
+            grid_prefix(G.icnt + gridDim.x, S);
+            int eq_before = S->isc[2] + eq_in;
+            base = gt_pre + gt_in + min(eq_before, need);
+            keep = 0;
+#pragma unroll
+            for (int i = 0; i < EQ; ++i) {
+              if ((gt >> i) & 1u) {
+                keep |= 1u << i;
+              } else if ((eq >> i) & 1u) {
+                if (eq_before < need) keep |= 1u << i;
+                ++eq_before;
+              }
+            }
+            total = K;
+          }
+          if (trunc) st |= kStTrunc;
+          const PathIO* gout = (write_paths && io.paths.count) ? &io.paths : nullptr;
+          int pos = base;
+#pragma unroll
+          for (int i = 0; i < EQ; ++i) {
+            if ((keep >> i) & 1u) {
+              const int q = q_beg + tid * EQ + i;
+              const int k = q & (M - 1), l = q >> logM;
+              const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
+              const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+              PathRec rec;
+              rec.h = hv[i];
+              rec.dk = dk;
+              rec.dl = dl;
+              rec.hf = cmul(hv[i], tw<R>(A, (size_t)((-dl * dk) & (MN - 1))));
+              rec.pad0 = rec.pad1 = 0;
+              G.list[pos] = rec;
+              if (gout) {
+                gout->dk[pos] = (int16_t)dk;
+                gout->dl[pos] = (int16_t)dl;
+                store_complex(gout->h, (size_t)pos, gout->tap_dtype, hv[i]);
+              }
+              ++pos;
+            }
+          }
+          if (gout && blockIdx.x == 0 && tid == 0) {
+            gout->count[0] = total;
+            if (gout->status) gout->status[0] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
           }
           if (!grid_sync(G.bar, gen)) return fail(io);
-          grid_prefix(G.icnt, S);
-          const int gt_pre = S->isc[2];
-          __syncthreads();
-          grid_prefix(G.icnt + gridDim.x, S);
-          int eq_before = S->isc[2] + eq_in;
-          base = gt_pre + gt_in + min(eq_before, need);
-          keep = 0;
-  #pragma unroll
-          for (int i = 0; i < EQ; ++i) {
-            if ((gt >> i) & 1u) {
-              keep |= 1u << i;
-            } else if ((eq >> i) & 1u) {
-              if (eq_before < need) keep |= 1u << i;
-              ++eq_before;
-            }
-          }
-          total = K;
-        }
-        if (trunc) st |= kStTrunc;
-        const PathIO* gout = (write_paths && io.paths.count) ? &io.paths : nullptr;
-        int pos = base;
-  #pragma unroll
-        for (int i = 0; i < EQ; ++i) {
-          if ((keep >> i) & 1u) {
-            const int q = q_beg + tid * EQ + i;
-            const int k = q & (M - 1), l = q >> logM;
-            const int dk = ((k - A.K0 + (M >> 1)) & (M - 1)) - (M >> 1);
-            const int dl = ((l - A.L0 + (N >> 1)) & (N - 1)) - (N >> 1);
+          P = total;
+          for (int p = tid; p < P; p += blockDim.x) {
             PathRec rec;
-            rec.h = hv[i];
-            rec.dk = dk;
-            rec.dl = dl;
-            rec.hf = cmul(hv[i], tw<R>(A, (size_t)((-dl * dk) & (MN - 1))));
+            const float4* s4 = reinterpret_cast<const float4*>(G.list + p);
+            const float4 a = __ldcg(s4), b = __ldcg(s4 + 1);
+            rec.h = make_float2(a.x, a.y);
+            rec.hf = make_float2(a.z, a.w);
+            rec.dk = __float_as_int(b.x);
+            rec.dl = __float_as_int(b.y);
             rec.pad0 = rec.pad1 = 0;
-            G.list[pos] = rec;
-            if (gout) {
-              gout->dk[pos] = (int16_t)dk;
-              gout->dl[pos] = (int16_t)dl;
-              store_complex(gout->h, (size_t)pos, gout->tap_dtype, hv[i]);
-            }
-            ++pos;
+            paths[p] = rec;
           }
-        }
-        if (gout && blockIdx.x == 0 && tid == 0) {
-          gout->count[0] = total;
-          if (gout->status) gout->status[0] = trunc ? ZOTFS_ETRUNCATED : ZOTFS_OK;
-        }
-        if (!grid_sync(G.bar, gen)) return fail(io);
-        P = total;
-        for (int p = tid; p < P; p += blockDim.x) {
-          PathRec rec;
-          const float4* s4 = reinterpret_cast<const float4*>(G.list + p);
-          const float4 a = __ldcg(s4), b = __ldcg(s4 + 1);
-          rec.h = make_float2(a.x, a.y);
-          rec.hf = make_float2(a.z, a.w);
-          rec.dk = __float_as_int(b.x);
-          rec.dl = __float_as_int(b.y);
-          rec.pad0 = rec.pad1 = 0;
-          paths[p] = rec;
         }
       }
       if (tid == 0) cnt[0] = P;
