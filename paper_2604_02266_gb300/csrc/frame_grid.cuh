@@ -8,9 +8,11 @@
 // path's delay offset is within the launch's cap it gathers from shared-memory windows of the
 // extensions (its columns and the offsets' reach on either side) with a per-CTA table of the
 // paths' coefficients, and keeps p's window in shared memory across the iterations: three grid
-// barriers per iteration.  The read-off is the threshold / stable-compaction / exact
-// top-P_max of the shared-memory kernel, with its scans and radix-select histograms taken over
-// the grid.  Algorithm 1's scalars are FP64 sums of per-CTA partials taken in CTA order, so
+// barriers per iteration.  The read-off happens inside the pilot's Zak transform: the taps
+// that pass the threshold are appended as candidates and, after the transforms' barrier, every
+// CTA selects the exact top-P_max (ties to the lowest q, list in ascending q) in shared memory;
+// with too many candidates the threshold / stable-compaction / radix select runs over the
+// grid with scans and histograms across the CTAs.  Algorithm 1's scalars are FP64 sums of per-CTA partials taken in CTA order, so
 // every CTA derives the same alpha, beta and stopping decision.  SISO, separate pilot frames
 // (or loaded lists), FP32.
 #pragma once
@@ -74,7 +76,8 @@ struct GridScratch {
   float2* extC;                  // extension of the residual c
   float2 *X, *Vv;                // [MN] the CG vectors x and a
   PathRecT<float>* list;         // [p_max] the frame's path list (read-offs with many taps)
-  GridCand* cand;                // [kGridCandMax] the passing taps of a read-off, ascending q
+  GridCand* cand;                // [kGridCandMax] the passing taps of a read-off (appended by
+                                 // the pilot's transform; in ascending q on the ordered route)
   double* part;                  // [2 grid] per-CTA partial sums, two alternating sets
   int* icnt;                     // [2 grid] per-CTA counts of the read-off compaction
   int* hist;                     // [5 x 128] radix-select histograms (zeroed per frame)
