@@ -457,6 +457,10 @@ extern "C" zotfs_status zotfs_equalize_mrc(zotfs_plan plan, const void* y, int y
     set_error("zotfs_equalize_mrc: frame does not fit one SM's shared memory");
     return ZOTFS_EUNSUPPORTED;
   }
+  // no more warps (frames) per CTA than it takes to give every SM a CTA: a frame is one warp's
+  // sequential work, so frames crowded onto fewer SMs only wait for each other
+  const int spread = (int)std::max<long long>(1, ((long long)n_frames + plan->sm_count - 1) / plan->sm_count);
+  warps = std::min(warps, spread);
   A.warps = warps;
   const size_t smem = per_warp * warps + (size_t)plan->N * sizeof(float2);
   int* counter = plan->d_counters + (plan->counter_next++ & 63);
