@@ -75,7 +75,7 @@ __host__ __device__ inline MrcSmem mrc_smem_layout(int MN, int p_max) {
 }
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kGainRegs = 16;  // branch gains (times elements per lane) kept in registers per step
+constexpr int kGainRegs = 8;  // branch gains (times elements per lane) kept in registers per step
 constexpr uint8_t kNoDecision = 0xff;  // x_hat = 0 before the first decision
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
