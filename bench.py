@@ -1036,6 +1036,53 @@ def ber_claims(rows, factor=2.0, min_errors=20, sigmas=3.0):
     return out
 
 
+def impl_equalizers(args):
+    """SS-CGA and SS-MRC equalisation alone with given lists (each frame's list estimated from
+    its pilot frame first, untimed): --eq-frames frames of 64x32 16-QAM, 10 iterations / sweeps,
+    device time per call over 20 calls."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    import synth
+    from paper_2604_02266_gb300 import Plan, launch_count
+    M, N, F = 64, 32, args.eq_frames
+    b = synth.fractional_batch(F, seed=SEED + 5, M=M, N=N, Q=Q)
+    plan = Plan(M, N, 1, 1, Q)
+    yd, nv = torch.from_numpy(b["y_data_td"]).to(dev), torch.from_numpy(b["noise_var"]).to(dev)
+    paths = plan.estimate(torch.from_numpy(b["y_pilot_td"]).to(dev), torch.from_numpy(b["theta"]).to(dev), F)
+    x = torch.empty(F, 1, M * N, dtype=torch.complex64, device=dev)
+
+    def timed(fn, reps=20):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_cga = timed(lambda: plan.equalize(yd, paths, nv, ITERS, F, x_hat=x))
+    ms_mrc = timed(lambda: plan.equalize_mrc(yd, paths, ITERS, F, x_hat=x))
+    line = {"metric": "equaliser throughput with given lists (SS-MRC)", "value": F / ms_mrc * 1e3, "unit": "frames/s",
+            "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{F} frames 64x32 16-QAM, lists estimated from the pilot frames (mean P "
+                                   f"{float(paths.count.float().mean().item()):.1f}), {ITERS} iterations / sweeps, "
+                                   "device time per call over 20 calls"},
+            "ss_mrc_ms": ms_mrc, "ss_cga_ms": ms_cga, "ss_cga_frames_s": F / ms_cga * 1e3,
+            "gpu_launches": launch_count()}
+    print(json.dumps(line))
+    return 0
+
+
 def impl_ber(args):
     """BER against SNR on Veh-A frames (Sec. VI's BER study; Table vehAProf): the library's
     SS-CGA (Algorithm 1) and SS-MRC, 10 iterations each as in the paper (and SS-CGA at 20), and
@@ -1269,12 +1316,15 @@ def main():
     ap.add_argument("--oracle-frames", type=int, default=24, help="oracle sample per host core for cpu_baseline")
     ap.add_argument("--ref-frames", type=int, default=4, help="oracle frames per host core per step (--impl reference)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper", "packets", "iterations", "ber"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serve", "mixed", "mimo", "latency", "paper", "packets", "iterations", "ber",
+                             "equalizers"],
                     help="batch: the 64x32 16-QAM batch (default line); serve: the Poisson serving loop; "
                          "mixed: the uneven FP16/BF16 batch under CUDA graphs; mimo: 4x4 128x64 64-QAM frames; "
                          "latency: one frame per call; paper: one 16384x32 packet per call on the grid receiver; "
                          "packets: one pilot frame per D data frames (pilot reuse); "
-                         "iterations: the BER-driven CG iteration budget on Veh-A frames")
+                         "iterations: the BER-driven CG iteration budget on Veh-A frames; "
+                         "equalizers: SS-CGA and SS-MRC alone on given lists")
+    ap.add_argument("--eq-frames", type=int, default=2048, help="equalizers: frames per call")
     ap.add_argument("--mimo-steps", type=int, default=5, help="mimo: timed steps")
     ap.add_argument("--latency-frames", type=int, default=200, help="latency: frames per shape")
     ap.add_argument("--paper-calls", type=int, default=200, help="paper: timed one-packet calls")
@@ -1320,6 +1370,8 @@ def main():
         return impl_latency(args)
     if args.workload == "ber":
         return impl_ber(args)
+    if args.workload == "equalizers":
+        return impl_equalizers(args)
     return impl_zotfs(args)
 
 
