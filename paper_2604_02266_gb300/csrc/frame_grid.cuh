@@ -82,9 +82,12 @@ struct GridScratch {
   int* icnt;                     // [2 grid] per-CTA counts of the read-off compaction
   int* hist;                     // [5 x 128] radix-select histograms (zeroed per frame)
   GridBarrier* bar;
+  float2* ctab_g;                // [grid][p_max][cpc] the CG's coefficient tables when they do not
+                                 // fit shared memory (large p_max at large M)
   // shared-memory windows of the CG gathers (set by the launch): columns per window row (0: no
-  // windows) and the largest |dk| a window covers
-  int win_cols, win_dcap;
+  // windows) and the largest |dk| a window covers; tab_smem: the coefficient table in shared
+  // memory (else ctab_g, and no windows)
+  int win_cols, win_dcap, tab_smem;
 };
 
 // TMA descriptors of the extensions of c and t (row-major, rows N + E + 3 of 2 M 8-byte
@@ -107,6 +110,7 @@ __host__ __device__ __forceinline__ size_t grid_scratch_bytes(int M, int N, int 
   take((size_t)grid * 8);
   take(5 * 128 * 4);
   take(sizeof(GridBarrier));
+  take((size_t)grid * grid_cols_per_cta(M, grid) * p_max * sizeof(float2));  // ctab_g
   return b;
 }
 
@@ -132,8 +136,10 @@ __host__ __device__ __forceinline__ GridScratch grid_scratch_carve(char* base, i
   G.icnt = reinterpret_cast<int*>(take((size_t)grid * 8));
   G.hist = reinterpret_cast<int*>(take(5 * 128 * 4));
   G.bar = reinterpret_cast<GridBarrier*>(take(sizeof(GridBarrier)));
+  G.ctab_g = reinterpret_cast<float2*>(take((size_t)grid * grid_cols_per_cta(M, grid) * p_max * sizeof(float2)));
   G.win_cols = 0;
   G.win_dcap = -1;
+  G.tab_smem = 1;
   return G;
 }
 
@@ -688,7 +694,8 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
   // the CG's coefficient table (p_max rows of the CTA's columns) with the paths' forward
   // phases, and windows (p and c / t: N + E + 3 rows of G.win_cols columns each)
   C* ctab = reinterpret_cast<C*>(smem + off);
-  off += ((size_t)A.p_max * grid_cols_per_cta(A.M, (int)gridDim.x) * sizeof(C) + 127) & ~size_t(127);
+  off += ((size_t)A.p_max * (G.tab_smem ? grid_cols_per_cta(A.M, (int)gridDim.x) : 0) * sizeof(C) + 127) &
+         ~size_t(127);
   C* phi = reinterpret_cast<C*>(smem + off);
   off += ((size_t)A.p_max * sizeof(C) + 127) & ~size_t(127);
   C* bufP = reinterpret_cast<C*>(smem + off);
@@ -985,11 +992,14 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       // The per-(path, column) factors of Eq. sparse_mvm / Eq. sparse_herm_mvm on the CTA's
       // columns, h_p W[dl_p k] (the adjoint's, conjugated at use), and each path's phase
       // W[-dl_p dk_p] that turns one into the forward factor hf_p W[dl_p k] (paths in the
-      // sorted order of the runs).
+      // sorted order of the runs).  In shared memory, or when it does not fit there (large
+      // p_max at large M) in the CTA's slice of global scratch, read by the global route only.
+      C* const tabg = G.ctab_g + (size_t)blockIdx.x * A.p_max * cpc;
+      C* const tabp = G.tab_smem ? ctab : tabg;
       for (int e = tid; e < P * ncol; e += blockDim.x) {
         const int p = e / ncol, c = e - p * ncol;
         const PathRec& rec = paths[p];
-        ctab[p * cpc + c] = cmul(rec.h, tab<R>(A, (size_t)(rec.dl + (N >> 1)) * M + k0 + c));
+        tabp[p * cpc + c] = cmul(rec.h, tab<R>(A, (size_t)(rec.dl + (N >> 1)) * M + k0 + c));
       }
       for (int p = tid; p < P; p += blockDim.x)
         phi[p] = tw<R>(A, (size_t)((-paths[p].dl * paths[p].dk) & (MN - 1)));
@@ -1007,7 +1017,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       }
       __syncthreads();
       const int dmax = S->isc[5];
-      const bool win = G.win_cols > 0 && dmax <= G.win_dcap;
+      const bool win = G.tab_smem && G.win_cols > 0 && dmax <= G.win_dcap;
       const int A0 = (k0 - dmax) & ~1, Wc = ((k1 + dmax + 1) & ~1) - A0, Wp = G.win_cols;
       const int A1 = ncol > 0 ? A0 + Wc : A0;  // no window when the CTA has no columns
       const uint32_t box_bytes = (uint32_t)(N + E + 3) * (uint32_t)Wp * 8u;
@@ -1047,7 +1057,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         if (kk >= ncol) continue;
         const int k = k0 + kk, j0 = g * E;
         if (win) gather_adj<R, E, true, 2, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
-        else gather_adj<R, E, true, 2, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
+        else gather_adj<R, E, true, 2, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, tabp, phi, cpc, k0);
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           G.X[(size_t)(j0 + i) * M + k] = make_float2(0.f, 0.f);
@@ -1129,7 +1139,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
             const int g = s >> gshift, kk = s - (g << gshift);
             if (kk >= ncol) continue;
             const int k = k0 + kk, j0 = g * E;
-            gather_fwd<R, E, true, 2, false>(extPc, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
+            gather_fwd<R, E, true, 2, false>(extPc, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, tabp, phi, cpc, k0);
             grid_ext_store<E>(G.extT, A, k, j0, v, true, wn);
           }
         }
@@ -1144,7 +1154,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
           if (kk >= ncol) continue;
           const int k = k0 + kk, j0 = g * E;
           if (win) gather_adj<R, E, true, 2, false>(bufX, 0, paths, runs, nruns, A, 0, k, j0, v, nullptr, Wp, colw, ctab, phi, cpc, k0);
-          else gather_adj<R, E, true, 2, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, ctab, phi, cpc, k0);
+          else gather_adj<R, E, true, 2, false>(G.extT, blk, paths, runs, nruns, A, 0, k, j0, v, nullptr, 0, kColHalf, tabp, phi, cpc, k0);
 #pragma unroll
           for (int i = 0; i < E; ++i) {
             const C pv = p_at(k, j0 + i);
@@ -1247,8 +1257,9 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
   }
 }
 
-// win_cols: columns per row of the two CG windows (0: none); cpc: delay columns per CTA.
-__host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max, int win_cols, int cpc) {
+// win_cols: columns per row of the two CG windows (0: none); tab_cols: delay columns of the
+// coefficient table in shared memory (the CTA's columns; 0 when the table is in global memory).
+__host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max, int win_cols, int tab_cols) {
   size_t off = (sizeof(SharedHdr) + 127) & ~size_t(127);
   off += ((size_t)p_max * sizeof(PathRecT<float>) + sizeof(int) * 2 + 127) & ~size_t(127);
   off += ((size_t)p_max * sizeof(RunRec) + 127) & ~size_t(127);
@@ -1256,7 +1267,7 @@ __host__ __device__ __forceinline__ size_t grid_smem_bytes(int N, int p_max, int
   off += ((size_t)((p_max + 3) & ~3) * sizeof(int) + 127) & ~size_t(127);
   off += (size_t)N * kGridDftCols * sizeof(float2);
   off += ((size_t)N * sizeof(float2) + 127) & ~size_t(127);
-  off += ((size_t)p_max * cpc * sizeof(float2) + 127) & ~size_t(127);
+  off += ((size_t)p_max * tab_cols * sizeof(float2) + 127) & ~size_t(127);
   off += ((size_t)p_max * sizeof(float2) + 127) & ~size_t(127);
   off += 2 * grid_window_elems(N, win_cols) * sizeof(float2);
   return off;

@@ -131,10 +131,11 @@ void grid_window(int M, int N, int p_max, int grid, int occ, int smem_per_sm, in
 }
 
 cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, int ctas_per_sm, GridCfg& cfg) {
-  int dev = 0, smem_sm = 0, smem_res = 0;
+  int dev = 0, smem_sm = 0, smem_res = 0, smem_optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cfg.T = kGridThreads;
   cfg.EQ = 0;
@@ -147,23 +148,29 @@ cudaError_t choose_grid_cfg(int M, int N, int p_max, int sm_count, int ctas_per_
       const int grid = occ_t * sm_count;
       if (grid > kGridMaxCtas) return cudaErrorInvalidConfiguration;
       if ((long long)grid * kGridThreads * gv.EQ < (long long)M * N) break;  // the read-off needs more threads
-      int cols = 0, dcap = -1;
-      grid_window(M, N, p_max, grid, occ_t, smem_sm, smem_res, cols, dcap);
-      const size_t smem = grid_smem_bytes(N, p_max, cols, grid_cols_per_cta(M, grid));
-      e = grant(v, smem);
-      if (e != cudaSuccess) return e;
-      int occ = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gv.k, kGridThreads, smem);
-      if (e != cudaSuccess) return e;
-      if (occ < occ_t) continue;
-      cfg.EQ = gv.EQ;
-      cfg.E = gv.E;
-      cfg.variant = v;
-      cfg.grid = grid;
-      cfg.smem = smem;
-      cfg.win_cols = cols;
-      cfg.win_dcap = dcap;
-      return cudaSuccess;
+      // the coefficient table in shared memory (with windows when room is left), else in global
+      // memory with no windows
+      for (int tab_smem = 1; tab_smem >= 0; --tab_smem) {
+        int cols = 0, dcap = -1;
+        if (tab_smem) grid_window(M, N, p_max, grid, occ_t, smem_sm, smem_res, cols, dcap);
+        const size_t smem = grid_smem_bytes(N, p_max, cols, tab_smem ? grid_cols_per_cta(M, grid) : 0);
+        if (smem > (size_t)smem_optin) continue;
+        e = grant(v, smem);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gv.k, kGridThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < occ_t) continue;
+        cfg.EQ = gv.EQ;
+        cfg.E = gv.E;
+        cfg.variant = v;
+        cfg.grid = grid;
+        cfg.smem = smem;
+        cfg.win_cols = cols;
+        cfg.win_dcap = dcap;
+        cfg.tab_smem = tab_smem;
+        return cudaSuccess;
+      }
     }
   }
   return cudaErrorInvalidConfiguration;
@@ -179,6 +186,7 @@ cudaError_t grid_launch(const GridCfg& cfg, const FrameArgs& A, char* scratch, c
   GridScratch G = grid_scratch_carve(scratch, A.M, A.N, A.p_max, cfg.grid);
   G.win_cols = cfg.win_cols;
   G.win_dcap = cfg.win_dcap;
+  G.tab_smem = cfg.tab_smem;
   // the windows' tensor copies; without the descriptors the gathers read global memory
   GridMaps maps;
   memset(&maps, 0, sizeof(maps));

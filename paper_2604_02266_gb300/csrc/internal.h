@@ -146,6 +146,7 @@ struct GridCfg {
   int T, EQ, E, grid, variant;
   size_t smem;
   int win_cols, win_dcap;  // the CG windows: columns per row (0: none), largest |dk| covered
+  int tab_smem;            // the CG coefficient table in shared memory (else in global scratch)
 };
 bool grid_shape(int M, int N, int nrx, int ntx);
 // ctas_per_sm: the plan's tuning, CTAs per SM of the cooperative launch (0: as many as fit, at

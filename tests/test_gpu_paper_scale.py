@@ -240,6 +240,31 @@ def test_grid_windowed_and_global_gathers_agree(M, N, ctas):
             assert rel_l2(xs[name][f].reshape(-1), ref) < TOL_X, (name, f)
 
 
+def test_grid_large_p_max_tables_in_global_memory():
+    """p_max 256 at M = 16384: the CG's per-CTA coefficient tables (p_max x 54 columns) do not
+    fit shared memory, so they go to global scratch and the gathers take the global route.  An
+    equalisation with given lists and a read-off both still match the oracle."""
+    M, N, F, iters = 16384, 16, 1, 10
+    g = np.random.default_rng(9970)
+    plan = Plan(M, N, 1, 1, 16, p_max=256)
+    b = synth.fractional_batch(F, seed=9971, M=M, N=N, Q=16, snr_db=(20,))
+    # a compact list of 24 taps near the origin (what a read-off gives), complex64 gains
+    cand = [(a, c) for a in range(-4, 8) for c in range(-3, 3)]
+    pick = g.choice(len(cand), size=24, replace=False)
+    dk = np.array([cand[i][0] for i in pick])
+    dl = np.array([cand[i][1] for i in pick])
+    h = ((g.standard_normal(24) + 1j * g.standard_normal(24)) / np.sqrt(48)).astype(np.complex64).astype(complex)
+    lists = [dc.PathList.from_offsets(M, N, M // 2, N // 2, h, dk, dl)]
+    paths = fill_paths(plan.new_paths(F), lists, plan.p_max)
+    x = plan.equalize(to_dev(b["y_data_td"]), paths, to_dev(b["noise_var"]), iters, F).cpu().numpy()
+    y_dd = zak.vec(zak.dzt(b["y_data_td"][0, 0].astype(complex), M, N))
+    ref = eq.cga([[lists[0]]], y_dd, float(b["noise_var"][0]), iters)
+    assert rel_l2(x[0].reshape(-1), ref) < TOL_X
+    est = plan.estimate(to_dev(b["y_pilot_td"]), to_dev(b["theta"]), F).to_host()
+    heff = dc.heff_readoff(zak.dzt(b["y_pilot_td"][0, 0, 0].astype(complex), M, N), M // 2, N // 2, b["a_pilot"])
+    check_path_list(M, N, est[0], heff, float(b["theta"][0]), 256)
+
+
 def _cg_case_grid(M, N, F, seed):
     from tests.test_gpu_stages import _cg_case
     return _cg_case(M, N, F, 20, seed=seed)
