@@ -590,6 +590,7 @@ __device__ __forceinline__ int grid_select_q(const GridCand* cand, int n, const 
           if (acc < kleft && acc + c[j] >= kleft) {
             S->isc[2] = 4 * lane + j;
             S->isc[3] = kleft - acc;
+            S->isc[0] = c[j];  // taps in that bin
           }
           acc += c[j];
         }
@@ -598,10 +599,43 @@ __device__ __forceinline__ int grid_select_q(const GridCand* cand, int n, const 
       prefix |= (uint32_t)S->isc[2] << sh;
       kleft = S->isc[3];
       fixed |= ((1u << w) - 1u) << sh;
+      const int in_bin = S->isc[0];
       __syncthreads();
+      if (sh > 0 && in_bin <= min(256, tie_cap)) {
+        // Few taps share the bits fixed so far: rank them against each other directly (the
+        // kleft-th largest among them is the K-th largest of all) instead of further passes.
+        uint32_t match = 0;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+          if (((have >> j) & 1u) && ((key[j] ^ prefix) & fixed) == 0) match |= 1u << j;
+        int nm;
+        int mpos = block_exclusive_scan(__popc(match), S->scan, nm);
+        uint32_t* mk = reinterpret_cast<uint32_t*>(tq);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+          if ((match >> j) & 1u) mk[mpos++] = key[j];
+        __syncthreads();
+        for (int i = tid; i < nm; i += blockDim.x) {
+          const uint32_t x = mk[i];
+          int gtc = 0, gec = 0;
+          for (int t = 0; t < nm; ++t) {
+            gtc += mk[t] > x;
+            gec += mk[t] >= x;
+          }
+          if (gtc < kleft && kleft <= gec) {  // every writer stores the same pair
+            S->isc[2] = (int)x;
+            S->isc[3] = kleft - gtc;
+          }
+        }
+        __syncthreads();
+        prefix = (uint32_t)S->isc[2];
+        kleft = S->isc[3];
+        __syncthreads();
+        break;
+      }
     }
-    const uint32_t vK = prefix;
-    const int need = kleft;
+    const uint32_t vK = prefix;  // the K-th largest key (all 31 bits fixed, by passes or ranking)
+    const int need = kleft;      // keys equal to vK that are kept
     uint32_t gt = 0, eq = 0;
 #pragma unroll
     for (int j = 0; j < CPT; ++j)
