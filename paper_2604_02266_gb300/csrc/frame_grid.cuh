@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
         phi[p] = tw<R>(A, (size_t)((-paths[p].dl * paths[p].dk) & (MN - 1)));
       for (int i = tid; i < N; i += blockDim.x) wn[i] = conjf2(tw<R>(A, (size_t)i << logM));  // W_N^{-l}
       // Window mode, when every path's |dk| is within the launch's cap: the CTA keeps p over the
-      // columns [A0, A1) -- its own and dmax more on either side -- in shared memory, forming it
+      // columns [A0, A0 + Wc) -- its own and dmax more on either side -- in shared memory, forming it
       // there from a window of c each iteration (so no grid barrier separates the p update from
       // the forward gather), and gathers t from a window of t.  Otherwise the gathers read the
       // global extensions, p included.
@@ -1053,7 +1053,6 @@ __global__ void __launch_bounds__(kGridThreads, MINB)
       const int dmax = S->isc[5];
       const bool win = G.tab_smem && G.win_cols > 0 && dmax <= G.win_dcap;
       const int A0 = (k0 - dmax) & ~1, Wc = ((k1 + dmax + 1) & ~1) - A0, Wp = G.win_cols;
-      const int A1 = ncol > 0 ? A0 + Wc : A0;  // no window when the CTA has no columns
       const uint32_t box_bytes = (uint32_t)(N + E + 3) * (uint32_t)Wp * 8u;
       const int Rw = N + E + 3, colw = -A0;
 
